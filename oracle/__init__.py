@@ -1,0 +1,178 @@
+"""FP64 CPU oracle of the lattice-Boltzmann plasma-wakefield step.
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline / reference arm of ``bench.py`` may import this package. The GPU
+library never calls it and shares no code with it.
+
+The arithmetic lives in ``pwfa_oracle.cpp`` (plain loops in double precision,
+one function per step of the method: Faraday, collision + source, streaming,
+Eq. 14 boundary, Ampere). This module only builds that file with g++ and
+marshals NumPy arrays through ctypes.
+
+Array layouts of every accessor: populations ``[lattice][q][z][y][x]``, Yee
+fields ``[component][z][y][x]`` (E_x at (i+1/2, j, k), B_x at (i, j+1/2, k+1/2)
+and cyclic), node quantities ``[component][z][y][x]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pwfa_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+COLL_BGK, COLL_REG, COLL_NONE = 0, 1, 2
+BND_OPEN, BND_PERIODIC = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (g++, OpenMP)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-Wall",
+           "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
+        ("collision", ctypes.c_int32), ("boundary", ctypes.c_int32), ("couple", ctypes.c_int32),
+        ("n0", ctypes.c_double),
+        ("profile", ctypes.POINTER(ctypes.c_double)), ("n_profile", ctypes.c_int32),
+        ("profile_rmax", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("sigma_r", ctypes.c_double), ("sigma_z", ctypes.c_double),
+        ("z0", ctypes.c_double),
+        ("n_floor", ctypes.c_double),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.oracle_create.restype = ctypes.c_void_p
+            lib.oracle_create.argtypes = [ctypes.POINTER(_Params)]
+            lib.oracle_destroy.argtypes = [ctypes.c_void_p]
+            lib.oracle_step.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+            lib.oracle_steps_done.restype = ctypes.c_int64
+            lib.oracle_steps_done.argtypes = [ctypes.c_void_p]
+            for name in ("oracle_get_f", "oracle_set_f", "oracle_set_equilibrium",
+                         "oracle_moments", "oracle_diag"):
+                getattr(lib, name).argtypes = [ctypes.c_void_p, dp]
+            lib.oracle_get_fields.argtypes = [ctypes.c_void_p, dp, dp]
+            lib.oracle_set_fields.argtypes = [ctypes.c_void_p, dp, dp]
+            lib.oracle_last_step.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
+            lib.oracle_qtilde.restype = ctypes.c_double
+            lib.oracle_qtilde.argtypes = [ctypes.c_double] * 5 + [dp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Oracle:
+    """One FP64 simulation instance (see ``pwfa_oracle.cpp`` for the step)."""
+
+    def __init__(self, nx, ny, nz, dx, dt, tau, collision=COLL_BGK, boundary=BND_OPEN,
+                 couple=1, n0=1.0, profile=None, profile_rmax=0.0, alpha=0.0,
+                 sigma_r=0.5, sigma_z=0.5, z0=0.0, n_floor=1e-6):
+        self._lib = _load()
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        prof = None if profile is None else np.ascontiguousarray(profile, dtype=np.float64)
+        self._prof = prof
+        p = _Params(nx, ny, nz, dx, dt, tau, collision, boundary, couple, n0,
+                    _ptr(prof) if prof is not None else None,
+                    0 if prof is None else len(prof), profile_rmax,
+                    alpha, sigma_r, sigma_z, z0, n_floor)
+        self._h = self._lib.oracle_create(ctypes.byref(p))
+        if not self._h:
+            raise ValueError("oracle_create rejected the parameters")
+        self.params = dict(nx=nx, ny=ny, nz=nz, dx=dx, dt=dt, tau=tau, collision=collision,
+                           boundary=boundary, couple=couple, n0=n0, alpha=alpha,
+                           sigma_r=sigma_r, sigma_z=sigma_z, z0=z0, n_floor=n_floor)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.oracle_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        self._lib.oracle_step(self._h, int(n))
+
+    @property
+    def steps_done(self) -> int:
+        return int(self._lib.oracle_steps_done(self._h))
+
+    def get_f(self) -> np.ndarray:
+        out = np.empty((4, 19) + self.shape, dtype=np.float64)
+        self._lib.oracle_get_f(self._h, _ptr(out))
+        return out
+
+    def set_f(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape((4, 19) + self.shape)
+        self._lib.oracle_set_f(self._h, _ptr(f))
+
+    def set_equilibrium(self, A: np.ndarray):
+        A = np.ascontiguousarray(A, dtype=np.float64).reshape((4,) + self.shape)
+        self._lib.oracle_set_equilibrium(self._h, _ptr(A))
+
+    def get_fields(self):
+        E = np.empty((3,) + self.shape, dtype=np.float64)
+        B = np.empty((3,) + self.shape, dtype=np.float64)
+        self._lib.oracle_get_fields(self._h, _ptr(E), _ptr(B))
+        return E, B
+
+    def set_fields(self, E: np.ndarray, B: np.ndarray):
+        E = np.ascontiguousarray(E, dtype=np.float64).reshape((3,) + self.shape)
+        B = np.ascontiguousarray(B, dtype=np.float64).reshape((3,) + self.shape)
+        self._lib.oracle_set_fields(self._h, _ptr(E), _ptr(B))
+
+    def moments(self) -> dict:
+        out = np.empty((8,) + self.shape, dtype=np.float64)
+        self._lib.oracle_moments(self._h, _ptr(out))
+        return {"n": out[0], "beta": out[1:4], "A": out[4:7], "beta_abs": out[7]}
+
+    def last_step(self) -> dict:
+        J = np.empty((3,) + self.shape)
+        F = np.empty((4,) + self.shape)
+        En = np.empty((3,) + self.shape)
+        Bn = np.empty((3,) + self.shape)
+        self._lib.oracle_last_step(self._h, _ptr(J), _ptr(F), _ptr(En), _ptr(Bn))
+        return {"J": J, "F": F, "E_node": En, "B_node": Bn}
+
+    def diag(self) -> np.ndarray:
+        out = np.empty(8, dtype=np.float64)
+        self._lib.oracle_diag(self._h, _ptr(out))
+        return out
+
+
+def qtilde(charge_coulomb, sx, sy, sz, n0_m3):
+    """Normalised charge (Eq. 15, read with k_p^3) and alpha = n_b/n0."""
+    a = np.zeros(1)
+    q = _load().oracle_qtilde(charge_coulomb, sx, sy, sz, n0_m3, _ptr(a))
+    return q, float(a[0])

@@ -1,0 +1,130 @@
+"""Seeded synthetic workloads shared by the tests, the smoke run and the bench.
+
+This module only states inputs: grid sizes, resolutions, driver parameters and
+seeded random draws. It holds none of the method's arithmetic and imports
+neither the GPU library nor the oracle.
+
+Shapes follow the paper's test case (Sec. IV): a bi-Gaussian electron driver in
+a uniform cold plasma, normalised charge between the linear (Q ~ 0.1) and the
+non-linear (Q ~ 1) regime, and the paper's ratio c dt / dz = 0.17628 (dt =
+0.147 fs at dz = 0.25 um, n0 = 1e16 cm^-3, so c/omega_p = 53.14 um).
+Lengths are in c/omega_p, times in 1/omega_p, densities in n0.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+#: c dt / dx of the paper's run: 0.147 fs * c / 0.25 um.
+DT_OVER_DX = 0.17628
+
+BGK, REGULARIZED, STREAM_ONLY = 0, 1, 2
+OPEN, PERIODIC = 0, 1
+F32, BF16, F16 = 0, 1, 2
+
+
+@dataclasses.dataclass
+class Workload:
+    """One simulation instance: grid, resolution, collision and driver."""
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    tau: float
+    alpha: float          # peak n_b / n0 of the driver
+    sigma_r: float
+    sigma_z: float
+    z0: float             # driver centre at t = 0
+    steps: int
+    collision: int = BGK
+    boundary: int = OPEN
+    storage: int = F32
+    couple: int = 1
+    n0: float = 1.0
+    n_floor: float = 1e-6
+    profile: np.ndarray | None = None
+    profile_rmax: float = 0.0
+    name: str = ""
+
+    @property
+    def dt(self) -> float:
+        return DT_OVER_DX * self.dx
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def replace(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+
+def parity_small() -> Workload:
+    """Plain method, 64x32x32 (z, y, x) at dx = 0.2, linear driver
+    n_b/n0 = 0.1, sigma_z = sigma_r = 0.5, 200 steps, BGK, open boundary."""
+    return Workload(nx=32, ny=32, nz=64, dx=0.2, tau=0.51, alpha=0.1, sigma_r=0.5,
+                    sigma_z=0.5, z0=-2.0, steps=200, name="lbm-pwfa 64x32x32 dx0.2 BGK")
+
+
+def production() -> Workload:
+    """Production forward run, 512x256x256 (z, y, x) at dx = 0.05, non-linear
+    driver n_b/n0 = 1.0, sigma_z = 0.5, sigma_r = 0.3, regularized collision,
+    2000 steps."""
+    return Workload(nx=256, ny=256, nz=512, dx=0.05, tau=0.51, alpha=1.0, sigma_r=0.3,
+                    sigma_z=0.5, z0=-2.0, steps=2000, collision=REGULARIZED,
+                    name="lbm-pwfa 512x256x256 dx0.05 regularized")
+
+
+def precision_form(storage: int = BF16) -> Workload:
+    """Config-1 physics on 256x128x128 with reduced-precision storage, 1000 steps."""
+    w = parity_small().replace(nx=128, ny=128, nz=256, steps=1000, storage=storage)
+    w.name = "lbm-pwfa 256x128x128 dx0.2 BGK store%s" % {F32: "f32", BF16: "bf16", F16: "f16"}[storage]
+    return w
+
+
+def differentiable() -> Workload:
+    """256x128x128, n_b/n0 = 0.5, 500 steps (gradients of a witness E_z loss)."""
+    return parity_small().replace(nx=128, ny=128, nz=256, alpha=0.5, steps=500,
+                                  name="lbm-pwfa 256x128x128 adjoint")
+
+
+def batched_scan(n_instances: int = 64, seed: int = 0, steps: int = 500):
+    """Parameter scan: grids k*(16, 8, 8) nodes (z, y, x) with k in {4..16},
+    n_b/n0 ~ U[0.05, 2.0], sigma_r, sigma_z ~ U[0.3, 1.0], z0 = -4 sigma_z."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for m in range(n_instances):
+        k = int(rng.integers(4, 17))
+        alpha = float(rng.uniform(0.05, 2.0))
+        sr = float(rng.uniform(0.3, 1.0))
+        sz = float(rng.uniform(0.3, 1.0))
+        out.append(Workload(nx=8 * k, ny=8 * k, nz=16 * k, dx=0.2, tau=0.51, alpha=alpha,
+                            sigma_r=sr, sigma_z=sz, z0=-4.0 * sz, steps=steps,
+                            name=f"scan{m}"))
+    return out
+
+
+def random_populations(shape_zyx, seed: int = 1, base: float = 1.0, spread: float = 0.05):
+    """Positive random populations [4][19][z][y][x] around a plasma at rest:
+    lattice 0 near base*w_i-sized values, momentum lattices small and signed."""
+    rng = np.random.default_rng(seed)
+    f = np.empty((4, 19) + tuple(shape_zyx))
+    f[0] = base / 19.0 * (1.0 + spread * rng.standard_normal(f[0].shape))
+    f[1:] = base / 19.0 * spread * rng.standard_normal(f[1:].shape)
+    return f
+
+
+def integer_populations(shape_zyx):
+    """Distinct integers (l*19 + q)*N + node, exactly representable in float32
+    while 76*N < 2^24; used for bit-exact streaming checks."""
+    nz, ny, nx = shape_zyx
+    N = nx * ny * nz
+    node = np.arange(N, dtype=np.float64).reshape(shape_zyx)
+    f = np.empty((4, 19) + tuple(shape_zyx))
+    for l in range(4):
+        for q in range(19):
+            f[l, q] = (l * 19 + q) * float(N) + node
+    if f.max() >= 2 ** 24:
+        raise ValueError("grid too large for exact float32 integer populations")
+    return f
