@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput of the fused LBM plasma-wakefield step on GB300.
+
+Metric: GLUPS (1e9 node-steps per second; one node-step advances all four
+D3Q19 lattices and the Yee fields of one node) and the fraction of the HBM
+roofline, on the production workload: 512x256x256 nodes (z, y, x), dx = 0.05
+c/omega_p, non-linear driver n_b/n0 = 1, sigma_z = 0.5, sigma_r = 0.3,
+regularized collision, FP32. Synthetic inputs: the initial condition is the
+paper's cold plasma at rest with a rigid Gaussian driver (no dataset exists).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 run under torchrun: every rank advances its own replica (the path
+has no data exchange between instances), value = all ranks' node-steps /
+max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2201_05473_gb300 import workloads as W  # noqa: E402
+
+METRIC = "GLUPS & %HBM peak, fused fwd and adjoint step, FP32 vs BF16-store"
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6800.0
+# Algorithmic bytes per node of the fused fluid kernel (FP32 storage):
+# 76 populations read + 76 written (608 B), E (12 B) and B at t_n and t_{n+1}
+# (24 B) read, node current J (12 B) written.
+FLUID_BYTES_F32 = 76 * 4 * 2 + 12 + 24 + 12
+# Algorithmic bytes per node-step of the whole step: populations read+write
+# plus E and B read+write.
+STEP_BYTES = {W.F32: 608 + 48, W.BF16: 304 + 48, W.F16: 304 + 48}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fluid_kernel_traffic.json")
+KERNEL_SOURCES = ["paper_2201_05473_gb300/csrc/fluid.cu", "paper_2201_05473_gb300/csrc/lbm_node.cuh",
+                  "paper_2201_05473_gb300/csrc/lbm_device.cuh"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d and isinstance(d[k], (int, float)):
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(nodes):
+    """DRAM bytes per fluid launch from the committed ncu capture, if it was
+    taken on the current kernel source; else None."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    try:
+        d = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None
+    if d.get("source_sha") != kernel_source_hash():
+        return None
+    return float(d["bytes_per_node"]) * nodes
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            c = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(target_seconds: float = 12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the production
+    workload: a 128x64x64 (z, y, x) sub-box with the same physics, stepped
+    until ~target_seconds of wall time."""
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+    oracle.build()
+    w = W.production().replace(nx=64, ny=64, nz=128, z0=-1.0)
+    o = oracle.Oracle(w.nx, w.ny, w.nz, w.dx, w.dt, w.tau, collision=w.collision, alpha=w.alpha,
+                      sigma_r=w.sigma_r, sigma_z=w.sigma_z, z0=w.z0)
+    o.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < target_seconds and steps < 400:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    o.close()
+    return {"value": w.nodes * steps / dt / 1e9, "unit": "GLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"FP64 oracle, {w.nz}x{w.ny}x{w.nx} sub-box of the 512x256x256 regularized workload, "
+                      f"{steps} steps in {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, each step a bounded
+    sample (64x64x128 sub-box) of the production workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+    oracle.build()
+    w = W.production().replace(nx=64, ny=64, nz=128, z0=-1.0)
+    o = oracle.Oracle(w.nx, w.ny, w.nz, w.dx, w.dt, w.tau, collision=w.collision, alpha=w.alpha,
+                      sigma_r=w.sigma_r, sigma_z=w.sigma_z, z0=w.z0)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    val = w.nodes * args.steps / dt / 1e9
+    line = {"metric": METRIC, "value": val, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": W.production().name, "sample": f"{w.nz}x{w.ny}x{w.nx} sub-box per step",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": val, "unit": "GLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle", "sample": f"{w.nz}x{w.ny}x{w.nx} sub-box of the "
+                                                          f"512x256x256 regularized workload, {args.steps} steps"},
+            "e2e": {"value": val, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2201_05473_gb300 import lbm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    lbm.load()
+    w = W.production()
+    if args.grid:
+        nz, ny, nx = (int(v) for v in args.grid.lower().split("x"))
+        w = w.replace(nx=nx, ny=ny, nz=nz, name=f"lbm-pwfa {nz}x{ny}x{nx} dx0.05 regularized")
+    if args.storage != "f32":
+        w = w.replace(storage={"bf16": W.BF16, "f16": W.F16}[args.storage])
+    N = w.nodes
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        sim = lbm.Simulation(w, stream=stream)
+        sim.step(args.warmup)
+        sim.kernel_times()  # reset counters
+        barrier()
+        # ---- value: K steps, device-timed with CUDA events on the stream
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev) as clk:
+            ev0.record(stream)
+            sim.step(args.steps)
+            ev1.record(stream)
+            stream.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        _, launches = sim.kernel_times()
+        # ---- per-kernel roofline: the same K steps with event pairs per kernel
+        sim.profile(True)
+        sim.step(args.steps)
+        kms, kl = sim.kernel_times()
+        sim.profile(False)
+        diag = sim.diag(check=False)
+        sim.close()
+        del sim
+        torch.cuda.synchronize()
+        # ---- e2e through the C ABI with host buffers: create from host
+        # params, K steps each followed by a device->host read of the FP64
+        # diagnostics, destroy.
+        e2e_s = float("nan")
+        if not args.no_e2e:
+            torch.cuda.empty_cache()
+            barrier()
+            host_diag = torch.zeros(8, dtype=torch.float64).pin_memory()
+            t0 = time.perf_counter()
+            sim = lbm.Simulation(w, stream=stream)
+            for _ in range(args.steps):
+                sim.step(1)
+                sim.diag_into(host_diag)
+            sim.close()
+            stream.synchronize()
+            e2e_s = time.perf_counter() - t0
+    ms_t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = ms_t.tolist()
+    value = world * N * args.steps / (ms_max * 1e-3) / 1e9
+    e2e_val = world * N * args.steps / e2e_max / 1e9
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = hbm_peak()
+    fluid_ms = kms["fluid"] / max(kl["fluid"], 1)
+    fluid_bytes = (FLUID_BYTES_F32 if w.storage == W.F32 else 76 * 2 * 2 + 48) * N
+    achieved = fluid_bytes / (fluid_ms * 1e-3) / 1e9
+    step_bytes = STEP_BYTES[w.storage]
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": w.name, "grid_zyx": [w.nz, w.ny, w.nx], "dx": w.dx, "dt": w.dt, "tau": w.tau,
+                   "driver": {"nb_over_n0": w.alpha, "sigma_r": w.sigma_r, "sigma_z": w.sigma_z},
+                   "storage": args.storage,
+                   "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * 76 * (4 if w.storage == W.F32 else 2) * N / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pct_hbm_step": {"of_" + peak_kind: value * 1e9 * step_bytes / (peak * 1e9),
+                         "of_nominal_8000": value * 1e9 * step_bytes / (NOMINAL_HBM_GBS * 1e9),
+                         "bytes_per_node_step": step_bytes},
+        "roofline": {"bound": "hbm", "kernel": "fluid", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(N), "algorithmic_bytes_per_launch": fluid_bytes,
+                     "avg_launch_ms": fluid_ms},
+        "kernel_ms_per_step": {k: kms[k] / max(kl[k], 1) for k in kms},
+        "gpu_launches": int(sum(launches.values())),
+        "e2e": {"value": e2e_val, "unit": "GLUPS",
+                "h2d_bytes_per_step": lbm.ctypes.sizeof(lbm.Params) / args.steps,
+                "d2h_bytes_per_step": 64,
+                "note": "create from host params + per step pwfa_lbm_step and a D2H read of the FP64 diagnostics"},
+        "clocks": clk.summary(),
+        "diag_after": {"sum_n": diag[0], "min_n": diag[5], "max_beta": diag[6], "nonfinite": diag[7]},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", default="", help="override the grid as ZxYxX (profiling captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

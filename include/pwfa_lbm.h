@@ -1,0 +1,194 @@
+/*
+ * pwfa_lbm.h - C ABI of the GB300 lattice-Boltzmann plasma-wakefield step.
+ *
+ * Method: Parise et al., "Lattice Boltzmann simulations of plasma wakefield
+ * acceleration", arXiv:2201.05473. The electron plasma is a cold relativistic
+ * fluid (Eq. 2) advanced as four D3Q19 advection-diffusion lattices for
+ * A = (n, n p_x, n p_y, n p_z) (Eq. 4 generalised to Cartesian momentum),
+ * each with BGK collision (Eq. 7), equilibrium Eq. 9 in lattice units
+ * (c_s^2 = 1/3, diffusivity D = (tau - 1/2)/3 of Eq. 12), source S_i = w_i F dt
+ * (Eq. 10) with the Lorentz force F = -n (E + beta x B) (Eq. 4), and
+ * equilibrium boundary nodes (Eq. 14). It is coupled to Maxwell's equations
+ * (Eq. 5) on a Yee grid (FDTD) through the current J = -n beta, and driven by
+ * a rigid bi-Gaussian electron bunch moving at c along +z.
+ *
+ * Units: time 1/omega_p, length c/omega_p, density n0, momentum m_e c,
+ * E and B in m_e c omega_p / e.
+ *
+ * Conventions shared by every call:
+ *   - Grid nodes x_i = i dx, i = 0..nx-1 (same for y, z); z is the driver's
+ *     propagation axis. Every node array is [z][y][x], x fastest.
+ *   - Yee staggering: E_x at (i+1/2, j, k), E_y at (i, j+1/2, k), E_z at
+ *     (i, j, k+1/2); B_x at (i, j+1/2, k+1/2), B_y at (i+1/2, j, k+1/2),
+ *     B_z at (i+1/2, j+1/2, k). Each stored as an [z][y][x] array indexed by
+ *     the integer part of its position.
+ *   - D3Q19 order: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (1,1,0),
+ *     (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1),
+ *     (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1). Populations are exchanged as
+ *     [lattice 0..3][q 0..18][z][y][x].
+ *   - Time levels: after s steps the populations and B are at t_s = s dt and
+ *     E at t_{s+1/2}.
+ *   - Every call returns PWFA_OK (0) or a negative PWFA_ERR_* code; the
+ *     message of the last failure on the calling thread is returned by
+ *     pwfa_lbm_last_error(). No C++ exception crosses this boundary.
+ *   - Pointers named dev_* must be device memory; pointers named out/in may
+ *     be host or device memory (the library checks with
+ *     cudaPointerGetAttributes and copies as needed). Caller-owned memory is
+ *     never retained after a call returns.
+ *   - All device work is ordered on the stream given at create (or set with
+ *     pwfa_lbm_set_stream). Calls that return data to host memory synchronise
+ *     that stream; the others are asynchronous.
+ */
+#ifndef PWFA_LBM_H
+#define PWFA_LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PWFA_OK 0
+#define PWFA_ERR_PARAM (-1)    /* invalid argument or parameter set */
+#define PWFA_ERR_CUDA (-2)     /* a CUDA runtime call or kernel launch failed */
+#define PWFA_ERR_UNSTABLE (-3) /* diagnostics found a non-finite value or n < 0 */
+#define PWFA_ERR_TIMEOUT (-4)  /* a bounded device-side wait expired */
+#define PWFA_ERR_ALLOC (-5)    /* device memory allocation failed */
+#define PWFA_ERR_STATE (-6)    /* call not valid in the handle's current state */
+
+/* Collision operator of every lattice. */
+#define PWFA_BGK 0          /* Eq. 7: f* = f - (f - f^eq)/tau + w_i F dt */
+#define PWFA_REGULARIZED 1  /* BGK on the first-order Hermite projection of f - f^eq
+                               (the paper names "more complicated" operators without
+                               defining one; this is the builder's choice) */
+#define PWFA_STREAM_ONLY 2  /* no collision and no source: pure streaming (testing) */
+
+/* Storage format of the populations (compute is always FP32). */
+#define PWFA_F32 0
+#define PWFA_BF16 1  /* deviations f - w_i n0 (lattice 0) and f (lattices 1-3), bf16 */
+#define PWFA_F16 2   /* same deviations in IEEE binary16 */
+
+/* Boundary treatment. */
+#define PWFA_OPEN 0      /* Eq. 14: boundary nodes = f^eq of the clamped interior
+                            node ("free flux"); conducting walls for the fields */
+#define PWFA_PERIODIC 1  /* every axis wraps */
+
+typedef struct {
+    int32_t nx, ny, nz;    /* grid nodes; each >= 3 */
+    double dx;             /* node spacing in c/omega_p, > 0 */
+    double dt;             /* time step in 1/omega_p; 0 selects 0.17628 dx, the
+                              paper's c dt / dz (Sec. IV); must satisfy
+                              dt < dx / sqrt(3) (Yee Courant limit) */
+    double tau;            /* BGK relaxation time in lattice units, > 0.5 (Eq. 12) */
+    int32_t collision;     /* PWFA_BGK / PWFA_REGULARIZED / PWFA_STREAM_ONLY */
+    int32_t storage;       /* PWFA_F32 / PWFA_BF16 / PWFA_F16 */
+    int32_t boundary;      /* PWFA_OPEN / PWFA_PERIODIC */
+    int32_t couple;        /* 1: Lorentz source + Maxwell update; 0: fluid only */
+    double n0;             /* background electron density (normalised, >= 0) */
+    const double* profile; /* host array of n_profile radial multipliers of n0 at
+                              r_j = j profile_rmax / (n_profile - 1), linear in
+                              between, last value beyond; NULL = uniform. Copied
+                              at create. r is measured from the axis
+                              x_c = (nx-1) dx / 2, y_c = (ny-1) dx / 2. */
+    int32_t n_profile;     /* 0 or >= 1 */
+    double profile_rmax;   /* > 0 when n_profile >= 2 */
+    double alpha;          /* driver peak density n_b / n0 (Eq. 15's alpha) */
+    double sigma_r;        /* driver rms radius, > 0 */
+    double sigma_z;        /* driver rms length, > 0 */
+    double z0;             /* driver centre at t = 0; it moves as z0 + t */
+    double n_floor;        /* p = A / max(n, n_floor); 0 selects 1e-6 */
+} pwfa_lbm_params;
+
+typedef struct pwfa_lbm pwfa_lbm_t;
+
+/* Create n_instances independent simulations (params is an array of that
+ * length), allocate their device state and set the initial condition: a cold
+ * plasma at rest with density n0 * profile(r), E = B = 0 (Sec. IV test case).
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream). The handle
+ * owns all device memory it allocates. On failure *out is NULL. */
+int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances,
+                    void* cuda_stream, pwfa_lbm_t** out);
+
+/* Advance every instance by nsteps (>= 0) time steps: Faraday, fused
+ * pull-stream + moments + Lorentz source + collision (Eqs. 6-10, 14), Ampere
+ * with J = -n beta and the driver current. Asynchronous on the stream. */
+int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps);
+
+/* Field export masks for pwfa_lbm_fields. */
+#define PWFA_FIELD_N (1u << 0)   /* electron density n = sum of lattice 0 */
+#define PWFA_FIELD_UX (1u << 1)  /* beta_x = p_x / sqrt(1 + p^2) */
+#define PWFA_FIELD_UY (1u << 2)
+#define PWFA_FIELD_UZ (1u << 3)
+#define PWFA_FIELD_EX (1u << 4)
+#define PWFA_FIELD_EY (1u << 5)
+#define PWFA_FIELD_EZ (1u << 6)
+#define PWFA_FIELD_BX (1u << 7)
+#define PWFA_FIELD_BY (1u << 8)
+#define PWFA_FIELD_BZ (1u << 9)
+#define PWFA_FIELD_JX (1u << 10) /* plasma current of the last step, at nodes */
+#define PWFA_FIELD_JY (1u << 11)
+#define PWFA_FIELD_JZ (1u << 12)
+#define PWFA_FIELD_PX (1u << 13) /* momentum density A_k = n p_k */
+#define PWFA_FIELD_PY (1u << 14)
+#define PWFA_FIELD_PZ (1u << 15)
+#define PWFA_RAW_YEE (1u << 31)  /* E, B as raw staggered Yee arrays instead of
+                                    node averages */
+
+/* Export the selected fields of one instance at its current time level into
+ * out (host or device), one [z][y][x] block of nx*ny*nz floats per set bit
+ * in increasing bit order. out_elems must be >= (#bits) * nodes; out may be
+ * NULL when only diagnostics are wanted. E and B are averaged to the nodes
+ * (E from its two edges, B from its four faces) unless PWFA_RAW_YEE is set.
+ * host_diag (nullable, 8 doubles, host) receives FP64 reductions over the
+ * instance: [0] sum n, [1..3] sum n p_k, [4] field energy 1/2 sum(E^2+B^2) dx^3,
+ * [5] min n, [6] max |beta|, [7] count of non-finite moments. A non-NULL
+ * host_diag synchronises the stream and returns PWFA_ERR_UNSTABLE (after
+ * filling host_diag) when [7] > 0 or [5] < 0. */
+int pwfa_lbm_fields(pwfa_lbm_t* h, int32_t instance, uint32_t mask, float* out,
+                    int64_t out_elems, double* host_diag);
+
+/* Full state of one instance: pre-collision populations f^n
+ * [4][19][z][y][x], raw Yee E (t_{n+1/2}) and B (t_n) [3][z][y][x]. Any of the
+ * three pointers may be NULL. Host or device memory. In open mode the
+ * boundary-node populations are not independent state: they are exported
+ * and re-derived as f^eq of the clamped interior node (Eq. 14). */
+int pwfa_lbm_get_state(pwfa_lbm_t* h, int32_t instance, float* f, float* E, float* B);
+int pwfa_lbm_set_state(pwfa_lbm_t* h, int32_t instance, const float* f,
+                       const float* E, const float* B);
+
+/* Steps taken by an instance so far (>= 0), or a negative error code. */
+int64_t pwfa_lbm_steps_done(pwfa_lbm_t* h, int32_t instance);
+
+/* Kernel kinds reported by pwfa_lbm_kernel_times. */
+#define PWFA_KERNEL_FARADAY 0 /* Yee B update */
+#define PWFA_KERNEL_FLUID 1   /* fused stream + moments + source + collide */
+#define PWFA_KERNEL_AMPERE 2  /* Yee E update with plasma and driver current */
+#define PWFA_KERNEL_KINDS 3
+
+/* Per-kernel device timing, off by default. While enabled, each step records
+ * a CUDA event pair around every kernel it launches on the handle's stream
+ * (no synchronisation is added). */
+int pwfa_lbm_profile(pwfa_lbm_t* h, int32_t enable);
+
+/* Synchronise the stream and return, per kernel kind, the device time in ms
+ * accumulated while profiling was enabled (ms, nullable, PWFA_KERNEL_KINDS
+ * doubles) and the number of launches (launches, nullable, PWFA_KERNEL_KINDS
+ * int64, counted whether or not profiling is on) since the previous call;
+ * both accumulators are then reset. */
+int pwfa_lbm_kernel_times(pwfa_lbm_t* h, double* ms, int64_t* launches);
+
+/* Re-target all later work of the handle to another cudaStream_t. */
+int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream);
+
+/* Release every device allocation of the handle. Accepts NULL. */
+int pwfa_lbm_destroy(pwfa_lbm_t* h);
+
+/* Message of the last failure on the calling thread ("" if none). The
+ * pointer stays valid until the next call on this thread. */
+const char* pwfa_lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PWFA_LBM_H */

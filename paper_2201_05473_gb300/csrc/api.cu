@@ -1,0 +1,469 @@
+// Host runtime of the C ABI declared in include/pwfa_lbm.h: parameter
+// validation, one device arena per instance, the per-step launch sequence
+// (Faraday -> fused fluid -> Ampere), state exchange and diagnostics.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pwfa_lbm.h"
+#include "lbm_kernels.h"
+
+using namespace pwfa;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(PWFA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PWFA_CUDA(call, where)                          \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+size_t storage_bytes(int st) { return st == PWFA_F32 ? 4 : 2; }
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Instance {
+    pwfa_lbm_params p{};
+    std::vector<double> profile;
+    Grid g{};
+    void* arena = nullptr;
+    void* f[2] = {nullptr, nullptr};
+    int fcur = 0;
+    float* E[3] = {nullptr, nullptr, nullptr};
+    float* B[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int bcur = 0;
+    float* J[3] = {nullptr, nullptr, nullptr};
+    double* d_profile = nullptr;
+    int64_t steps = 0;
+};
+
+}  // namespace
+
+struct pwfa_lbm {
+    std::vector<Instance> inst;
+    cudaStream_t stream = nullptr;
+    double* d_partials = nullptr;  // kDiagBlocks x 8 doubles
+    double* d_diag = nullptr;      // 8 doubles
+    void* staging = nullptr;       // device buffer for host-side exchanges
+    size_t staging_bytes = 0;
+    // per-kernel timing
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;          // pool, used in start/stop pairs
+    std::vector<int> pending_kind;            // kind of each recorded pair
+    double ms[PWFA_KERNEL_KINDS] = {0, 0, 0};
+    int64_t launches[PWFA_KERNEL_KINDS] = {0, 0, 0};
+};
+
+namespace {
+
+int validate(const pwfa_lbm_params& p, int idx) {
+    char buf[256];
+    auto bad = [&](const char* what) {
+        std::snprintf(buf, sizeof buf, "instance %d: %s", idx, what);
+        return fail(PWFA_ERR_PARAM, buf);
+    };
+    if (p.nx < 3 || p.ny < 3 || p.nz < 3) return bad("nx, ny, nz must be >= 3");
+    if ((int64_t)p.nx * p.ny > (int64_t)1 << 30 || p.nz > 65535) return bad("grid too large");
+    if (!(p.dx > 0) || !std::isfinite(p.dx)) return bad("dx must be > 0");
+    if (!(p.dt >= 0) || !std::isfinite(p.dt)) return bad("dt must be >= 0 (0 = default)");
+    const double dt = p.dt > 0 ? p.dt : 0.17628 * p.dx;
+    if (p.couple && !(dt < p.dx / std::sqrt(3.0))) return bad("dt violates the Yee Courant limit dx/sqrt(3)");
+    if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return bad("tau must be > 0.5");
+    if (p.collision < 0 || p.collision > 2) return bad("unknown collision operator");
+    if (p.storage < 0 || p.storage > 2) return bad("unknown storage format");
+    if (p.boundary < 0 || p.boundary > 1) return bad("unknown boundary mode");
+    if (p.couple < 0 || p.couple > 1) return bad("couple must be 0 or 1");
+    if (!(p.n0 >= 0) || !std::isfinite(p.n0)) return bad("n0 must be >= 0");
+    if (p.n_profile < 0) return bad("n_profile must be >= 0");
+    if (p.n_profile > 0 && !p.profile) return bad("profile is NULL but n_profile > 0");
+    if (p.n_profile >= 2 && !(p.profile_rmax > 0)) return bad("profile_rmax must be > 0");
+    for (int i = 0; i < p.n_profile; ++i)
+        if (!(p.profile[i] >= 0) || !std::isfinite(p.profile[i])) return bad("profile values must be finite and >= 0");
+    if (!(p.alpha >= 0) || !std::isfinite(p.alpha)) return bad("alpha must be >= 0");
+    if (!(p.sigma_r > 0) || !(p.sigma_z > 0)) return bad("sigma_r and sigma_z must be > 0");
+    if (!std::isfinite(p.z0)) return bad("z0 must be finite");
+    if (!(p.n_floor >= 0)) return bad("n_floor must be >= 0");
+    return PWFA_OK;
+}
+
+int check_instance(pwfa_lbm* h, int32_t i) {
+    if (!h) return fail(PWFA_ERR_PARAM, "null handle");
+    if (i < 0 || i >= (int32_t)h->inst.size()) return fail(PWFA_ERR_PARAM, "instance index out of range");
+    return PWFA_OK;
+}
+
+StepArgs make_args(const Instance& in) {
+    StepArgs a{};
+    a.g = in.g;
+    a.fin = in.f[in.fcur];
+    a.fout = in.f[1 - in.fcur];
+    const int bc = in.bcur, bn = 1 - in.bcur;
+    for (int c = 0; c < 3; ++c) {
+        a.E[c] = in.E[c];
+        a.Eout[c] = in.E[c];
+        a.Bc[c] = in.B[bc][c];
+        a.Bn[c] = in.B[bn][c];
+        a.J[c] = in.J[c];
+    }
+    const pwfa_lbm_params& p = in.p;
+    a.omega = (float)(1.0 / p.tau);
+    a.lat = (float)(p.dt / p.dx);
+    a.dt = (float)p.dt;
+    a.cdt = (float)(p.dt / p.dx);
+    a.n_floor = (float)p.n_floor;
+    a.n0 = (float)p.n0;
+    a.couple = p.couple;
+    a.alpha = (float)p.alpha;
+    a.inv2sr2 = (float)(1.0 / (2.0 * p.sigma_r * p.sigma_r));
+    a.inv2sz2 = (float)(1.0 / (2.0 * p.sigma_z * p.sigma_z));
+    a.zc = (float)(p.z0 + (double)(in.steps + 1) * p.dt);  // driver centre at t_{n+1}
+    a.dx = (float)p.dx;
+    return a;
+}
+
+bool is_device_ptr(const void* ptr) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+int ensure_staging(pwfa_lbm* h, size_t bytes) {
+    if (h->staging_bytes >= bytes) return PWFA_OK;
+    if (h->staging) cudaFree(h->staging);
+    h->staging = nullptr;
+    h->staging_bytes = 0;
+    if (cudaMalloc(&h->staging, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PWFA_ERR_ALLOC, "cudaMalloc of the staging buffer failed");
+    }
+    h->staging_bytes = bytes;
+    return PWFA_OK;
+}
+
+void free_instance(Instance& in) {
+    if (in.arena) cudaFree(in.arena);
+    in.arena = nullptr;
+}
+
+int alloc_instance(Instance& in, cudaStream_t s) {
+    const int64_t N = in.g.N;
+    const size_t fbytes = align_up((size_t)N * kPop * storage_bytes(in.p.storage));
+    const size_t vbytes = align_up((size_t)N * sizeof(float));
+    const size_t pbytes = align_up(sizeof(double) * (in.profile.empty() ? 1 : in.profile.size()));
+    const size_t total = 2 * fbytes + 12 * vbytes + pbytes;  // f x2, E 3, B 2x3, J 3
+    if (cudaMalloc(&in.arena, total) != cudaSuccess) {
+        cudaGetLastError();
+        in.arena = nullptr;
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "cudaMalloc of %.3f GB for one instance failed", total / 1e9);
+        return fail(PWFA_ERR_ALLOC, buf);
+    }
+    char* base = static_cast<char*>(in.arena);
+    in.f[0] = base; base += fbytes;
+    in.f[1] = base; base += fbytes;
+    for (int c = 0; c < 3; ++c) { in.E[c] = (float*)base; base += vbytes; }
+    for (int t = 0; t < 2; ++t)
+        for (int c = 0; c < 3; ++c) { in.B[t][c] = (float*)base; base += vbytes; }
+    for (int c = 0; c < 3; ++c) { in.J[c] = (float*)base; base += vbytes; }
+    in.d_profile = (double*)base;
+    // Fields, currents and the second population buffer start at zero.
+    PWFA_CUDA(cudaMemsetAsync(in.f[1], 0, fbytes, s), "cudaMemsetAsync");
+    PWFA_CUDA(cudaMemsetAsync(in.E[0], 0, 12 * vbytes, s), "cudaMemsetAsync");
+    if (!in.profile.empty())
+        PWFA_CUDA(cudaMemcpyAsync(in.d_profile, in.profile.data(), sizeof(double) * in.profile.size(),
+                                  cudaMemcpyHostToDevice, s),
+                  "cudaMemcpyAsync profile");
+    PWFA_CUDA(launch_init(in.g, in.f[0], in.p.storage, (float)in.p.n0, in.d_profile, (int)in.profile.size(),
+                          in.p.profile_rmax, in.p.dx, s),
+              "init kernel");
+    return PWFA_OK;
+}
+
+constexpr size_t kEventPairs = 2048;
+
+// Fold the recorded event pairs into the per-kind accumulators.
+int fold_events(pwfa_lbm* h) {
+    if (h->pending_kind.empty()) return PWFA_OK;
+    PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    for (size_t k = 0; k < h->pending_kind.size(); ++k) {
+        float t = 0.0f;
+        PWFA_CUDA(cudaEventElapsedTime(&t, h->events[2 * k], h->events[2 * k + 1]), "cudaEventElapsedTime");
+        h->ms[h->pending_kind[k]] += t;
+    }
+    h->pending_kind.clear();
+    return PWFA_OK;
+}
+
+// Launch one kernel, bracketed by an event pair when profiling.
+template <class F>
+int timed_launch(pwfa_lbm* h, int kind, const char* what, F&& launch) {
+    if (h->profiling) {
+        if (h->pending_kind.size() == kEventPairs) {
+            int rc = fold_events(h);
+            if (rc) return rc;
+        }
+        const size_t k = h->pending_kind.size();
+        PWFA_CUDA(cudaEventRecord(h->events[2 * k], h->stream), "cudaEventRecord");
+        PWFA_CUDA(launch(), what);
+        PWFA_CUDA(cudaEventRecord(h->events[2 * k + 1], h->stream), "cudaEventRecord");
+        h->pending_kind.push_back(kind);
+    } else {
+        PWFA_CUDA(launch(), what);
+    }
+    ++h->launches[kind];
+    return PWFA_OK;
+}
+
+int step_instance(pwfa_lbm* h, Instance& in) {
+    cudaStream_t s = h->stream;
+    StepArgs a = make_args(in);
+    int rc;
+    if (in.p.couple) {
+        rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(a, s); });
+        if (rc) return rc;
+    }
+    rc = timed_launch(h, PWFA_KERNEL_FLUID, "fluid kernel",
+                      [&] { return launch_fluid(a, in.p.storage, in.p.collision, s); });
+    if (rc) return rc;
+    if (in.p.couple) {
+        rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere kernel", [&] { return launch_ampere(a, s); });
+        if (rc) return rc;
+    }
+    in.fcur = 1 - in.fcur;
+    if (in.p.couple) in.bcur = 1 - in.bcur;
+    ++in.steps;
+    return PWFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pwfa_lbm_last_error(void) { return g_err.c_str(); }
+
+int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances, void* cuda_stream, pwfa_lbm_t** out) {
+    if (!out) return fail(PWFA_ERR_PARAM, "out is NULL");
+    *out = nullptr;
+    if (!params || n_instances < 1) return fail(PWFA_ERR_PARAM, "params is NULL or n_instances < 1");
+    for (int i = 0; i < n_instances; ++i) {
+        int rc = validate(params[i], i);
+        if (rc) return rc;
+    }
+    pwfa_lbm* h = new (std::nothrow) pwfa_lbm();
+    if (!h) return fail(PWFA_ERR_ALLOC, "host allocation failed");
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->inst.resize(n_instances);
+    int rc = PWFA_OK;
+    for (int i = 0; i < n_instances && rc == PWFA_OK; ++i) {
+        Instance& in = h->inst[i];
+        in.p = params[i];
+        if (in.p.dt == 0) in.p.dt = 0.17628 * in.p.dx;
+        if (in.p.n_floor == 0) in.p.n_floor = 1e-6;
+        if (in.p.n_profile > 0) in.profile.assign(in.p.profile, in.p.profile + in.p.n_profile);
+        in.p.profile = nullptr;
+        in.g.nx = in.p.nx; in.g.ny = in.p.ny; in.g.nz = in.p.nz;
+        in.g.N = (int64_t)in.p.nx * in.p.ny * in.p.nz;
+        in.g.periodic = in.p.boundary == PWFA_PERIODIC;
+        rc = alloc_instance(in, h->stream);
+    }
+    if (rc == PWFA_OK) {
+        if (cudaMalloc(&h->d_partials, sizeof(double) * 8 * (kDiagBlocks + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics buffer failed");
+        } else {
+            h->d_diag = h->d_partials + 8 * kDiagBlocks;
+        }
+    }
+    if (rc == PWFA_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "create");
+    }
+    if (rc != PWFA_OK) {
+        std::string msg = g_err;
+        pwfa_lbm_destroy(h);
+        g_err = msg;
+        return rc;
+    }
+    *out = h;
+    return PWFA_OK;
+}
+
+int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps) {
+    if (!h) return fail(PWFA_ERR_PARAM, "null handle");
+    if (nsteps < 0) return fail(PWFA_ERR_PARAM, "nsteps must be >= 0");
+    for (int32_t s = 0; s < nsteps; ++s)
+        for (auto& in : h->inst) {
+            int rc = step_instance(h, in);
+            if (rc) return rc;
+        }
+    return PWFA_OK;
+}
+
+int pwfa_lbm_fields(pwfa_lbm_t* h, int32_t instance, uint32_t mask, float* out, int64_t out_elems,
+                    double* host_diag) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    Instance& in = h->inst[instance];
+    const uint32_t comp = mask & 0xFFFFu;
+    if (mask & 0x7FFF0000u) return fail(PWFA_ERR_PARAM, "unknown bits in mask");
+    const int nbits = __builtin_popcount(comp);
+    StepArgs a = make_args(in);
+    if (nbits > 0) {
+        if (!out) return fail(PWFA_ERR_PARAM, "out is NULL");
+        if (out_elems < (int64_t)nbits * in.g.N) return fail(PWFA_ERR_PARAM, "out_elems too small for the mask");
+        const bool dev = is_device_ptr(out);
+        float* dst = out;
+        const size_t bytes = sizeof(float) * (size_t)nbits * in.g.N;
+        if (!dev) {
+            rc = ensure_staging(h, bytes);
+            if (rc) return rc;
+            dst = static_cast<float*>(h->staging);
+        }
+        PWFA_CUDA(launch_export_fields(a, in.p.storage, mask, dst, h->stream), "export kernel");
+        if (!dev) {
+            PWFA_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync");
+            PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        }
+    }
+    if (host_diag) {
+        const double dx3 = in.p.dx * in.p.dx * in.p.dx;
+        PWFA_CUDA(launch_diag(a, in.p.storage, dx3, h->d_partials, h->d_diag, h->stream), "diag kernel");
+        PWFA_CUDA(cudaMemcpyAsync(host_diag, h->d_diag, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                  "cudaMemcpyAsync");
+        PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        if (host_diag[7] > 0 || host_diag[5] < 0) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "instance %d unstable: %g non-finite nodes, min n = %g", instance,
+                          host_diag[7], host_diag[5]);
+            return fail(PWFA_ERR_UNSTABLE, buf);
+        }
+    }
+    return PWFA_OK;
+}
+
+int pwfa_lbm_get_state(pwfa_lbm_t* h, int32_t instance, float* f, float* E, float* B) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    Instance& in = h->inst[instance];
+    const int64_t N = in.g.N;
+    StepArgs a = make_args(in);
+    if (f) {
+        const size_t bytes = sizeof(float) * (size_t)kPop * N;
+        const bool dev = is_device_ptr(f);
+        float* dst = f;
+        if (!dev) {
+            rc = ensure_staging(h, bytes);
+            if (rc) return rc;
+            dst = static_cast<float*>(h->staging);
+        }
+        PWFA_CUDA(launch_export_f(a, in.p.storage, dst, h->stream), "export kernel");
+        if (!dev) PWFA_CUDA(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync");
+    }
+    const size_t vb = sizeof(float) * (size_t)N;
+    for (int c = 0; c < 3; ++c) {
+        if (E) PWFA_CUDA(cudaMemcpyAsync(E + c * N, in.E[c], vb, cudaMemcpyDefault, h->stream), "cudaMemcpyAsync E");
+        if (B) PWFA_CUDA(cudaMemcpyAsync(B + c * N, in.B[in.bcur][c], vb, cudaMemcpyDefault, h->stream),
+                         "cudaMemcpyAsync B");
+    }
+    PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return PWFA_OK;
+}
+
+int pwfa_lbm_set_state(pwfa_lbm_t* h, int32_t instance, const float* f, const float* E, const float* B) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    Instance& in = h->inst[instance];
+    const int64_t N = in.g.N;
+    if (f) {
+        const size_t bytes = sizeof(float) * (size_t)kPop * N;
+        const float* src = f;
+        if (!is_device_ptr(f)) {
+            rc = ensure_staging(h, bytes);
+            if (rc) return rc;
+            PWFA_CUDA(cudaMemcpyAsync(h->staging, f, bytes, cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync");
+            src = static_cast<const float*>(h->staging);
+        }
+        PWFA_CUDA(launch_import_f(in.g, src, in.f[in.fcur], in.p.storage, (float)in.p.n0, h->stream),
+                  "import kernel");
+    }
+    const size_t vb = sizeof(float) * (size_t)N;
+    for (int c = 0; c < 3; ++c) {
+        if (E) PWFA_CUDA(cudaMemcpyAsync(in.E[c], E + c * N, vb, cudaMemcpyDefault, h->stream), "cudaMemcpyAsync E");
+        if (B) PWFA_CUDA(cudaMemcpyAsync(in.B[in.bcur][c], B + c * N, vb, cudaMemcpyDefault, h->stream),
+                         "cudaMemcpyAsync B");
+    }
+    PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return PWFA_OK;
+}
+
+int64_t pwfa_lbm_steps_done(pwfa_lbm_t* h, int32_t instance) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    return h->inst[instance].steps;
+}
+
+int pwfa_lbm_profile(pwfa_lbm_t* h, int32_t enable) {
+    if (!h) return fail(PWFA_ERR_PARAM, "null handle");
+    if (enable && h->events.empty()) {
+        h->events.resize(2 * kEventPairs);
+        for (auto& e : h->events) PWFA_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    }
+    if (!enable) {
+        int rc = fold_events(h);
+        if (rc) return rc;
+    }
+    h->profiling = enable != 0;
+    return PWFA_OK;
+}
+
+int pwfa_lbm_kernel_times(pwfa_lbm_t* h, double* ms, int64_t* launches) {
+    if (!h) return fail(PWFA_ERR_PARAM, "null handle");
+    int rc = fold_events(h);
+    if (rc) return rc;
+    PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    for (int k = 0; k < PWFA_KERNEL_KINDS; ++k) {
+        if (ms) ms[k] = h->ms[k];
+        if (launches) launches[k] = h->launches[k];
+        h->ms[k] = 0;
+        h->launches[k] = 0;
+    }
+    return PWFA_OK;
+}
+
+int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream) {
+    if (!h) return fail(PWFA_ERR_PARAM, "null handle");
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return PWFA_OK;
+}
+
+int pwfa_lbm_destroy(pwfa_lbm_t* h) {
+    if (!h) return PWFA_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (auto& in : h->inst) free_instance(in);
+    if (h->d_partials) cudaFree(h->d_partials);
+    if (h->staging) cudaFree(h->staging);
+    for (auto& e : h->events) cudaEventDestroy(e);
+    delete h;
+    return PWFA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+// Set-up, state exchange and diagnostics kernels (not on the per-step path).
+#include "lbm_kernels.h"
+#include "lbm_node.cuh"
+
+namespace pwfa {
+
+namespace {
+
+constexpr int kBX = 32;
+constexpr int kBY = 4;
+
+__device__ __forceinline__ void node_xyz(const Grid& g, int64_t node, int& x, int& y, int& z) {
+    const int64_t sxy = (int64_t)g.nx * g.ny;
+    z = (int)(node / sxy);
+    const int64_t r = node - (int64_t)z * sxy;
+    y = (int)(r / g.nx);
+    x = (int)(r - (int64_t)y * g.nx);
+}
+
+// Radial multiplier: linear between r_j = j rmax/(np-1), last value beyond.
+__device__ double profile_at(const double* prof, int np, double rmax, double r) {
+    if (np <= 0) return 1.0;
+    if (np == 1 || r >= rmax) return prof[np - 1];
+    const double h = rmax / (np - 1);
+    const double t = r / h;
+    int j = (int)floor(t);
+    if (j >= np - 1) return prof[np - 1];
+    const double fr = t - j;
+    return (1.0 - fr) * prof[j] + fr * prof[j + 1];
+}
+
+// Stored array S with S_i(y) = f^0_i(y + xi_i): pulling it yields the plasma
+// at rest f^0 = w_i n0 prof(r) (lattice 0) and 0 (momentum lattices). Open
+// grids clamp y + xi_i to the interior (such entries are only pulled by
+// interior nodes, for which the clamp is the identity).
+template <int ST>
+__global__ void init_kernel(Grid g, typename Codec<ST>::T* f, float n0, const double* prof, int np,
+                            double rmax, double dx) {
+    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= g.N) return;
+    int x, y, z;
+    node_xyz(g, node, x, y, z);
+    const double xc = 0.5 * (g.nx - 1) * dx, yc = 0.5 * (g.ny - 1) * dx;
+#pragma unroll 1
+    for (int q = 0; q < kQ; ++q) {
+        int sx = x + xi_x(q), sy = y + xi_y(q);
+        if (g.periodic) { sx = wrapi(sx, g.nx); sy = wrapi(sy, g.ny); }
+        else { sx = min(max(sx, 1), g.nx - 2); sy = min(max(sy, 1), g.ny - 2); }
+        const double rx = sx * dx - xc, ry = sy * dx - yc;
+        const double n = (double)n0 * profile_at(prof, np, rmax, sqrt(rx * rx + ry * ry));
+        Codec<ST>::store(f + (int64_t)q * g.N + node, (float)(wq(q) * n), wq(q) * n0);
+        for (int l = 1; l < kL; ++l) Codec<ST>::store(f + (int64_t)(l * kQ + q) * g.N + node, 0.0f, 0.0f);
+    }
+}
+
+// f^n at every node (boundary nodes: f^eq of the clamped interior node).
+template <int ST, bool PER>
+__global__ void __launch_bounds__(kBX * kBY) export_f_kernel(const StepArgs a, float* out) {
+    using T = typename Codec<ST>::T;
+    const Grid& g = a.g;
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    const int y = blockIdx.y * kBY + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const int64_t node = ((int64_t)z * g.ny + y) * g.nx + x;
+    float f[kL][kQ];
+    bool bnd;
+    gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+    if (!PER && bnd) {
+        float A[kL], nn, beta[3], phi[kQ];
+        node_moments(f, a.n_floor, A, nn, beta);
+        const float u[3] = {beta[0] * a.lat, beta[1] * a.lat, beta[2] * a.lat};
+        eq_factors(u, phi);
+        for (int l = 0; l < kL; ++l)
+            for (int q = 0; q < kQ; ++q) f[l][q] = A[l] * phi[q];
+    }
+#pragma unroll
+    for (int l = 0; l < kL; ++l)
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) out[(int64_t)(l * kQ + q) * g.N + node] = f[l][q];
+}
+
+// Inverse of the pull: S_i(y) = f^n_i(y + xi_i).
+template <int ST>
+__global__ void import_f_kernel(Grid g, const float* in, typename Codec<ST>::T* f, float n0) {
+    const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= g.N) return;
+    int x, y, z;
+    node_xyz(g, node, x, y, z);
+#pragma unroll 1
+    for (int q = 0; q < kQ; ++q) {
+        int sx = x + xi_x(q), sy = y + xi_y(q), sz = z + xi_z(q);
+        if (g.periodic) { sx = wrapi(sx, g.nx); sy = wrapi(sy, g.ny); sz = wrapi(sz, g.nz); }
+        else { sx = min(max(sx, 0), g.nx - 1); sy = min(max(sy, 0), g.ny - 1); sz = min(max(sz, 0), g.nz - 1); }
+        const int64_t src = ((int64_t)sz * g.ny + sy) * g.nx + sx;
+        for (int l = 0; l < kL; ++l)
+            Codec<ST>::store(f + (int64_t)(l * kQ + q) * g.N + node, in[(int64_t)(l * kQ + q) * g.N + src],
+                             l == 0 ? wq(q) * n0 : 0.0f);
+    }
+}
+
+template <int ST, bool PER>
+__global__ void __launch_bounds__(kBX * kBY) export_fields_kernel(const StepArgs a, unsigned mask, float* out) {
+    using T = typename Codec<ST>::T;
+    const Grid& g = a.g;
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    const int y = blockIdx.y * kBY + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const int64_t node = ((int64_t)z * g.ny + y) * g.nx + x;
+    float vals[16];
+    if (mask & 0xE00Fu) {
+        float f[kL][kQ];
+        bool bnd;
+        gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+        float A[kL], nn, beta[3];
+        node_moments(f, a.n_floor, A, nn, beta);
+        vals[0] = A[0];
+        vals[1] = beta[0]; vals[2] = beta[1]; vals[3] = beta[2];
+        vals[13] = A[1]; vals[14] = A[2]; vals[15] = A[3];
+    }
+    const bool raw = (mask >> 31) & 1u;
+    if (mask & 0x70u) {
+        if (raw) { for (int c = 0; c < 3; ++c) vals[4 + c] = a.E[c][node]; }
+        else { float e[3]; node_E<PER>(g, a.E, x, y, z, e); for (int c = 0; c < 3; ++c) vals[4 + c] = e[c]; }
+    }
+    if (mask & 0x380u) {
+        if (raw) { for (int c = 0; c < 3; ++c) vals[7 + c] = a.Bc[c][node]; }
+        else { float b[3]; node_B_sum<PER>(g, a.Bc, x, y, z, b); for (int c = 0; c < 3; ++c) vals[7 + c] = 0.25f * b[c]; }
+    }
+    if (mask & 0x1C00u) { for (int c = 0; c < 3; ++c) vals[10 + c] = a.J[c][node]; }
+    int slot = 0;
+    for (int bit = 0; bit < 16; ++bit)
+        if (mask & (1u << bit)) out[(int64_t)(slot++) * g.N + node] = vals[bit];
+}
+
+// ---------------------------------------------------------------- diagnostics
+struct Diag {
+    double sn, s1, s2, s3, en, mn, mb, bad;
+};
+
+__device__ __forceinline__ void diag_combine(Diag& a, const Diag& b) {
+    a.sn += b.sn; a.s1 += b.s1; a.s2 += b.s2; a.s3 += b.s3; a.en += b.en;
+    a.mn = fmin(a.mn, b.mn); a.mb = fmax(a.mb, b.mb); a.bad += b.bad;
+}
+
+__device__ __forceinline__ Diag diag_shfl(const Diag& d, int off) {
+    Diag r;
+    r.sn = __shfl_down_sync(0xffffffffu, d.sn, off);
+    r.s1 = __shfl_down_sync(0xffffffffu, d.s1, off);
+    r.s2 = __shfl_down_sync(0xffffffffu, d.s2, off);
+    r.s3 = __shfl_down_sync(0xffffffffu, d.s3, off);
+    r.en = __shfl_down_sync(0xffffffffu, d.en, off);
+    r.mn = __shfl_down_sync(0xffffffffu, d.mn, off);
+    r.mb = __shfl_down_sync(0xffffffffu, d.mb, off);
+    r.bad = __shfl_down_sync(0xffffffffu, d.bad, off);
+    return r;
+}
+
+// Block reduction (warp shuffles, then one warp over the warp results).
+__device__ void diag_block_reduce(Diag d, double* dst) {
+    __shared__ Diag sh[kDiagThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) diag_combine(d, diag_shfl(d, off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = d;
+    __syncthreads();
+    if (warp == 0) {
+        d = lane < kDiagThreads / 32 ? sh[lane] : Diag{0, 0, 0, 0, 0, 1e300, 0, 0};
+        for (int off = 16; off > 0; off >>= 1) diag_combine(d, diag_shfl(d, off));
+        if (lane == 0) {
+            dst[0] = d.sn; dst[1] = d.s1; dst[2] = d.s2; dst[3] = d.s3;
+            dst[4] = d.en; dst[5] = d.mn; dst[6] = d.mb; dst[7] = d.bad;
+        }
+    }
+}
+
+// Grid-stride over nodes; one partial record of 8 doubles per block.
+template <int ST, bool PER>
+__global__ void __launch_bounds__(kDiagThreads) diag_kernel(const StepArgs a, double dxcube, double* partials) {
+    using T = typename Codec<ST>::T;
+    const Grid& g = a.g;
+    Diag d{0, 0, 0, 0, 0, 1e300, 0, 0};
+    for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < g.N;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        node_xyz(g, node, x, y, z);
+        float f[kL][kQ];
+        bool bnd;
+        gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+        float A[kL], nn, beta[3];
+        node_moments(f, a.n_floor, A, nn, beta);
+        const bool fin = isfinite(A[0]) && isfinite(A[1]) && isfinite(A[2]) && isfinite(A[3]);
+        d.bad += fin ? 0.0 : 1.0;
+        d.sn += A[0]; d.s1 += A[1]; d.s2 += A[2]; d.s3 += A[3];
+        d.mn = fmin(d.mn, (double)A[0]);
+        d.mb = fmax(d.mb, sqrt((double)beta[0] * beta[0] + (double)beta[1] * beta[1] + (double)beta[2] * beta[2]));
+        double e2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double ev = a.E[c][node], bv = a.Bc[c][node];
+            e2 += ev * ev + bv * bv;
+        }
+        d.en += 0.5 * e2 * dxcube;
+    }
+    diag_block_reduce(d, partials + 8 * (int64_t)blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kDiagThreads) diag_finish_kernel(const double* partials, int nparts, double* out) {
+    Diag d{0, 0, 0, 0, 0, 1e300, 0, 0};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const double* p = partials + 8 * (int64_t)b;
+        diag_combine(d, Diag{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7]});
+    }
+    diag_block_reduce(d, out);
+}
+
+dim3 node_grid(const Grid& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz); }
+
+}  // namespace
+
+cudaError_t launch_init(const Grid& g, void* f, int storage, float n0, const double* d_profile, int n_profile,
+                        double profile_rmax, double dx, cudaStream_t s) {
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((g.N + threads - 1) / threads);
+    switch (storage) {
+        case 0: init_kernel<0><<<blocks, threads, 0, s>>>(g, (float*)f, n0, d_profile, n_profile, profile_rmax, dx); break;
+        case 1: init_kernel<1><<<blocks, threads, 0, s>>>(g, (__nv_bfloat16*)f, n0, d_profile, n_profile, profile_rmax, dx); break;
+        case 2: init_kernel<2><<<blocks, threads, 0, s>>>(g, (__half*)f, n0, d_profile, n_profile, profile_rmax, dx); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_f(const StepArgs& a, int storage, float* out, cudaStream_t s) {
+    const dim3 grid = node_grid(a.g), block(kBX, kBY, 1);
+    const bool per = a.g.periodic;
+    switch (storage) {
+        case 0: if (per) export_f_kernel<0, true><<<grid, block, 0, s>>>(a, out); else export_f_kernel<0, false><<<grid, block, 0, s>>>(a, out); break;
+        case 1: if (per) export_f_kernel<1, true><<<grid, block, 0, s>>>(a, out); else export_f_kernel<1, false><<<grid, block, 0, s>>>(a, out); break;
+        case 2: if (per) export_f_kernel<2, true><<<grid, block, 0, s>>>(a, out); else export_f_kernel<2, false><<<grid, block, 0, s>>>(a, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_f(const Grid& g, const float* in, void* f, int storage, float n0, cudaStream_t s) {
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((g.N + threads - 1) / threads);
+    switch (storage) {
+        case 0: import_f_kernel<0><<<blocks, threads, 0, s>>>(g, in, (float*)f, n0); break;
+        case 1: import_f_kernel<1><<<blocks, threads, 0, s>>>(g, in, (__nv_bfloat16*)f, n0); break;
+        case 2: import_f_kernel<2><<<blocks, threads, 0, s>>>(g, in, (__half*)f, n0); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_fields(const StepArgs& a, int storage, unsigned mask, float* out, cudaStream_t s) {
+    const dim3 grid = node_grid(a.g), block(kBX, kBY, 1);
+    const bool per = a.g.periodic;
+    switch (storage) {
+        case 0: if (per) export_fields_kernel<0, true><<<grid, block, 0, s>>>(a, mask, out); else export_fields_kernel<0, false><<<grid, block, 0, s>>>(a, mask, out); break;
+        case 1: if (per) export_fields_kernel<1, true><<<grid, block, 0, s>>>(a, mask, out); else export_fields_kernel<1, false><<<grid, block, 0, s>>>(a, mask, out); break;
+        case 2: if (per) export_fields_kernel<2, true><<<grid, block, 0, s>>>(a, mask, out); else export_fields_kernel<2, false><<<grid, block, 0, s>>>(a, mask, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const StepArgs& a, int storage, double dxcube, double* partials, double* out, cudaStream_t s) {
+    const int64_t need = (a.g.N + kDiagThreads - 1) / kDiagThreads;
+    const int blocks = (int)(need < kDiagBlocks ? need : kDiagBlocks);
+    const bool per = a.g.periodic;
+    switch (storage) {
+        case 0: if (per) diag_kernel<0, true><<<blocks, kDiagThreads, 0, s>>>(a, dxcube, partials); else diag_kernel<0, false><<<blocks, kDiagThreads, 0, s>>>(a, dxcube, partials); break;
+        case 1: if (per) diag_kernel<1, true><<<blocks, kDiagThreads, 0, s>>>(a, dxcube, partials); else diag_kernel<1, false><<<blocks, kDiagThreads, 0, s>>>(a, dxcube, partials); break;
+        case 2: if (per) diag_kernel<2, true><<<blocks, kDiagThreads, 0, s>>>(a, dxcube, partials); else diag_kernel<2, false><<<blocks, kDiagThreads, 0, s>>>(a, dxcube, partials); break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_finish_kernel<<<1, kDiagThreads, 0, s>>>(partials, blocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pwfa

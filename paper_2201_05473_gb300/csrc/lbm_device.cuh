@@ -1,0 +1,121 @@
+// Device-side building blocks of the GB300 LBM plasma-wakefield step.
+//
+// D3Q19 velocity set (Sec. III uses D2Q9; the 3D analogue keeps the same
+// construction: rest particle, nearest neighbours, diagonals), storage codecs
+// for the populations, and the argument blocks passed to every kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace pwfa {
+
+constexpr int kQ = 19;   // velocities per lattice
+constexpr int kL = 4;    // lattices: n, n p_x, n p_y, n p_z (Eq. 4)
+constexpr int kPop = kQ * kL;
+
+// Canonical D3Q19 order: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 the edge
+// diagonals (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1)
+// (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1). Opposites are (2m-1, 2m).
+__host__ __device__ __forceinline__ constexpr int xi_x(int q) {
+    return (q == 1 || q == 7 || q == 9 || q == 11 || q == 13) ? 1
+         : (q == 2 || q == 8 || q == 10 || q == 12 || q == 14) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int xi_y(int q) {
+    return (q == 3 || q == 7 || q == 10 || q == 15 || q == 17) ? 1
+         : (q == 4 || q == 8 || q == 9 || q == 16 || q == 18) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int xi_z(int q) {
+    return (q == 5 || q == 11 || q == 14 || q == 15 || q == 18) ? 1
+         : (q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0;
+}
+// Lattice weights: 1/3 rest, 1/18 axis, 1/36 diagonal (c_s^2 = 1/3).
+__host__ __device__ __forceinline__ constexpr float wq(int q) {
+    return q == 0 ? (1.0f / 3.0f) : (q <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
+}
+
+// ------------------------------------------------------------ storage codecs
+// FP32 stores f itself. BF16/FP16 store the deviation from the plasma at rest
+// (w_i n0 for lattice 0, 0 for the momentum lattices) so that the 8/11-bit
+// mantissa resolves the perturbation rather than the background.
+template <int ST> struct Codec;
+
+template <> struct Codec<0> {
+    using T = float;
+    static __device__ __forceinline__ float load(const T* p, float) { return __ldg(p); }
+    static __device__ __forceinline__ void store(T* p, float v, float) { __stcs(p, v); }
+};
+template <> struct Codec<1> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float load(const T* p, float base) {
+        return __bfloat162float(__ldg(p)) + base;
+    }
+    static __device__ __forceinline__ void store(T* p, float v, float base) {
+        *p = __float2bfloat16_rn(v - base);
+    }
+};
+template <> struct Codec<2> {
+    using T = __half;
+    static __device__ __forceinline__ float load(const T* p, float base) {
+        return __half2float(__ldg(p)) + base;
+    }
+    static __device__ __forceinline__ void store(T* p, float v, float base) {
+        *p = __float2half_rn(v - base);
+    }
+};
+
+// ------------------------------------------------------------ kernel args
+struct Grid {
+    int nx, ny, nz;
+    int64_t N;        // nx * ny * nz
+    int periodic;     // 1: every axis wraps; 0: open (Eq. 14) + conducting walls
+};
+
+// One instance's device state as the step kernels see it.
+struct StepArgs {
+    Grid g;
+    const void* fin;      // stored post-collision populations, 76 planes of N
+    void* fout;
+    const float* E[3];    // Yee E at t_{n+1/2}
+    const float* Bc[3];   // Yee B at t_n
+    float* Bn[3];         // Yee B at t_{n+1} (written by Faraday)
+    float* Eout[3];       // E updated in place by Ampere
+    float* J[3];          // node current -n beta(p*) of the step
+    float omega;          // 1 / tau
+    float lat;            // dt / dx: physical velocity -> lattice units
+    float dt;
+    float cdt;            // dt / dx for the curls
+    float n_floor;
+    float n0;             // background (deviation storage base)
+    int couple;
+    // driver: J_b,z = -alpha exp(-r^2/(2 sr^2) - (z - zc)^2/(2 sz^2)) at t_{n+1}
+    float alpha, inv2sr2, inv2sz2, zc, dx;
+};
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+// Node index of the source of pull q at node (x,y,z); assumes that for open
+// grids (x,y,z) is an interior node so the source lies inside the grid.
+__device__ __forceinline__ int64_t pull_src(const Grid& g, int x, int y, int z, int q) {
+    int sx = x - xi_x(q), sy = y - xi_y(q), sz = z - xi_z(q);
+    if (g.periodic) { sx = wrapi(sx, g.nx); sy = wrapi(sy, g.ny); sz = wrapi(sz, g.nz); }
+    return ((int64_t)sz * g.ny + sy) * g.nx + sx;
+}
+
+// Value of a Yee array at integer index (i,j,k) with i,j,k >= -1: wraps on
+// periodic grids, zero below the grid otherwise (indices above the grid are
+// never requested by the averages).
+__device__ __forceinline__ float yee_at(const Grid& g, const float* a, int i, int j, int k) {
+    if (g.periodic) {
+        i = wrapi(i, g.nx); j = wrapi(j, g.ny); k = wrapi(k, g.nz);
+    } else if (i < 0 || j < 0 || k < 0) {
+        return 0.0f;
+    }
+    return __ldg(a + ((int64_t)k * g.ny + j) * g.nx + i);
+}
+
+}  // namespace pwfa

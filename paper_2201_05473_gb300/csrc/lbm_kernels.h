@@ -1,0 +1,42 @@
+// Host-side launchers of the LBM plasma-wakefield kernels (internal to the
+// library; the public interface is include/pwfa_lbm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace pwfa {
+
+// Fused fluid step: pull streaming (Eq. 6), moments, Lorentz source (Eqs. 4,
+// 10), collision (Eq. 7 or regularized), Eq. 14 boundary nodes, node current.
+cudaError_t launch_fluid(const StepArgs& a, int storage, int collision, cudaStream_t s);
+
+// Faraday, dB/dt = -curl E: Bn = Bc - dt curl_h E (Yee, Eq. 5).
+cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s);
+
+// Ampere, dE/dt = curl B - J: E += dt (curl_h Bn - J_edge - J_b(t_{n+1})).
+cudaError_t launch_ampere(const StepArgs& a, cudaStream_t s);
+
+// Initial condition: stored populations whose pull gives the plasma at rest,
+// f = w_i n0 prof(r) (lattice 0), 0 (momentum lattices).
+cudaError_t launch_init(const Grid& g, void* f, int storage, float n0, const double* d_profile,
+                        int n_profile, double profile_rmax, double dx, cudaStream_t s);
+
+// Export the pre-collision populations f^n as FP32 [4][19][N].
+cudaError_t launch_export_f(const StepArgs& a, int storage, float* out, cudaStream_t s);
+
+// Import FP32 pre-collision populations [4][19][N] into the stored layout.
+cudaError_t launch_import_f(const Grid& g, const float* in, void* f, int storage, float n0, cudaStream_t s);
+
+// Node fields selected by a PWFA_FIELD_* mask into out, one block of N per bit.
+cudaError_t launch_export_fields(const StepArgs& a, int storage, unsigned mask, float* out, cudaStream_t s);
+
+// FP64 diagnostics: partial sums per block into partials (nblocks x 8), then
+// reduced into out[8] (device).
+constexpr int kDiagBlocks = 1024;
+constexpr int kDiagThreads = 256;
+cudaError_t launch_diag(const StepArgs& a, int storage, double dxcube, double* partials, double* out,
+                        cudaStream_t s);
+
+}  // namespace pwfa

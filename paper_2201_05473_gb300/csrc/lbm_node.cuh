@@ -1,0 +1,103 @@
+// Per-node device functions shared by the step, export and diagnostics
+// kernels: pull gather (Eq. 6), moments (Eq. 8 first line + Eq. 2), the
+// shared equilibrium factors of Eq. 9 and the node-averaged Yee fields.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace pwfa {
+
+template <bool PER>
+__device__ __forceinline__ int64_t src_index(const Grid& g, int x, int y, int z, int q) {
+    int sx = x - xi_x(q), sy = y - xi_y(q), sz = z - xi_z(q);
+    if (PER) { sx = wrapi(sx, g.nx); sy = wrapi(sy, g.ny); sz = wrapi(sz, g.nz); }
+    return ((int64_t)sz * g.ny + sy) * g.nx + sx;
+}
+
+// Pull the 76 populations f^n(x) = f*(x - xi_i) of node (x,y,z). Open grids
+// gather at the clamped interior node instead and flag the node as a boundary
+// node: its state is then f^eq of those moments (Eq. 14).
+template <int ST, bool PER>
+__device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::T* __restrict__ fin,
+                                       float n0, int x, int y, int z, float f[kL][kQ], bool& bnd) {
+    int xs = x, ys = y, zs = z;
+    bnd = false;
+    if (!PER) {
+        xs = min(max(x, 1), g.nx - 2);
+        ys = min(max(y, 1), g.ny - 2);
+        zs = min(max(z, 1), g.nz - 2);
+        bnd = (xs != x) | (ys != y) | (zs != z);
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        const int64_t src = src_index<PER>(g, xs, ys, zs, q);
+#pragma unroll
+        for (int l = 0; l < kL; ++l)
+            f[l][q] = Codec<ST>::load(fin + (int64_t)(l * kQ + q) * g.N + src, l == 0 ? wq(q) * n0 : 0.0f);
+    }
+}
+
+// Lattice sums A_l, the floored density and beta = p / sqrt(1 + p^2),
+// p = A_{1..3} / max(n, n_floor).
+__device__ __forceinline__ void node_moments(const float f[kL][kQ], float n_floor, float A[kL],
+                                             float& nn, float beta[3]) {
+#pragma unroll
+    for (int l = 0; l < kL; ++l) {
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) s += f[l][q];
+        A[l] = s;
+    }
+    nn = A[0] > n_floor ? A[0] : n_floor;
+    const float p0 = A[1] / nn, p1 = A[2] / nn, p2 = A[3] / nn;
+    const float gam = sqrtf(1.0f + p0 * p0 + p1 * p1 + p2 * p2);
+    beta[0] = p0 / gam;
+    beta[1] = p1 / gam;
+    beta[2] = p2 / gam;
+}
+
+// phi_i = w_i (1 + 3 xi.u + 4.5 (xi.u)^2 - 1.5 u.u): f^eq_{l,i} = A_l phi_i,
+// shared by the four lattices (one advecting velocity, Eq. 4).
+__device__ __forceinline__ void eq_factors(const float u[3], float phi[kQ]) {
+    const float base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        const float xu = (float)xi_x(q) * u[0] + (float)xi_y(q) * u[1] + (float)xi_z(q) * u[2];
+        phi[q] = wq(q) * (base + 3.0f * xu + 4.5f * xu * xu);
+    }
+}
+
+// E at node (x,y,z): mean of its two edges per component. B: mean over the
+// four adjacent faces of the two time levels Bc (t_n) and Bn (t_{n+1}).
+template <bool PER>
+__device__ __forceinline__ float yat(const Grid& g, const float* a, int i, int j, int k) {
+    if (PER) {
+        i = wrapi(i, g.nx); j = wrapi(j, g.ny); k = wrapi(k, g.nz);
+    } else if (i < 0 || j < 0 || k < 0) {
+        return 0.0f;
+    }
+    return __ldg(a + ((int64_t)k * g.ny + j) * g.nx + i);
+}
+
+template <bool PER>
+__device__ __forceinline__ void node_E(const Grid& g, const float* const E[3], int x, int y, int z, float e[3]) {
+    e[0] = 0.5f * (yat<PER>(g, E[0], x - 1, y, z) + yat<PER>(g, E[0], x, y, z));
+    e[1] = 0.5f * (yat<PER>(g, E[1], x, y - 1, z) + yat<PER>(g, E[1], x, y, z));
+    e[2] = 0.5f * (yat<PER>(g, E[2], x, y, z - 1) + yat<PER>(g, E[2], x, y, z));
+}
+
+template <bool PER>
+__device__ __forceinline__ float face4(const Grid& g, const float* a, int x0, int y0, int z0,
+                                       int x1, int y1, int z1, int x2, int y2, int z2) {
+    return yat<PER>(g, a, x0, y0, z0) + yat<PER>(g, a, x1, y1, z1) + yat<PER>(g, a, x2, y2, z2);
+}
+
+// Average of the four faces around the node for one B array.
+template <bool PER>
+__device__ __forceinline__ void node_B_sum(const Grid& g, const float* const B[3], int x, int y, int z, float b[3]) {
+    b[0] = yat<PER>(g, B[0], x, y, z) + face4<PER>(g, B[0], x, y - 1, z, x, y, z - 1, x, y - 1, z - 1);
+    b[1] = yat<PER>(g, B[1], x, y, z) + face4<PER>(g, B[1], x - 1, y, z, x, y, z - 1, x - 1, y, z - 1);
+    b[2] = yat<PER>(g, B[2], x, y, z) + face4<PER>(g, B[2], x - 1, y, z, x, y - 1, z, x - 1, y - 1, z);
+}
+
+}  // namespace pwfa

@@ -1,0 +1,245 @@
+"""ctypes binding of the C ABI in ``include/pwfa_lbm.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``libpwfa_lbm.so``. PyTorch supplies device memory for exported arrays and
+the CUDA stream. There is no CPU fallback: loading fails loudly if the library
+is missing or cannot be built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpwfa_lbm.so")
+
+PWFA_OK = 0
+ERRORS = {-1: "PWFA_ERR_PARAM", -2: "PWFA_ERR_CUDA", -3: "PWFA_ERR_UNSTABLE",
+          -4: "PWFA_ERR_TIMEOUT", -5: "PWFA_ERR_ALLOC", -6: "PWFA_ERR_STATE"}
+
+FIELD_N = 1 << 0
+FIELD_UX, FIELD_UY, FIELD_UZ = 1 << 1, 1 << 2, 1 << 3
+FIELD_EX, FIELD_EY, FIELD_EZ = 1 << 4, 1 << 5, 1 << 6
+FIELD_BX, FIELD_BY, FIELD_BZ = 1 << 7, 1 << 8, 1 << 9
+FIELD_JX, FIELD_JY, FIELD_JZ = 1 << 10, 1 << 11, 1 << 12
+FIELD_PX, FIELD_PY, FIELD_PZ = 1 << 13, 1 << 14, 1 << 15
+RAW_YEE = 1 << 31
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``pwfa_lbm_params``."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
+        ("collision", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("boundary", ctypes.c_int32), ("couple", ctypes.c_int32),
+        ("n0", ctypes.c_double),
+        ("profile", ctypes.POINTER(ctypes.c_double)), ("n_profile", ctypes.c_int32),
+        ("profile_rmax", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("sigma_r", ctypes.c_double), ("sigma_z", ctypes.c_double),
+        ("z0", ctypes.c_double), ("n_floor", ctypes.c_double),
+    ]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_state",
+           "pwfa_lbm_set_state", "pwfa_lbm_steps_done", "pwfa_lbm_set_stream",
+           "pwfa_lbm_destroy", "pwfa_lbm_last_error", "pwfa_lbm_profile", "pwfa_lbm_kernel_times")
+
+
+def load(build: bool = True):
+    """Load ``libpwfa_lbm.so`` (building it with nvcc first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build:
+            from .build import build as _build
+            _build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing; run paper_2201_05473_gb300.build")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        fp, dp = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
+        lib.pwfa_lbm_create.argtypes = [ctypes.POINTER(Params), i32, vp, ctypes.POINTER(vp)]
+        lib.pwfa_lbm_step.argtypes = [vp, i32]
+        lib.pwfa_lbm_fields.argtypes = [vp, i32, ctypes.c_uint32, vp, i64, dp]
+        lib.pwfa_lbm_get_state.argtypes = [vp, i32, vp, vp, vp]
+        lib.pwfa_lbm_set_state.argtypes = [vp, i32, vp, vp, vp]
+        lib.pwfa_lbm_steps_done.argtypes = [vp, i32]
+        lib.pwfa_lbm_steps_done.restype = i64
+        lib.pwfa_lbm_set_stream.argtypes = [vp, vp]
+        lib.pwfa_lbm_destroy.argtypes = [vp]
+        lib.pwfa_lbm_profile.argtypes = [vp, i32]
+        lib.pwfa_lbm_kernel_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
+        lib.pwfa_lbm_last_error.restype = ctypes.c_char_p
+        for name in ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_state",
+                     "pwfa_lbm_set_state", "pwfa_lbm_set_stream", "pwfa_lbm_destroy",
+                     "pwfa_lbm_profile", "pwfa_lbm_kernel_times"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != PWFA_OK:
+        raise LBMError(rc, _lib.pwfa_lbm_last_error().decode())
+
+
+def params_of(w: W.Workload):
+    """Fill a ``Params`` from a workload; returns (params, keep-alive arrays)."""
+    keep = []
+    p = Params()
+    p.nx, p.ny, p.nz = w.nx, w.ny, w.nz
+    p.dx, p.dt, p.tau = w.dx, w.dt, w.tau
+    p.collision, p.storage, p.boundary, p.couple = w.collision, w.storage, w.boundary, w.couple
+    p.n0 = w.n0
+    if w.profile is not None:
+        prof = np.ascontiguousarray(w.profile, dtype=np.float64)
+        keep.append(prof)
+        p.profile = prof.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.n_profile = len(prof)
+        p.profile_rmax = w.profile_rmax
+    p.alpha, p.sigma_r, p.sigma_z, p.z0 = w.alpha, w.sigma_r, w.sigma_z, w.z0
+    p.n_floor = w.n_floor
+    return p, keep
+
+
+def _ptr(t):
+    """Raw pointer of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return ctypes.c_void_p(t.ctypes.data)
+    assert t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Simulation:
+    """One or more instances advanced together through the C ABI."""
+
+    def __init__(self, works, stream=None):
+        import torch
+        self._torch = torch
+        self._lib = load()
+        if isinstance(works, W.Workload):
+            works = [works]
+        self.works = list(works)
+        arr = (Params * len(self.works))()
+        keep = []
+        for i, w in enumerate(self.works):
+            arr[i], k = params_of(w)
+            keep += k
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(self._lib.pwfa_lbm_create(arr, len(self.works), ctypes.c_void_p(stream.cuda_stream),
+                                         ctypes.byref(h)))
+        self._h = h
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pwfa_lbm_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- stepping
+    def step(self, n: int = 1):
+        _check(self._lib.pwfa_lbm_step(self._h, int(n)))
+
+    def steps_done(self, instance: int = 0) -> int:
+        r = self._lib.pwfa_lbm_steps_done(self._h, instance)
+        if r < 0:
+            _check(int(r))
+        return int(r)
+
+    def shape(self, instance: int = 0):
+        w = self.works[instance]
+        return (w.nz, w.ny, w.nx)
+
+    # -- exports
+    def fields(self, mask: int, instance: int = 0, out=None):
+        """Selected fields as a [n_bits][z][y][x] float32 tensor (device unless
+        ``out`` is a host tensor/array)."""
+        torch = self._torch
+        nb = bin(mask & 0xFFFF).count("1")
+        shp = (nb,) + self.shape(instance)
+        if out is None:
+            out = torch.empty(shp, dtype=torch.float32, device="cuda")
+        n_el = int(np.prod(shp))
+        _check(self._lib.pwfa_lbm_fields(self._h, instance, mask, _ptr(out), n_el, None))
+        return out
+
+    def diag(self, instance: int = 0, check: bool = True) -> np.ndarray:
+        d = np.zeros(8, dtype=np.float64)
+        rc = self._lib.pwfa_lbm_fields(self._h, instance, 0, None, 0,
+                                       d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if check or rc != -3:
+            _check(rc)
+        return d
+
+    def diag_into(self, host_buf, instance: int = 0):
+        """FP64 diagnostics into a caller-owned host float64 tensor/array of 8."""
+        ptr = _ptr(host_buf)
+        rc = self._lib.pwfa_lbm_fields(self._h, instance, 0, None, 0,
+                                       ctypes.cast(ptr, ctypes.POINTER(ctypes.c_double)))
+        _check(rc)
+
+    def profile(self, enable: bool = True):
+        _check(self._lib.pwfa_lbm_profile(self._h, 1 if enable else 0))
+
+    KERNELS = ("faraday", "fluid", "ampere")
+
+    def kernel_times(self):
+        """(ms, launches) per kernel kind since the previous call."""
+        ms = np.zeros(3, dtype=np.float64)
+        n = np.zeros(3, dtype=np.int64)
+        _check(self._lib.pwfa_lbm_kernel_times(
+            self._h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return dict(zip(self.KERNELS, ms)), dict(zip(self.KERNELS, n.tolist()))
+
+    def get_state(self, instance: int = 0, device: bool = True):
+        torch = self._torch
+        shp = self.shape(instance)
+        kw = dict(dtype=torch.float32, device="cuda" if device else "cpu")
+        f = torch.empty((4, 19) + shp, **kw)
+        E = torch.empty((3,) + shp, **kw)
+        B = torch.empty((3,) + shp, **kw)
+        _check(self._lib.pwfa_lbm_get_state(self._h, instance, _ptr(f), _ptr(E), _ptr(B)))
+        return f, E, B
+
+    def set_state(self, f=None, E=None, B=None, instance: int = 0):
+        torch = self._torch
+        conv = lambda a: None if a is None else (
+            a.contiguous().to(torch.float32) if isinstance(a, torch.Tensor)
+            else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)))
+        f, E, B = conv(f), conv(E), conv(B)
+        _check(self._lib.pwfa_lbm_set_state(self._h, instance, _ptr(f), _ptr(E), _ptr(B)))

@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element.
+
+Tolerance: FP32 compute and storage against FP64, relative L2 <= 1e-5 on n,
+beta and E_z after 200 steps of the 64x32x32 linear-driver case; the same
+bound elsewhere unless stated. Integer streaming is bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_05473_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2201_05473_gb300 import lbm  # noqa: E402
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def make_oracle(w: W.Workload) -> oracle.Oracle:
+    oracle.build()
+    return oracle.Oracle(w.nx, w.ny, w.nz, w.dx, w.dt, w.tau, collision=w.collision, boundary=w.boundary,
+                         couple=w.couple, n0=w.n0, profile=w.profile, profile_rmax=w.profile_rmax,
+                         alpha=w.alpha, sigma_r=w.sigma_r, sigma_z=w.sigma_z, z0=w.z0, n_floor=w.n_floor)
+
+
+def gpu_moments(sim, instance=0):
+    m = lbm.FIELD_N | lbm.FIELD_UX | lbm.FIELD_UY | lbm.FIELD_UZ | lbm.FIELD_EZ | lbm.RAW_YEE
+    out = sim.fields(m, instance).cpu().numpy().astype(np.float64)
+    return {"n": out[0], "beta": out[1:4], "Ez": out[4]}
+
+
+def compare(o, sim, tol=TOL, instance=0):
+    g = gpu_moments(sim, instance)
+    m = o.moments()
+    E, _ = o.get_fields()
+    errs = {"n": rel(g["n"], m["n"]), "beta": rel(g["beta"], m["beta"]), "Ez": rel(g["Ez"], E[2])}
+    for k in ("x", "y", "z"):
+        i = "xyz".index(k)
+        errs["beta_" + k] = rel(g["beta"][i], m["beta"][i])
+    assert errs["n"] <= tol and errs["beta"] <= tol and errs["Ez"] <= tol, errs
+    return errs
+
+
+def test_parity_linear_driver_200_steps():
+    """64x32x32, dx 0.2, n_b/n0 = 0.1, sigma 0.5, BGK, open: rel-L2 <= 1e-5."""
+    w = W.parity_small()
+    o = make_oracle(w)
+    with lbm.Simulation(w) as sim:
+        for chunk in (50, 50, 100):
+            o.step(chunk)
+            sim.step(chunk)
+            errs = compare(o, sim)
+        assert sim.steps_done() == 200
+        print("parity 200 steps:", errs)
+        # the wake is really there
+        assert np.abs(gpu_moments(sim)["Ez"]).max() > 0.01
+
+
+def test_parity_regularized_ragged_tiles():
+    """Ragged grid (x spans two 32-wide tiles + tail, y a 4-row tail),
+    regularized collision, stronger driver."""
+    w = W.parity_small().replace(nx=37, ny=10, nz=26, collision=W.REGULARIZED, alpha=0.5,
+                                 sigma_r=0.6, sigma_z=0.6, z0=-1.0, tau=0.55)
+    o = make_oracle(w)
+    with lbm.Simulation(w) as sim:
+        o.step(120)
+        sim.step(120)
+        compare(o, sim)
+
+
+@pytest.mark.parametrize("collision", [W.BGK, W.REGULARIZED])
+def test_parity_periodic_random_state(collision):
+    """Periodic 11x6x9 from random populations and fields: full populations
+    and Yee fields after 30 steps."""
+    w = W.parity_small().replace(nx=9, ny=6, nz=11, collision=collision, boundary=W.PERIODIC, tau=0.7,
+                                 alpha=0.3, z0=1.0)
+    rng = np.random.default_rng(5)
+    f0 = W.random_populations((w.nz, w.ny, w.nx), seed=5)
+    E0 = 0.05 * rng.standard_normal((3, w.nz, w.ny, w.nx))
+    B0 = 0.05 * rng.standard_normal((3, w.nz, w.ny, w.nx))
+    o = make_oracle(w)
+    o.set_f(f0)
+    o.set_fields(E0, B0)
+    with lbm.Simulation(w) as sim:
+        sim.set_state(f0, E0, B0)
+        o.step(30)
+        sim.step(30)
+        f, E, B = sim.get_state()
+        Eo, Bo = o.get_fields()
+        assert rel(f.cpu().numpy(), o.get_f()) < TOL
+        assert rel(E.cpu().numpy(), Eo) < TOL
+        assert rel(B.cpu().numpy(), Bo) < TOL
+
+
+@pytest.mark.parametrize("shape", [(5, 3, 7), (4, 4, 40)])
+def test_streaming_bit_exact(shape):
+    """Collision off, periodic: integer populations move exactly (Eq. 6)."""
+    nz, ny, nx = shape
+    w = W.parity_small().replace(nx=nx, ny=ny, nz=nz, collision=W.STREAM_ONLY, boundary=W.PERIODIC, couple=0)
+    f0 = W.integer_populations(shape)
+    o = make_oracle(w)
+    o.set_f(f0)
+    with lbm.Simulation(w) as sim:
+        sim.set_state(f0)
+        for _ in range(3):
+            o.step(2)
+            sim.step(2)
+            f, _, _ = sim.get_state()
+            assert np.array_equal(f.cpu().numpy().astype(np.float64), o.get_f())
+
+
+def test_state_roundtrip_and_host_buffers():
+    w = W.parity_small().replace(nx=9, ny=6, nz=11, boundary=W.PERIODIC)
+    f0 = W.random_populations((w.nz, w.ny, w.nx), seed=9).astype(np.float32)
+    rng = np.random.default_rng(9)
+    E0 = rng.standard_normal((3, w.nz, w.ny, w.nx)).astype(np.float32)
+    B0 = rng.standard_normal((3, w.nz, w.ny, w.nx)).astype(np.float32)
+    with lbm.Simulation(w) as sim:
+        sim.set_state(f0, E0, B0)
+        f, E, B = sim.get_state(device=False)
+        assert np.array_equal(f.numpy(), f0)
+        assert np.array_equal(E.numpy(), E0) and np.array_equal(B.numpy(), B0)
+        sim.step(3)
+        dev = sim.fields(lbm.FIELD_N | lbm.FIELD_EZ).cpu()
+        host = torch.empty_like(dev)
+        sim.fields(lbm.FIELD_N | lbm.FIELD_EZ, out=host)
+        assert torch.equal(dev, host)
+
+
+def test_diagnostics_match_oracle():
+    w = W.parity_small()
+    o = make_oracle(w)
+    with lbm.Simulation(w) as sim:
+        o.step(60)
+        sim.step(60)
+        d = sim.diag()
+        do = o.diag()
+        assert abs(d[0] - do[0]) / do[0] < 1e-6
+        assert abs(d[3] - do[3]) / abs(do[3]) < 1e-4
+        assert abs(d[4] - do[4]) / do[4] < 1e-5
+        # min n and max |beta| are pointwise extremes: FP32 pointwise error is
+        # larger than the relative-L2 figure (a few ulp of n per step)
+        assert abs(d[5] - do[5]) < 1e-5 and abs(d[6] - do[6]) / do[6] < 1e-4
+        assert d[7] == 0
+
+
+def test_radial_profile_parity():
+    prof = np.linspace(1.0, 0.6, 8)
+    w = W.parity_small().replace(nz=32, profile=prof, profile_rmax=2.5)
+    o = make_oracle(w)
+    with lbm.Simulation(w) as sim:
+        n0 = gpu_moments(sim)["n"]
+        assert rel(n0, o.moments()["n"]) < 1e-6
+        o.step(80)
+        sim.step(80)
+        compare(o, sim)
+
+
+def test_minimum_grid_and_zero_steps():
+    w = W.parity_small().replace(nx=3, ny=3, nz=3, alpha=0.5, z0=0.0)
+    o = make_oracle(w)
+    with lbm.Simulation(w) as sim:
+        sim.step(0)
+        assert sim.steps_done() == 0
+        o.step(25)
+        sim.step(25)
+        g = gpu_moments(sim)
+        assert rel(g["n"], o.moments()["n"]) < TOL
+        assert rel(g["Ez"], o.get_fields()[0][2]) < TOL or np.abs(g["Ez"]).max() < 1e-12
+
+
+def test_multi_instance_handle():
+    """Two independent instances of different size in one handle."""
+    w1 = W.parity_small().replace(nz=32)
+    w2 = W.parity_small().replace(nx=16, ny=24, nz=40, alpha=0.3, collision=W.REGULARIZED)
+    o1, o2 = make_oracle(w1), make_oracle(w2)
+    with lbm.Simulation([w1, w2]) as sim:
+        sim.step(40)
+        o1.step(40)
+        o2.step(40)
+        compare(o1, sim, instance=0)
+        compare(o2, sim, instance=1)
+        with pytest.raises(lbm.LBMError):
+            sim.fields(lbm.FIELD_N, instance=2)
+
+
+def test_production_grid_properties():
+    """512x256x256 regularized, the benchmarked launch configuration: after a
+    few steps every moment is finite, the wake is mirror-symmetric in x and y,
+    and the FP64 diagnostics match a direct reduction of the exported n."""
+    w = W.production().replace(z0=-1.0)
+    with lbm.Simulation(w) as sim:
+        sim.step(100)
+        d = sim.diag()
+        assert d[7] == 0 and d[5] > 0
+        n = sim.fields(lbm.FIELD_N)[0]
+        assert abs(float(n.double().sum()) - d[0]) / d[0] < 1e-9
+        nmx = (n - n.flip(2)).abs().max().item()
+        nmy = (n - n.flip(1)).abs().max().item()
+        assert nmx < 1e-5 and nmy < 1e-5, (nmx, nmy)
