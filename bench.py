@@ -223,6 +223,8 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         sim = lbm.Simulation(w, stream=stream)
         sim.step(args.warmup)
+        sim.autotune(3)
+        launch_shape = sim.get_launch()
         sim.kernel_times()  # reset counters
         barrier()
         # ---- value: K steps, device-timed with CUDA events on the stream
@@ -284,7 +286,8 @@ def run_ours(args):
                    "driver": {"nb_over_n0": w.alpha, "sigma_r": w.sigma_r, "sigma_z": w.sigma_z},
                    "storage": args.storage,
                    "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * 76 * (4 if w.storage == W.F32 else 2) * N / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "fluid_block": list(launch_shape)},
         "pct_hbm_step": {"of_" + peak_kind: value * 1e9 * step_bytes / (peak * 1e9),
                          "of_nominal_8000": value * 1e9 * step_bytes / (NOMINAL_HBM_GBS * 1e9),
                          "bytes_per_node_step": step_bytes},

@@ -177,6 +177,17 @@ int pwfa_lbm_profile(pwfa_lbm_t* h, int32_t enable);
  * both accumulators are then reset. */
 int pwfa_lbm_kernel_times(pwfa_lbm_t* h, double* ms, int64_t* launches);
 
+/* Thread-block shape (bx * by threads, bx along x) of the fused fluid kernel
+ * for one instance. bx, by >= 1 and bx * by <= 256; PWFA_ERR_PARAM otherwise. */
+int pwfa_lbm_set_launch(pwfa_lbm_t* h, int32_t instance, int32_t bx, int32_t by);
+int pwfa_lbm_get_launch(pwfa_lbm_t* h, int32_t instance, int32_t* bx, int32_t* by);
+
+/* Autotune the fluid kernel's block shape of every instance: time reps
+ * launches (>= 1) of each candidate shape with CUDA events and keep the
+ * fastest. The kernel is re-run on the current state without advancing it,
+ * so the simulation state is unchanged. Synchronises the stream. */
+int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps);
+
 /* Re-target all later work of the handle to another cudaStream_t. */
 int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream);
 

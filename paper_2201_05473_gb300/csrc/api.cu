@@ -50,6 +50,7 @@ struct Instance {
     float* J[3] = {nullptr, nullptr, nullptr};
     double* d_profile = nullptr;
     int64_t steps = 0;
+    int bx = 64, by = 2;  // fluid kernel block shape (pwfa_lbm_autotune refines it)
 };
 
 }  // namespace
@@ -79,6 +80,8 @@ int validate(const pwfa_lbm_params& p, int idx) {
     };
     if (p.nx < 3 || p.ny < 3 || p.nz < 3) return bad("nx, ny, nz must be >= 3");
     if ((int64_t)p.nx * p.ny > (int64_t)1 << 30 || p.nz > 65535) return bad("grid too large");
+    // one lattice's 19 planes are addressed with 32-bit element offsets
+    if ((int64_t)p.nx * p.ny * p.nz * 19 >= ((int64_t)1 << 32)) return bad("grid too large (nodes * 19 >= 2^32)");
     if (!(p.dx > 0) || !std::isfinite(p.dx)) return bad("dx must be > 0");
     if (!(p.dt >= 0) || !std::isfinite(p.dt)) return bad("dt must be >= 0 (0 = default)");
     const double dt = p.dt > 0 ? p.dt : 0.17628 * p.dx;
@@ -133,6 +136,8 @@ StepArgs make_args(const Instance& in) {
     a.inv2sz2 = (float)(1.0 / (2.0 * p.sigma_z * p.sigma_z));
     a.zc = (float)(p.z0 + (double)(in.steps + 1) * p.dt);  // driver centre at t_{n+1}
     a.dx = (float)p.dx;
+    a.bx = in.bx;
+    a.by = in.by;
     return a;
 }
 
@@ -166,7 +171,10 @@ void free_instance(Instance& in) {
 int alloc_instance(Instance& in, cudaStream_t s) {
     const int64_t N = in.g.N;
     const size_t fbytes = align_up((size_t)N * kPop * storage_bytes(in.p.storage));
-    const size_t vbytes = align_up((size_t)N * sizeof(float));
+    // Each Yee/current array is preceded by one zero x-y plane: in open mode the
+    // node averages read index -1 / -nx / -nx*ny without bounds checks.
+    const size_t pad = align_up((size_t)in.g.nx * in.g.ny * sizeof(float));
+    const size_t vbytes = pad + align_up((size_t)N * sizeof(float));
     const size_t pbytes = align_up(sizeof(double) * (in.profile.empty() ? 1 : in.profile.size()));
     const size_t total = 2 * fbytes + 12 * vbytes + pbytes;  // f x2, E 3, B 2x3, J 3
     if (cudaMalloc(&in.arena, total) != cudaSuccess) {
@@ -179,14 +187,16 @@ int alloc_instance(Instance& in, cudaStream_t s) {
     char* base = static_cast<char*>(in.arena);
     in.f[0] = base; base += fbytes;
     in.f[1] = base; base += fbytes;
-    for (int c = 0; c < 3; ++c) { in.E[c] = (float*)base; base += vbytes; }
+    char* fields = base;
+    for (int c = 0; c < 3; ++c) { in.E[c] = (float*)(base + pad); base += vbytes; }
     for (int t = 0; t < 2; ++t)
-        for (int c = 0; c < 3; ++c) { in.B[t][c] = (float*)base; base += vbytes; }
-    for (int c = 0; c < 3; ++c) { in.J[c] = (float*)base; base += vbytes; }
+        for (int c = 0; c < 3; ++c) { in.B[t][c] = (float*)(base + pad); base += vbytes; }
+    for (int c = 0; c < 3; ++c) { in.J[c] = (float*)(base + pad); base += vbytes; }
     in.d_profile = (double*)base;
-    // Fields, currents and the second population buffer start at zero.
+    // Fields, currents, their guard planes and the second population buffer
+    // start at zero.
     PWFA_CUDA(cudaMemsetAsync(in.f[1], 0, fbytes, s), "cudaMemsetAsync");
-    PWFA_CUDA(cudaMemsetAsync(in.E[0], 0, 12 * vbytes, s), "cudaMemsetAsync");
+    PWFA_CUDA(cudaMemsetAsync(fields, 0, 12 * vbytes, s), "cudaMemsetAsync");
     if (!in.profile.empty())
         PWFA_CUDA(cudaMemcpyAsync(in.d_profile, in.profile.data(), sizeof(double) * in.profile.size(),
                                   cudaMemcpyHostToDevice, s),
@@ -410,6 +420,8 @@ int pwfa_lbm_set_state(pwfa_lbm_t* h, int32_t instance, const float* f, const fl
         if (B) PWFA_CUDA(cudaMemcpyAsync(in.B[in.bcur][c], B + c * N, vb, cudaMemcpyDefault, h->stream),
                          "cudaMemcpyAsync B");
     }
+    // Open grids: components on or outside the conducting walls are zero.
+    if ((E || B) && !in.g.periodic) PWFA_CUDA(launch_zero_walls(make_args(in), h->stream), "wall kernel");
     PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return PWFA_OK;
 }
@@ -446,6 +458,58 @@ int pwfa_lbm_kernel_times(pwfa_lbm_t* h, double* ms, int64_t* launches) {
         h->launches[k] = 0;
     }
     return PWFA_OK;
+}
+
+int pwfa_lbm_set_launch(pwfa_lbm_t* h, int32_t instance, int32_t bx, int32_t by) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    if (bx < 1 || by < 1 || bx * by > 256) return fail(PWFA_ERR_PARAM, "block shape must satisfy 1 <= bx*by <= 256");
+    h->inst[instance].bx = bx;
+    h->inst[instance].by = by;
+    return PWFA_OK;
+}
+
+int pwfa_lbm_get_launch(pwfa_lbm_t* h, int32_t instance, int32_t* bx, int32_t* by) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    if (bx) *bx = h->inst[instance].bx;
+    if (by) *by = h->inst[instance].by;
+    return PWFA_OK;
+}
+
+int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
+    if (!h) return fail(PWFA_ERR_PARAM, "null handle");
+    if (reps < 1) return fail(PWFA_ERR_PARAM, "reps must be >= 1");
+    static const int cand[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+    cudaEvent_t e0, e1;
+    PWFA_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    PWFA_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    int rc = PWFA_OK;
+    for (auto& in : h->inst) {
+        float best = 1e30f;
+        int bb[2] = {in.bx, in.by};
+        for (const auto& c : cand) {
+            if (c[0] > 2 * in.g.nx && c[0] > 32) continue;  // mostly idle lanes
+            in.bx = c[0];
+            in.by = c[1];
+            StepArgs a = make_args(in);
+            cudaError_t e = launch_fluid(a, in.p.storage, in.p.collision, h->stream);  // warm
+            if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_fluid(a, in.p.storage, in.p.collision, h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "autotune"); break; }
+            if (ms < best) { best = ms; bb[0] = c[0]; bb[1] = c[1]; }
+        }
+        in.bx = bb[0];
+        in.by = bb[1];
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream) {

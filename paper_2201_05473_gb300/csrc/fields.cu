@@ -94,7 +94,33 @@ __global__ void __launch_bounds__(kBX * kBY) ampere_kernel(const StepArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(kBX * kBY) zero_walls_kernel(const StepArgs a) {
+    const Grid& g = a.g;
+    const int i = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    if (!(i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2)) a.Eout[0][o] = 0.0f;
+    if (!(i >= 1 && i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2)) a.Eout[1][o] = 0.0f;
+    if (!(i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2)) a.Eout[2][o] = 0.0f;
+    float* Bc0 = const_cast<float*>(a.Bc[0]);
+    float* Bc1 = const_cast<float*>(a.Bc[1]);
+    float* Bc2 = const_cast<float*>(a.Bc[2]);
+    if (!(i >= 1 && i <= nx - 2 && j <= ny - 2 && k <= nz - 2)) Bc0[o] = 0.0f;
+    if (!(i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2)) Bc1[o] = 0.0f;
+    if (!(i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2)) Bc2[o] = 0.0f;
+}
+
 }  // namespace
+
+cudaError_t launch_zero_walls(const StepArgs& a, cudaStream_t s) {
+    dim3 block(kBX, kBY, 1);
+    dim3 grid((a.g.nx + kBX - 1) / kBX, (a.g.ny + kBY - 1) / kBY, a.g.nz);
+    zero_walls_kernel<<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s) {
     dim3 block(kBX, kBY, 1);

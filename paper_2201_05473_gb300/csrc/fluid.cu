@@ -21,18 +21,22 @@ namespace pwfa {
 
 namespace {
 
-constexpr int kBX = 32;
-constexpr int kBY = 4;
+#ifndef PWFA_FLUID_MAX_THREADS
+#define PWFA_FLUID_MAX_THREADS 256
+#endif
+#ifndef PWFA_FLUID_MIN_BLOCKS
+#define PWFA_FLUID_MIN_BLOCKS 2
+#endif
 
 template <int ST, int COLL, bool PER>
-__global__ void __launch_bounds__(kBX * kBY) fluid_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS) fluid_kernel(const StepArgs a) {
     using T = typename Codec<ST>::T;
     const Grid& g = a.g;
-    const int x = blockIdx.x * kBX + threadIdx.x;
-    const int y = blockIdx.y * kBY + threadIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const int64_t node = ((int64_t)z * g.ny + y) * g.nx + x;
+    const uint32_t node = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x;
 
     float f[kL][kQ];
     bool bnd;
@@ -42,7 +46,8 @@ __global__ void __launch_bounds__(kBX * kBY) fluid_kernel(const StepArgs a) {
     node_moments(f, a.n_floor, A, nn, beta);
     const float n = A[0];
 
-    // Lorentz source (Eq. 4): F_0 = 0, F_k = -n (E + beta x B)_k.
+    // Lorentz source (Eq. 4): F_0 = 0, F_k = -n (E + beta x B)_k, with B the
+    // mean of its two time levels.
     float F[3] = {0.0f, 0.0f, 0.0f};
     if (COLL != 2 && a.couple) {
         float e[3], bc[3], bn[3];
@@ -57,7 +62,9 @@ __global__ void __launch_bounds__(kBX * kBY) fluid_kernel(const StepArgs a) {
         F[2] = -n * (e[2] + beta[0] * b1 - beta[1] * b0);
     }
 
-    T* fout = static_cast<T*>(a.fout);
+    const uint32_t N = (uint32_t)g.N;
+    T* const fo0 = static_cast<T*>(a.fout);
+    T* const fo[kL] = {fo0, fo0 + (size_t)kQ * N, fo0 + (size_t)2 * kQ * N, fo0 + (size_t)3 * kQ * N};
     const float u[3] = {beta[0] * a.lat, beta[1] * a.lat, beta[2] * a.lat};
     float phi[kQ];
     eq_factors(u, phi);
@@ -68,43 +75,45 @@ __global__ void __launch_bounds__(kBX * kBY) fluid_kernel(const StepArgs a) {
 #pragma unroll
             for (int q = 0; q < kQ; ++q) f[l][q] = A[l] * phi[q];
     }
-    if (COLL == 2) {
-        // streaming only: f* = f
+    const float om = a.omega;
 #pragma unroll
-        for (int l = 0; l < kL; ++l)
+    for (int l = 0; l < kL; ++l) {
+        const float Fl = l == 0 ? 0.0f : F[l - 1] * a.dt;
+        if (COLL == 2) {
+            // streaming only: f* = f
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                Codec<ST>::store(fout + (int64_t)(l * kQ + q) * g.N + node, f[l][q], l == 0 ? wq(q) * a.n0 : 0.0f);
-    } else {
-        const float om = a.omega;
+                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, f[l][q], l == 0 ? wq(q) * a.n0 : 0.0f);
+        } else if (COLL == 0) {
+            // BGK, Eq. 7, plus the source of Eq. 10
 #pragma unroll
-        for (int l = 0; l < kL; ++l) {
-            const float Fl = l == 0 ? 0.0f : F[l - 1] * a.dt;
-            if (COLL == 0) {
-                // BGK, Eq. 7 + source Eq. 10
+            for (int q = 0; q < kQ; ++q) {
+                const float fs = f[l][q] + om * (A[l] * phi[q] - f[l][q]) + wq(q) * Fl;
+                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l == 0 ? wq(q) * a.n0 : 0.0f);
+            }
+        } else {
+            // Regularized: relax only the first Hermite moment of f - f^eq,
+            // Pi = sum_i xi_i (f_i - A phi_i) = sum_i xi_i f_i - A u
+            // (sum_i xi_i phi_i = u exactly for the D3Q19 weights).
+            float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
 #pragma unroll
-                for (int q = 0; q < kQ; ++q) {
-                    const float fe = A[l] * phi[q];
-                    const float fs = f[l][q] + om * (fe - f[l][q]) + wq(q) * Fl;
-                    Codec<ST>::store(fout + (int64_t)(l * kQ + q) * g.N + node, fs, l == 0 ? wq(q) * a.n0 : 0.0f);
-                }
-            } else {
-                // Regularized: relax only Pi = sum_i xi_i (f_i - f^eq_i).
-                float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f;
+            for (int q = 1; q < kQ; ++q) {
+                if (xi_x(q) > 0) m0 += f[l][q]; else if (xi_x(q) < 0) m0 -= f[l][q];
+                if (xi_y(q) > 0) m1 += f[l][q]; else if (xi_y(q) < 0) m1 -= f[l][q];
+                if (xi_z(q) > 0) m2 += f[l][q]; else if (xi_z(q) < 0) m2 -= f[l][q];
+            }
+            const float k3 = 3.0f * (1.0f - om);
+            const float P0 = k3 * (m0 - A[l] * u[0]);
+            const float P1 = k3 * (m1 - A[l] * u[1]);
+            const float P2 = k3 * (m2 - A[l] * u[2]);
 #pragma unroll
-                for (int q = 0; q < kQ; ++q) {
-                    const float d = f[l][q] - A[l] * phi[q];
-                    if (xi_x(q)) P0 += (float)xi_x(q) * d;
-                    if (xi_y(q)) P1 += (float)xi_y(q) * d;
-                    if (xi_z(q)) P2 += (float)xi_z(q) * d;
-                }
-                const float k3 = 3.0f * (1.0f - om);
-#pragma unroll
-                for (int q = 0; q < kQ; ++q) {
-                    const float xp = (float)xi_x(q) * P0 + (float)xi_y(q) * P1 + (float)xi_z(q) * P2;
-                    const float fs = A[l] * phi[q] + k3 * wq(q) * xp + wq(q) * Fl;
-                    Codec<ST>::store(fout + (int64_t)(l * kQ + q) * g.N + node, fs, l == 0 ? wq(q) * a.n0 : 0.0f);
-                }
+            for (int q = 0; q < kQ; ++q) {
+                float xp = 0.0f;
+                if (xi_x(q)) xp += (float)xi_x(q) * P0;
+                if (xi_y(q)) xp += (float)xi_y(q) * P1;
+                if (xi_z(q)) xp += (float)xi_z(q) * P2;
+                const float fs = A[l] * phi[q] + wq(q) * (xp + Fl);
+                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l == 0 ? wq(q) * a.n0 : 0.0f);
             }
         }
     }
@@ -121,8 +130,10 @@ __global__ void __launch_bounds__(kBX * kBY) fluid_kernel(const StepArgs a) {
 
 template <int ST, int COLL>
 cudaError_t launch_fluid_t(const StepArgs& a, cudaStream_t s) {
-    dim3 block(kBX, kBY, 1);
-    dim3 grid((a.g.nx + kBX - 1) / kBX, (a.g.ny + kBY - 1) / kBY, a.g.nz);
+    const int bx = a.bx, by = a.by;
+    if (bx * by > PWFA_FLUID_MAX_THREADS || bx <= 0 || by <= 0) return cudaErrorInvalidConfiguration;
+    dim3 block(bx, by, 1);
+    dim3 grid((a.g.nx + bx - 1) / bx, (a.g.ny + by - 1) / by, a.g.nz);
     if (a.g.periodic) fluid_kernel<ST, COLL, true><<<grid, block, 0, s>>>(a);
     else fluid_kernel<ST, COLL, false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();

@@ -92,30 +92,11 @@ struct StepArgs {
     int couple;
     // driver: J_b,z = -alpha exp(-r^2/(2 sr^2) - (z - zc)^2/(2 sz^2)) at t_{n+1}
     float alpha, inv2sr2, inv2sz2, zc, dx;
+    int bx, by;           // fluid kernel block shape (autotuned per instance)
 };
 
 __device__ __forceinline__ int wrapi(int a, int n) {
     return a < 0 ? a + n : (a >= n ? a - n : a);
-}
-
-// Node index of the source of pull q at node (x,y,z); assumes that for open
-// grids (x,y,z) is an interior node so the source lies inside the grid.
-__device__ __forceinline__ int64_t pull_src(const Grid& g, int x, int y, int z, int q) {
-    int sx = x - xi_x(q), sy = y - xi_y(q), sz = z - xi_z(q);
-    if (g.periodic) { sx = wrapi(sx, g.nx); sy = wrapi(sy, g.ny); sz = wrapi(sz, g.nz); }
-    return ((int64_t)sz * g.ny + sy) * g.nx + sx;
-}
-
-// Value of a Yee array at integer index (i,j,k) with i,j,k >= -1: wraps on
-// periodic grids, zero below the grid otherwise (indices above the grid are
-// never requested by the averages).
-__device__ __forceinline__ float yee_at(const Grid& g, const float* a, int i, int j, int k) {
-    if (g.periodic) {
-        i = wrapi(i, g.nx); j = wrapi(j, g.ny); k = wrapi(k, g.nz);
-    } else if (i < 0 || j < 0 || k < 0) {
-        return 0.0f;
-    }
-    return __ldg(a + ((int64_t)k * g.ny + j) * g.nx + i);
 }
 
 }  // namespace pwfa

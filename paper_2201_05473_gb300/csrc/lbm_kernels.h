@@ -18,6 +18,10 @@ cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s);
 // Ampere, dE/dt = curl B - J: E += dt (curl_h Bn - J_edge - J_b(t_{n+1})).
 cudaError_t launch_ampere(const StepArgs& a, cudaStream_t s);
 
+// Open grids: zero the Yee components of E and B(t_n) that lie on or outside
+// the conducting walls (tangential E, normal B, components past the grid).
+cudaError_t launch_zero_walls(const StepArgs& a, cudaStream_t s);
+
 // Initial condition: stored populations whose pull gives the plasma at rest,
 // f = w_i n0 prof(r) (lattice 0), 0 (momentum lattices).
 cudaError_t launch_init(const Grid& g, void* f, int storage, float n0, const double* d_profile,

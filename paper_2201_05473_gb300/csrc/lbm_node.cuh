@@ -16,10 +16,13 @@ __device__ __forceinline__ int64_t src_index(const Grid& g, int x, int y, int z,
 
 // Pull the 76 populations f^n(x) = f*(x - xi_i) of node (x,y,z). Open grids
 // gather at the clamped interior node instead and flag the node as a boundary
-// node: its state is then f^eq of those moments (Eq. 14).
+// node: its state is then f^eq of those moments (Eq. 14). Each lattice's 19
+// planes form one block of 19 N elements addressed with 32-bit offsets
+// (the host limits N so that 19 N < 2^32).
 template <int ST, bool PER>
 __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::T* __restrict__ fin,
                                        float n0, int x, int y, int z, float f[kL][kQ], bool& bnd) {
+    using T = typename Codec<ST>::T;
     int xs = x, ys = y, zs = z;
     bnd = false;
     if (!PER) {
@@ -28,12 +31,22 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
         zs = min(max(z, 1), g.nz - 2);
         bnd = (xs != x) | (ys != y) | (zs != z);
     }
+    const uint32_t N = (uint32_t)g.N;
+    const T* __restrict__ fl[kL] = {fin, fin + (size_t)kQ * N, fin + (size_t)2 * kQ * N, fin + (size_t)3 * kQ * N};
+    const uint32_t sxy = (uint32_t)g.nx * (uint32_t)g.ny;
+    const uint32_t nodec = ((uint32_t)zs * (uint32_t)g.ny + (uint32_t)ys) * (uint32_t)g.nx + (uint32_t)xs;
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
-        const int64_t src = src_index<PER>(g, xs, ys, zs, q);
+        uint32_t src;
+        if (PER) {
+            src = (uint32_t)src_index<true>(g, xs, ys, zs, q);
+        } else {
+            const int d = xi_x(q) + xi_y(q) * g.nx;
+            src = nodec - (uint32_t)d - (uint32_t)(xi_z(q)) * sxy;
+        }
+        const uint32_t off = (uint32_t)q * N + src;
 #pragma unroll
-        for (int l = 0; l < kL; ++l)
-            f[l][q] = Codec<ST>::load(fin + (int64_t)(l * kQ + q) * g.N + src, l == 0 ? wq(q) * n0 : 0.0f);
+        for (int l = 0; l < kL; ++l) f[l][q] = Codec<ST>::load(fl[l] + off, l == 0 ? wq(q) * n0 : 0.0f);
     }
 }
 
@@ -79,25 +92,44 @@ __device__ __forceinline__ float yat(const Grid& g, const float* a, int i, int j
     return __ldg(a + ((int64_t)k * g.ny + j) * g.nx + i);
 }
 
+// Open grids keep a zero plane in front of every Yee array and every
+// component outside the conducting box at zero, so the index just below the
+// grid (x-1, y-1 or z-1 wrapping into the previous row/plane) always reads 0.
 template <bool PER>
 __device__ __forceinline__ void node_E(const Grid& g, const float* const E[3], int x, int y, int z, float e[3]) {
-    e[0] = 0.5f * (yat<PER>(g, E[0], x - 1, y, z) + yat<PER>(g, E[0], x, y, z));
-    e[1] = 0.5f * (yat<PER>(g, E[1], x, y - 1, z) + yat<PER>(g, E[1], x, y, z));
-    e[2] = 0.5f * (yat<PER>(g, E[2], x, y, z - 1) + yat<PER>(g, E[2], x, y, z));
+    if (PER) {
+        e[0] = 0.5f * (yat<PER>(g, E[0], x - 1, y, z) + yat<PER>(g, E[0], x, y, z));
+        e[1] = 0.5f * (yat<PER>(g, E[1], x, y - 1, z) + yat<PER>(g, E[1], x, y, z));
+        e[2] = 0.5f * (yat<PER>(g, E[2], x, y, z - 1) + yat<PER>(g, E[2], x, y, z));
+    } else {
+        const int64_t o = ((int64_t)z * g.ny + y) * g.nx + x;
+        const int64_t sxy = (int64_t)g.nx * g.ny;
+        e[0] = 0.5f * (__ldg(E[0] + o - 1) + __ldg(E[0] + o));
+        e[1] = 0.5f * (__ldg(E[1] + o - g.nx) + __ldg(E[1] + o));
+        e[2] = 0.5f * (__ldg(E[2] + o - sxy) + __ldg(E[2] + o));
+    }
 }
 
-template <bool PER>
-__device__ __forceinline__ float face4(const Grid& g, const float* a, int x0, int y0, int z0,
-                                       int x1, int y1, int z1, int x2, int y2, int z2) {
-    return yat<PER>(g, a, x0, y0, z0) + yat<PER>(g, a, x1, y1, z1) + yat<PER>(g, a, x2, y2, z2);
-}
-
-// Average of the four faces around the node for one B array.
+// Sum over the four faces around the node for one B array.
 template <bool PER>
 __device__ __forceinline__ void node_B_sum(const Grid& g, const float* const B[3], int x, int y, int z, float b[3]) {
-    b[0] = yat<PER>(g, B[0], x, y, z) + face4<PER>(g, B[0], x, y - 1, z, x, y, z - 1, x, y - 1, z - 1);
-    b[1] = yat<PER>(g, B[1], x, y, z) + face4<PER>(g, B[1], x - 1, y, z, x, y, z - 1, x - 1, y, z - 1);
-    b[2] = yat<PER>(g, B[2], x, y, z) + face4<PER>(g, B[2], x - 1, y, z, x, y - 1, z, x - 1, y - 1, z);
+    if (PER) {
+        b[0] = yat<PER>(g, B[0], x, y, z) + yat<PER>(g, B[0], x, y - 1, z) + yat<PER>(g, B[0], x, y, z - 1)
+             + yat<PER>(g, B[0], x, y - 1, z - 1);
+        b[1] = yat<PER>(g, B[1], x, y, z) + yat<PER>(g, B[1], x - 1, y, z) + yat<PER>(g, B[1], x, y, z - 1)
+             + yat<PER>(g, B[1], x - 1, y, z - 1);
+        b[2] = yat<PER>(g, B[2], x, y, z) + yat<PER>(g, B[2], x - 1, y, z) + yat<PER>(g, B[2], x, y - 1, z)
+             + yat<PER>(g, B[2], x - 1, y - 1, z);
+    } else {
+        const int64_t o = ((int64_t)z * g.ny + y) * g.nx + x;
+        const int64_t sx = g.nx, sxy = (int64_t)g.nx * g.ny;
+        const float* b0 = B[0] + o;
+        const float* b1 = B[1] + o;
+        const float* b2 = B[2] + o;
+        b[0] = __ldg(b0) + __ldg(b0 - sx) + __ldg(b0 - sxy) + __ldg(b0 - sx - sxy);
+        b[1] = __ldg(b1) + __ldg(b1 - 1) + __ldg(b1 - sxy) + __ldg(b1 - 1 - sxy);
+        b[2] = __ldg(b2) + __ldg(b2 - 1) + __ldg(b2 - sx) + __ldg(b2 - 1 - sx);
+    }
 }
 
 }  // namespace pwfa

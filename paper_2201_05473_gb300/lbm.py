@@ -57,7 +57,8 @@ _lib = None
 
 EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_state",
            "pwfa_lbm_set_state", "pwfa_lbm_steps_done", "pwfa_lbm_set_stream",
-           "pwfa_lbm_destroy", "pwfa_lbm_last_error", "pwfa_lbm_profile", "pwfa_lbm_kernel_times")
+           "pwfa_lbm_destroy", "pwfa_lbm_last_error", "pwfa_lbm_profile", "pwfa_lbm_kernel_times",
+           "pwfa_lbm_set_launch", "pwfa_lbm_get_launch", "pwfa_lbm_autotune")
 
 
 def load(build: bool = True):
@@ -85,10 +86,14 @@ def load(build: bool = True):
         lib.pwfa_lbm_destroy.argtypes = [vp]
         lib.pwfa_lbm_profile.argtypes = [vp, i32]
         lib.pwfa_lbm_kernel_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
+        lib.pwfa_lbm_set_launch.argtypes = [vp, i32, i32, i32]
+        lib.pwfa_lbm_get_launch.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.pwfa_lbm_autotune.argtypes = [vp, i32]
         lib.pwfa_lbm_last_error.restype = ctypes.c_char_p
         for name in ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_state",
                      "pwfa_lbm_set_state", "pwfa_lbm_set_stream", "pwfa_lbm_destroy",
-                     "pwfa_lbm_profile", "pwfa_lbm_kernel_times"):
+                     "pwfa_lbm_profile", "pwfa_lbm_kernel_times", "pwfa_lbm_set_launch",
+                     "pwfa_lbm_get_launch", "pwfa_lbm_autotune"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -181,6 +186,8 @@ class Simulation:
         return int(r)
 
     def shape(self, instance: int = 0):
+        if not 0 <= instance < len(self.works):
+            raise LBMError(-1, f"instance {instance} out of range (0..{len(self.works) - 1})")
         w = self.works[instance]
         return (w.nz, w.ny, w.nx)
 
@@ -211,6 +218,17 @@ class Simulation:
         rc = self._lib.pwfa_lbm_fields(self._h, instance, 0, None, 0,
                                        ctypes.cast(ptr, ctypes.POINTER(ctypes.c_double)))
         _check(rc)
+
+    def set_launch(self, bx: int, by: int, instance: int = 0):
+        _check(self._lib.pwfa_lbm_set_launch(self._h, instance, bx, by))
+
+    def get_launch(self, instance: int = 0):
+        bx, by = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.pwfa_lbm_get_launch(self._h, instance, ctypes.byref(bx), ctypes.byref(by)))
+        return bx.value, by.value
+
+    def autotune(self, reps: int = 3):
+        _check(self._lib.pwfa_lbm_autotune(self._h, reps))
 
     def profile(self, enable: bool = True):
         _check(self._lib.pwfa_lbm_profile(self._h, 1 if enable else 0))
