@@ -191,6 +191,31 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps);
 /* Re-target all later work of the handle to another cudaStream_t. */
 int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream);
 
+/* FP64 diagnostics of a state the caller holds in device memory, computed
+ * without allocating anything. The paper has no counterpart: this serves
+ * callers that must not let a library call cudaMalloc/cudaFree, such as an
+ * in-situ analysis hook inside another code, or an application that owns a
+ * fixed device-memory budget through its own pool (cudaFree also
+ * synchronises the whole device and would stall its other streams).
+ *   dev_f   pre-collision populations f^n, [4][19][z][y][x] FP32 (the
+ *           layout of pwfa_lbm_get_state), device memory
+ *   dev_E, dev_B  raw Yee E and B, [3][z][y][x] FP32, device memory
+ *   dev_out 8 doubles, device memory, the same quantities as the host_diag
+ *           of pwfa_lbm_fields: sum n, sum n p_k (3), field energy
+ *           1/2 sum(E^2 + B^2) dx^3, min n, max |beta|, non-finite count
+ *   n_floor density floor of p = A / max(n, n_floor); <= 0 selects 1e-6
+ * Work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default
+ * stream) and not synchronised. Scratch is a fixed 1 MiB array inside the
+ * library that every GPU which loads it holds until exit; grids of more than
+ * 67,108,864 nodes are rejected with PWFA_ERR_PARAM. The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress), so make
+ * the first call on a device before any stream capture. All calls share the
+ * array: calls that overlap on the GPU (different streams, or several host
+ * threads) race and must be serialised by the caller. */
+int pwfa_lbm_diag_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double n_floor,
+                          const float* dev_f, const float* dev_E, const float* dev_B,
+                          double* dev_out, void* cuda_stream);
+
 /* Release every device allocation of the handle. Accepts NULL. */
 int pwfa_lbm_destroy(pwfa_lbm_t* h);
 

@@ -55,6 +55,12 @@ struct Instance {
 
 }  // namespace
 
+namespace pwfa {
+// Record the calling thread's error message for pwfa_lbm_last_error (used by
+// entry points defined in other translation units).
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace pwfa
+
 struct pwfa_lbm {
     std::vector<Instance> inst;
     cudaStream_t stream = nullptr;

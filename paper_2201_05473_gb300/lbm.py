@@ -58,7 +58,8 @@ _lib = None
 EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_state",
            "pwfa_lbm_set_state", "pwfa_lbm_steps_done", "pwfa_lbm_set_stream",
            "pwfa_lbm_destroy", "pwfa_lbm_last_error", "pwfa_lbm_profile", "pwfa_lbm_kernel_times",
-           "pwfa_lbm_set_launch", "pwfa_lbm_get_launch", "pwfa_lbm_autotune")
+           "pwfa_lbm_set_launch", "pwfa_lbm_get_launch", "pwfa_lbm_autotune",
+           "pwfa_lbm_diag_noalloc")
 
 
 def load(build: bool = True):
@@ -89,6 +90,9 @@ def load(build: bool = True):
         lib.pwfa_lbm_set_launch.argtypes = [vp, i32, i32, i32]
         lib.pwfa_lbm_get_launch.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         lib.pwfa_lbm_autotune.argtypes = [vp, i32]
+        lib.pwfa_lbm_diag_noalloc.argtypes = [i32, i32, i32, ctypes.c_double, ctypes.c_double,
+                                              vp, vp, vp, vp, vp]
+        lib.pwfa_lbm_diag_noalloc.restype = ctypes.c_int
         lib.pwfa_lbm_last_error.restype = ctypes.c_char_p
         for name in ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_state",
                      "pwfa_lbm_set_state", "pwfa_lbm_set_stream", "pwfa_lbm_destroy",
