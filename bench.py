@@ -262,6 +262,99 @@ def run_ours(args):
             sim.close()
             stream.synchronize()
             e2e_s = time.perf_counter() - t0
+        # ---- reduced-precision storage: same workload, BF16 / FP16 deviations
+        storage_lines = {}
+        if not args.no_extra:
+            for name, st in (("bf16", W.BF16), ("f16", W.F16)):
+                w2 = w.replace(storage=st)
+                torch.cuda.empty_cache()
+                sim = lbm.Simulation(w2, stream=stream)
+                sim.step(args.warmup)
+                sim.autotune(3)
+                sim.kernel_times()
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(args.steps)
+                e1.record(stream)
+                stream.synchronize()
+                ms2 = e0.elapsed_time(e1)
+                sim.profile(True)
+                sim.step(args.steps)
+                k2, l2 = sim.kernel_times()
+                sim.profile(False)
+                d2 = sim.diag(check=False)
+                sim.close()
+                glups = N * args.steps / (ms2 * 1e-3) / 1e9
+                fl_ms = k2["fluid"] / max(l2["fluid"], 1)
+                storage_lines[name] = {
+                    "value": glups, "unit": "GLUPS", "vs_f32": glups / (N * args.steps / (ms * 1e-3) / 1e9),
+                    "ms_per_step": ms2 / args.steps, "bytes_per_node_step": STEP_BYTES[st],
+                    "pct_hbm_step": glups * 1e9 * STEP_BYTES[st] / (hbm_peak()[0] * 1e9),
+                    "fluid_kernel_GBs": (76 * 2 * 2 + 48) * N / (fl_ms * 1e-3) / 1e9,
+                    "finite": bool(d2[7] == 0)}
+        # ---- adjoint: the differentiable form (256x128x128, 500 steps,
+        # checkpoints every 23 steps, witness loss)
+        adjoint_line = None
+        if not args.no_extra:
+            torch.cuda.empty_cache()
+            wa = W.differentiable().replace(profile=__import__("numpy").ones(64), profile_rmax=128 * 0.2 / 2)
+            Ta = args.adjoint_steps
+            sim = lbm.Simulation(wa, stream=stream)
+            barrier()
+            t0 = time.perf_counter()
+            sim.record(Ta, 0)
+            stream.synchronize()
+            t_rec = time.perf_counter() - t0
+            k, mask = W.witness_slab(wa, Ta)
+            seed = torch.zeros((3, wa.nz, wa.ny, wa.nx), dtype=torch.float32, device="cuda")
+            seed[2, k][torch.from_numpy(mask).cuda()] = -1.0 / float(mask.sum())
+            t0 = time.perf_counter()
+            g = sim.adjoint_step(seed)
+            t_adj = time.perf_counter() - t0
+            sim.close()
+            adjoint_line = {"value": wa.nodes * Ta / t_adj / 1e9, "unit": "GLUPS",
+                            "note": "reverse sweep incl. segment recompute; node-steps of the adjoint / wall time",
+                            "record_glups": wa.nodes * Ta / t_rec / 1e9, "grid_zyx": [wa.nz, wa.ny, wa.nx],
+                            "steps": Ta, "ckpt_every": int(__import__("math").ceil(Ta ** 0.5)),
+                            "grad_alpha_sigr_sigz": [float(v) for v in g[:3]]}
+        # ---- batched form: 64 instances of uneven size in one persistent,
+        # graph-replayed launch per phase, against the same instances stepped
+        # one after another
+        batch_line = None
+        if not args.no_extra:
+            torch.cuda.empty_cache()
+            ws = W.batched_scan(64, seed=0)
+            tot = sum(x.nodes for x in ws)
+            sb = lbm.Simulation(ws, stream=stream)
+            sb.step(args.warmup + (args.warmup % 2))
+            sb.autotune(2)
+            sb.step(2)
+            sb.kernel_times()
+            Kb = args.steps - args.steps % 2
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sb.step(Kb)
+            e1.record(stream)
+            stream.synchronize()
+            msb = e0.elapsed_time(e1)
+            _, lb = sb.kernel_times()
+            sb.set_batching(False)
+            sb.step(2)
+            e0.record(stream)
+            sb.step(Kb)
+            e1.record(stream)
+            stream.synchronize()
+            msu = e0.elapsed_time(e1)
+            db = [sb.diag(i, check=False)[7] for i in range(len(ws))]
+            sb.close()
+            batch_line = {"value": tot * Kb / (msb * 1e-3) / 1e9, "unit": "GLUPS", "instances": len(ws),
+                          "nodes_total": tot, "steps": Kb,
+                          "grids_zyx": sorted({(x.nz, x.ny, x.nx) for x in ws}),
+                          "launches_per_step": sum(lb.values()) / Kb,
+                          "unbatched_glups": tot * Kb / (msu * 1e-3) / 1e9, "speedup_vs_unbatched": msu / msb,
+                          "nonfinite_instances": int(sum(1 for v in db if v > 0))}
     ms_t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -301,6 +394,9 @@ def run_ours(args):
                 "h2d_bytes_per_step": lbm.ctypes.sizeof(lbm.Params) / args.steps,
                 "d2h_bytes_per_step": 64,
                 "note": "create from host params + per step pwfa_lbm_step and a D2H read of the FP64 diagnostics"},
+        "storage_forms": storage_lines or None,
+        "adjoint": adjoint_line,
+        "batched": batch_line,
         "clocks": clk.summary(),
         "diag_after": {"sum_n": diag[0], "min_n": diag[5], "max_beta": diag[6], "nonfinite": diag[7]},
     }
@@ -309,6 +405,43 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def precision_report(args):
+    """Precision form: config-1 physics on 256x128x128, populations stored in
+    FP32, BF16 and FP16 (deviations), errors of n, beta and E_z against the
+    FP64 oracle every 100 steps up to 1000. One JSON line."""
+    import numpy as np
+    import torch
+    from paper_2201_05473_gb300 import lbm
+    import oracle
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    oracle.build()
+    base = W.precision_form(W.F32)
+    steps = args.steps if args.steps != 200 else base.steps
+    o = oracle.Oracle(base.nx, base.ny, base.nz, base.dx, base.dt, base.tau, alpha=base.alpha,
+                      sigma_r=base.sigma_r, sigma_z=base.sigma_z, z0=base.z0)
+    sims = {name: lbm.Simulation(base.replace(storage=st)) for name, st in
+            (("f32", W.F32), ("bf16", W.BF16), ("f16", W.F16))}
+    m = lbm.FIELD_N | lbm.FIELD_UX | lbm.FIELD_UY | lbm.FIELD_UZ | lbm.FIELD_EZ | lbm.RAW_YEE
+
+    def rel(a, b):
+        return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+    table = {name: [] for name in sims}
+    for s0 in range(100, steps + 1, 100):
+        o.step(100)
+        mo = o.moments()
+        E, _ = o.get_fields()
+        for name, sim in sims.items():
+            sim.step(100)
+            g = sim.fields(m).cpu().numpy().astype(np.float64)
+            table[name].append({"step": s0, "n": rel(g[0], mo["n"]), "beta": rel(g[1:4], mo["beta"]),
+                                "Ez": rel(g[4], E[2])})
+    for sim in sims.values():
+        sim.close()
+    print(json.dumps({"report": "precision", "workload": base.name, "grid_zyx": [base.nz, base.ny, base.nx],
+                      "errors_vs_fp64_oracle": table}), flush=True)
 
 
 def main():
@@ -321,10 +454,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", default="", help="override the grid as ZxYxX (profiling captures)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the BF16/FP16 and adjoint lines")
+    ap.add_argument("--adjoint-steps", type=int, default=500)
+    ap.add_argument("--report", default="", choices=["", "precision"],
+                    help="precision: error table of BF16/FP16/FP32 storage against the oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.report == "precision":
+        precision_report(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -114,6 +114,31 @@ int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances,
  * with J = -n beta and the driver current. Asynchronous on the stream. */
 int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps);
 
+/* Gradients by the discrete adjoint (the paper has no adjoint; this
+ * differentiates the scheme above exactly, step by step in reverse).
+ *
+ * pwfa_lbm_record resets the instance to its initial condition (t = 0) and
+ * advances it nsteps, keeping a checkpoint of the full state every
+ * ckpt_every steps (0 selects ceil(sqrt(nsteps))) plus the final state. The
+ * instance is left at step nsteps. Device memory: (nsteps/ckpt_every + 1)
+ * states of 76 N populations + 6 N field values, ckpt_every segment states
+ * and ~174 N floats of adjoint scratch; PWFA_ERR_ALLOC if it does not fit. */
+int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckpt_every);
+
+/* Gradient of L = sum(seed_E * E(t_{T+1/2})) over the raw Yee E after the
+ * recorded T steps (seed_E: [3][z][y][x] FP32, host or device) with respect
+ * to theta = (alpha, sigma_r, sigma_z, profile[0..n_profile-1]), written to
+ * host_grad (n_grad >= 3 + n_profile doubles). Each segment is recomputed
+ * from its checkpoint, then reversed: transposed Ampere (with the driver's
+ * parameter derivatives), transposed fluid step (J = -n beta(p*), collision,
+ * equilibrium, Lorentz source, beta(p), the n-floor branch, Eq. 14 boundary
+ * nodes, transposed pull), transposed node averages and Faraday; the initial
+ * populations give the profile derivative. Adjoint state is FP32, parameter
+ * gradients are accumulated in FP64. n_profile <= 256. PWFA_ERR_STATE if
+ * nothing was recorded. The instance ends at step T again. */
+int pwfa_lbm_adjoint_step(pwfa_lbm_t* h, int32_t instance, const float* seed_E, double* host_grad,
+                          int32_t n_grad);
+
 /* Field export masks for pwfa_lbm_fields. */
 #define PWFA_FIELD_N (1u << 0)   /* electron density n = sum of lattice 0 */
 #define PWFA_FIELD_UX (1u << 1)  /* beta_x = p_x / sqrt(1 + p^2) */
@@ -163,7 +188,8 @@ int64_t pwfa_lbm_steps_done(pwfa_lbm_t* h, int32_t instance);
 #define PWFA_KERNEL_FARADAY 0 /* Yee B update */
 #define PWFA_KERNEL_FLUID 1   /* fused stream + moments + source + collide */
 #define PWFA_KERNEL_AMPERE 2  /* Yee E update with plasma and driver current */
-#define PWFA_KERNEL_KINDS 3
+#define PWFA_KERNEL_AUX 3     /* batched path: per-instance step counters */
+#define PWFA_KERNEL_KINDS 4
 
 /* Per-kernel device timing, off by default. While enabled, each step records
  * a CUDA event pair around every kernel it launches on the handle's stream
@@ -187,6 +213,16 @@ int pwfa_lbm_get_launch(pwfa_lbm_t* h, int32_t instance, int32_t* bx, int32_t* b
  * fastest. The kernel is re-run on the current state without advancing it,
  * so the simulation state is unchanged. Synchronises the stream. */
 int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps);
+
+/* Batched path, on by default. A handle with several instances that share
+ * storage, collision, boundary and coupling advances them together: one
+ * persistent launch per phase (Faraday, fluid, Ampere) strides over a work
+ * list of 128-node tiles of every instance, and two steps at a time are
+ * replayed from a captured CUDA graph (an odd remainder step runs per
+ * instance). The instance table and graph are rebuilt lazily after any call
+ * that changes an instance's state or launch shape. enable = 0 advances the
+ * instances one after another with ordinary launches. */
+int pwfa_lbm_set_batching(pwfa_lbm_t* h, int32_t enable);
 
 /* Re-target all later work of the handle to another cudaStream_t. */
 int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream);

@@ -77,6 +77,9 @@ def _load():
             lib.oracle_get_fields.argtypes = [ctypes.c_void_p, dp, dp]
             lib.oracle_set_fields.argtypes = [ctypes.c_void_p, dp, dp]
             lib.oracle_last_step.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
+            lib.oracle_tangent_run.argtypes = [ctypes.POINTER(_Params), ctypes.c_int32, ctypes.c_int32,
+                                               dp, dp, dp]
+            lib.oracle_tangent_run.restype = ctypes.c_int
             lib.oracle_qtilde.restype = ctypes.c_double
             lib.oracle_qtilde.argtypes = [ctypes.c_double] * 5 + [dp]
             _lib = lib
@@ -169,6 +172,27 @@ class Oracle:
         out = np.empty(8, dtype=np.float64)
         self._lib.oracle_diag(self._h, _ptr(out))
         return out
+
+
+def tangent_run(nsteps, dirs, nx, ny, nz, dx, dt, tau, collision=COLL_BGK, boundary=BND_OPEN,
+                couple=1, n0=1.0, profile=None, profile_rmax=0.0, alpha=0.0, sigma_r=0.5,
+                sigma_z=0.5, z0=0.0, n_floor=1e-6):
+    """Raw Yee E after nsteps and its derivatives along dirs ([ndir][3 + n_profile],
+    parameters ordered alpha, sigma_r, sigma_z, profile...), by forward-mode
+    dual numbers. Returns (E [3][z][y][x], dE [ndir][3][z][y][x])."""
+    lib = _load()
+    dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    prof = None if profile is None else np.ascontiguousarray(profile, dtype=np.float64)
+    p = _Params(nx, ny, nz, dx, dt, tau, collision, boundary, couple, n0,
+                _ptr(prof) if prof is not None else None, 0 if prof is None else len(prof),
+                profile_rmax, alpha, sigma_r, sigma_z, z0, n_floor)
+    nd = dirs.shape[0]
+    assert dirs.shape[1] == 3 + (0 if prof is None else len(prof))
+    E = np.empty((3, nz, ny, nx))
+    dE = np.empty((nd, 3, nz, ny, nx))
+    if lib.oracle_tangent_run(ctypes.byref(p), int(nsteps), nd, _ptr(dirs), _ptr(E), _ptr(dE)) != 0:
+        raise ValueError("oracle_tangent_run failed")
+    return E, dE
 
 
 def qtilde(charge_coulomb, sx, sy, sz, n0_m3):

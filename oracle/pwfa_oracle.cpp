@@ -544,6 +544,43 @@ void oracle_diag(void* h, double* out) {
     out[5] = mn; out[6] = mb; out[7] = bad;
 }
 
+/* Forward-mode derivatives. Parameters theta = (alpha, sigma_r, sigma_z,
+ * profile[0 .. n_profile-1]); dirs holds ndir (1..4) tangent directions of
+ * length 3 + n_profile. Runs nsteps from the initial state on dual numbers
+ * and returns the raw Yee E (value, [3][N]) and its directional derivatives
+ * dE ([ndir][3][N]). The same step code as the primal path, templated on the
+ * scalar type. */
+int oracle_tangent_run(const oracle_params* prm, int32_t nsteps, int32_t ndir, const double* dirs,
+                       double* E, double* dE) {
+    if (!prm || ndir < 1 || ndir > 4 || nsteps < 0) return -1;
+    using D = Dual<4>;
+    Sim<D>* s = new (std::nothrow) Sim<D>();
+    if (!s) return -1;
+    s->p = *prm;
+    const int np = prm->profile && prm->n_profile > 0 ? prm->n_profile : 0;
+    const int nt = 3 + np;
+    auto seed = [&](double v, int idx) {
+        D d(v);
+        for (int k = 0; k < ndir; ++k) d.d[k] = dirs[k * nt + idx];
+        return d;
+    };
+    s->alpha = seed(prm->alpha, 0);
+    s->sigma_r = seed(prm->sigma_r, 1);
+    s->sigma_z = seed(prm->sigma_z, 2);
+    for (int j = 0; j < np; ++j) s->prof.push_back(seed(prm->profile[j], 3 + j));
+    s->p.profile = nullptr;
+    s->init();
+    for (int n = 0; n < nsteps; ++n) s->step();
+    const int64_t N = s->N;
+    for (int c = 0; c < 3; ++c)
+        for (int64_t o = 0; o < N; ++o) {
+            E[c * N + o] = s->E[c][o].v;
+            for (int k = 0; k < ndir; ++k) dE[((int64_t)k * 3 + c) * N + o] = s->E[c][o].d[k];
+        }
+    delete s;
+    return 0;
+}
+
 /* Normalised charge of Eq. 15, read with k_p^{+3} (the printed exponent -3
  * is dimensionally inconsistent): Q = (2 pi)^{3/2} sx sy sz alpha k_p^3.
  * Inputs in SI units: sigmas in metres, n0 in m^-3; k_p = omega_p / c;

@@ -9,6 +9,8 @@
 #include <vector>
 
 #include "../../include/pwfa_lbm.h"
+#include "lbm_adjoint.h"
+#include "lbm_batch.h"
 #include "lbm_kernels.h"
 
 using namespace pwfa;
@@ -51,6 +53,18 @@ struct Instance {
     double* d_profile = nullptr;
     int64_t steps = 0;
     int bx = 64, by = 2;  // fluid kernel block shape (pwfa_lbm_autotune refines it)
+    // recording for the adjoint: checkpoints every K steps (+ the final
+    // state), one segment of per-step states, adjoint scratch
+    struct Recording {
+        int64_t T = 0;
+        int K = 0, ncp = 0;
+        bool valid = false;
+        void* cp = nullptr;
+        size_t cp_stride = 0;
+        void* seg = nullptr;
+        size_t seg_stride = 0;
+        void* adj = nullptr;
+    } rec;
 };
 
 }  // namespace
@@ -72,8 +86,16 @@ struct pwfa_lbm {
     bool profiling = false;
     std::vector<cudaEvent_t> events;          // pool, used in start/stop pairs
     std::vector<int> pending_kind;            // kind of each recorded pair
-    double ms[PWFA_KERNEL_KINDS] = {0, 0, 0};
-    int64_t launches[PWFA_KERNEL_KINDS] = {0, 0, 0};
+    double ms[PWFA_KERNEL_KINDS] = {0, 0, 0, 0};
+    int64_t launches[PWFA_KERNEL_KINDS] = {0, 0, 0, 0};
+    // batched persistent path (several homogeneous instances)
+    bool batching = true;
+    bool batch_valid = false;
+    BatchEntry* d_entries = nullptr;
+    int64_t* d_steps = nullptr;
+    BatchLaunch blaunch{};
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph2 = nullptr;  // two steps (both parities)
 };
 
 namespace {
@@ -169,7 +191,15 @@ int ensure_staging(pwfa_lbm* h, size_t bytes) {
     return PWFA_OK;
 }
 
+void free_recording(Instance& in) {
+    if (in.rec.cp) cudaFree(in.rec.cp);
+    if (in.rec.seg) cudaFree(in.rec.seg);
+    if (in.rec.adj) cudaFree(in.rec.adj);
+    in.rec = Instance::Recording{};
+}
+
 void free_instance(Instance& in) {
+    free_recording(in);
     if (in.arena) cudaFree(in.arena);
     in.arena = nullptr;
 }
@@ -248,6 +278,162 @@ int timed_launch(pwfa_lbm* h, int kind, const char* what, F&& launch) {
     return PWFA_OK;
 }
 
+// Back to the initial condition (t = 0): populations of the plasma at
+// rest, zero fields and currents.
+int reset_instance(Instance& in, cudaStream_t s) {
+    const int64_t N = in.g.N;
+    for (int c = 0; c < 3; ++c) {
+        PWFA_CUDA(cudaMemsetAsync(in.E[c], 0, sizeof(float) * N, s), "cudaMemsetAsync");
+        PWFA_CUDA(cudaMemsetAsync(in.J[c], 0, sizeof(float) * N, s), "cudaMemsetAsync");
+        for (int t = 0; t < 2; ++t) PWFA_CUDA(cudaMemsetAsync(in.B[t][c], 0, sizeof(float) * N, s), "cudaMemsetAsync");
+    }
+    in.fcur = 0;
+    in.bcur = 0;
+    in.steps = 0;
+    PWFA_CUDA(launch_init(in.g, in.f[0], in.p.storage, (float)in.p.n0, in.d_profile, (int)in.profile.size(),
+                          in.p.profile_rmax, in.p.dx, s),
+              "init kernel");
+    return PWFA_OK;
+}
+
+// ---------------------------------------------------------------- batched
+bool batch_eligible(const pwfa_lbm* h) {
+    if (!h->batching || h->inst.size() < 2) return false;
+    const auto& p0 = h->inst[0].p;
+    for (const auto& in : h->inst)
+        if (in.p.storage != p0.storage || in.p.collision != p0.collision || in.p.boundary != p0.boundary ||
+            in.p.couple != p0.couple)
+            return false;
+    return true;
+}
+
+void batch_release(pwfa_lbm* h) {
+    if (h->graph2) cudaGraphExecDestroy(h->graph2);
+    h->graph2 = nullptr;
+    h->batch_valid = false;
+}
+
+int batch_launch_all(pwfa_lbm* h, int parity, cudaStream_t s, bool timed);
+
+// Build the device instance table for the current ping-pong state and
+// capture a two-step graph (parity 0 then 1).
+int batch_build(pwfa_lbm* h) {
+    batch_release(h);
+    const int n = (int)h->inst.size();
+    if (!h->d_entries) {
+        if (cudaMalloc(&h->d_entries, sizeof(BatchEntry) * n) != cudaSuccess ||
+            cudaMalloc(&h->d_steps, sizeof(int64_t) * n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the batch table failed");
+        }
+    }
+    std::vector<BatchEntry> ent(n);
+    std::vector<int64_t> steps(n);
+    int64_t items = 0;
+    for (int i = 0; i < n; ++i) {
+        Instance& in = h->inst[i];
+        if (in.bx * in.by != kBatchTile) { in.bx = 64; in.by = 2; }
+        BatchEntry& e = ent[i];
+        e.args[0] = make_args(in);
+        in.fcur = 1 - in.fcur;
+        if (in.p.couple) in.bcur = 1 - in.bcur;
+        e.args[1] = make_args(in);
+        in.fcur = 1 - in.fcur;
+        if (in.p.couple) in.bcur = 1 - in.bcur;
+        e.bx = in.bx;
+        e.by = in.by;
+        e.tiles_x = (in.g.nx + in.bx - 1) / in.bx;
+        e.tiles_y = (in.g.ny + in.by - 1) / in.by;
+        e.item_begin = items;
+        items += (int64_t)e.tiles_x * e.tiles_y * in.g.nz;
+        e.z0 = in.p.z0;
+        e.dt = in.p.dt;
+        e.step = h->d_steps + i;
+        steps[i] = in.steps;
+    }
+    PWFA_CUDA(cudaMemcpyAsync(h->d_entries, ent.data(), sizeof(BatchEntry) * n, cudaMemcpyHostToDevice, h->stream),
+              "batch table copy");
+    PWFA_CUDA(cudaMemcpyAsync(h->d_steps, steps.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream),
+              "batch counters copy");
+    PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    const auto& p0 = h->inst[0].p;
+    h->blaunch.entries = h->d_entries;
+    h->blaunch.ninst = n;
+    h->blaunch.nitems = items;
+    PWFA_CUDA(batch_grid_size(p0.storage, p0.collision, p0.boundary == PWFA_PERIODIC, &h->blaunch.grid),
+              "batch occupancy");
+    if (!h->capture_stream) PWFA_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaGraph_t graph = nullptr;
+    PWFA_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    int rc = batch_launch_all(h, 0, h->capture_stream, false);
+    if (rc == PWFA_OK) rc = batch_launch_all(h, 1, h->capture_stream, false);
+    cudaError_t e = cudaStreamEndCapture(h->capture_stream, &graph);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph2, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    h->batch_valid = true;
+    return PWFA_OK;
+}
+
+int step_instance(pwfa_lbm* h, Instance& in);
+
+// One batched step of every instance with the given parity.
+int batch_launch_all(pwfa_lbm* h, int parity, cudaStream_t s, bool timed) {
+    const auto& p0 = h->inst[0].p;
+    const bool per = p0.boundary == PWFA_PERIODIC;
+    const int kinds[4] = {PWFA_KERNEL_FARADAY, PWFA_KERNEL_FLUID, PWFA_KERNEL_AMPERE, PWFA_KERNEL_AUX};
+    for (int phase = 0; phase < 4; ++phase) {
+        if ((phase == 0 || phase == 2) && !p0.couple) continue;
+        if (timed) {
+            cudaStream_t keep = h->stream;
+            h->stream = s;
+            int rc = timed_launch(h, kinds[phase], "batch kernel", [&] {
+                return launch_batch_phase(h->blaunch, phase, parity, p0.storage, p0.collision, per, s);
+            });
+            h->stream = keep;
+            if (rc) return rc;
+        } else {
+            PWFA_CUDA(launch_batch_phase(h->blaunch, phase, parity, p0.storage, p0.collision, per, s), "batch kernel");
+        }
+    }
+    return PWFA_OK;
+}
+
+int batch_steps(pwfa_lbm* h, int32_t nsteps) {
+    const int32_t pairs = nsteps / 2;
+    if (pairs > 0) {
+        if (!h->batch_valid) {
+            int rc = batch_build(h);
+            if (rc) return rc;
+        }
+        const int per_pair = h->inst[0].p.couple ? 4 : 2;
+        for (int32_t k = 0; k < pairs; ++k) {
+            if (h->profiling) {
+                int rc = batch_launch_all(h, 0, h->stream, true);
+                if (rc == PWFA_OK) rc = batch_launch_all(h, 1, h->stream, true);
+                if (rc) return rc;
+            } else {
+                PWFA_CUDA(cudaGraphLaunch(h->graph2, h->stream), "cudaGraphLaunch");
+                // launches inside the graph
+                h->launches[PWFA_KERNEL_FLUID] += 2;
+                h->launches[PWFA_KERNEL_AUX] += 2;
+                if (per_pair == 4) { h->launches[PWFA_KERNEL_FARADAY] += 2; h->launches[PWFA_KERNEL_AMPERE] += 2; }
+            }
+        }
+        for (auto& in : h->inst) in.steps += 2 * (int64_t)pairs;
+    }
+    if (nsteps % 2) {
+        for (auto& in : h->inst) {
+            int rc = step_instance(h, in);
+            if (rc) return rc;
+        }
+        h->batch_valid = false;  // ping-pong parity changed
+    }
+    return PWFA_OK;
+}
+
 int step_instance(pwfa_lbm* h, Instance& in) {
     cudaStream_t s = h->stream;
     StepArgs a = make_args(in);
@@ -269,11 +455,185 @@ int step_instance(pwfa_lbm* h, Instance& in) {
     return PWFA_OK;
 }
 
+// ---------------------------------------------------------------- adjoint
+size_t fbytes_of(const Instance& in) { return align_up((size_t)in.g.N * kPop * storage_bytes(in.p.storage)); }
+size_t vbytes_of(const Instance& in) { return align_up((size_t)in.g.N * sizeof(float)); }
+
+struct StateRef {  // one stored state inside a recording buffer
+    void* f;
+    float* E[3];
+    float* B[3];
+    float* Bn[3];
+};
+
+StateRef state_at(const Instance& in, void* base, bool with_bn) {
+    const size_t fb = fbytes_of(in), vb = vbytes_of(in);
+    char* p = static_cast<char*>(base);
+    StateRef r{};
+    r.f = p; p += fb;
+    for (int c = 0; c < 3; ++c) { r.E[c] = (float*)p; p += vb; }
+    for (int c = 0; c < 3; ++c) { r.B[c] = (float*)p; p += vb; }
+    if (with_bn) for (int c = 0; c < 3; ++c) { r.Bn[c] = (float*)p; p += vb; }
+    return r;
+}
+
+int copy_state(const Instance& in, const StateRef& dst, bool to_rec, cudaStream_t s) {
+    const size_t fb = (size_t)in.g.N * kPop * storage_bytes(in.p.storage);
+    const size_t vb = sizeof(float) * (size_t)in.g.N;
+    if (to_rec) {
+        PWFA_CUDA(cudaMemcpyAsync(dst.f, in.f[in.fcur], fb, cudaMemcpyDeviceToDevice, s), "checkpoint copy");
+        for (int c = 0; c < 3; ++c) {
+            PWFA_CUDA(cudaMemcpyAsync(dst.E[c], in.E[c], vb, cudaMemcpyDeviceToDevice, s), "checkpoint copy");
+            PWFA_CUDA(cudaMemcpyAsync(dst.B[c], in.B[in.bcur][c], vb, cudaMemcpyDeviceToDevice, s), "checkpoint copy");
+        }
+    } else {
+        PWFA_CUDA(cudaMemcpyAsync(in.f[in.fcur], dst.f, fb, cudaMemcpyDeviceToDevice, s), "restore copy");
+        for (int c = 0; c < 3; ++c) {
+            PWFA_CUDA(cudaMemcpyAsync(in.E[c], dst.E[c], vb, cudaMemcpyDeviceToDevice, s), "restore copy");
+            PWFA_CUDA(cudaMemcpyAsync(in.B[in.bcur][c], dst.B[c], vb, cudaMemcpyDeviceToDevice, s), "restore copy");
+        }
+    }
+    return PWFA_OK;
+}
+
+int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_every) {
+    cudaStream_t s = h->stream;
+    free_recording(in);
+    auto& r = in.rec;
+    r.T = nsteps;
+    r.K = ckpt_every > 0 ? ckpt_every : (int)std::ceil(std::sqrt((double)nsteps));
+    if (r.K > nsteps) r.K = nsteps;
+    r.ncp = (int)((nsteps + r.K - 1) / r.K);
+    const size_t fb = fbytes_of(in), vb = vbytes_of(in);
+    r.cp_stride = fb + 6 * vb;
+    r.seg_stride = fb + 9 * vb;
+    const int64_t N = in.g.N;
+    const size_t adj_bytes = 2 * align_up((size_t)N * kPop * sizeof(float)) + 22 * vb + align_up(sizeof(double) * 260);
+    if (cudaMalloc(&r.cp, r.cp_stride * (r.ncp + 1)) != cudaSuccess ||
+        cudaMalloc(&r.seg, r.seg_stride * r.K) != cudaSuccess || cudaMalloc(&r.adj, adj_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        char buf[200];
+        std::snprintf(buf, sizeof buf, "recording needs %.2f GB (%d checkpoints + %d segment states)",
+                      (r.cp_stride * (r.ncp + 1) + r.seg_stride * r.K + adj_bytes) / 1e9, r.ncp + 1, r.K);
+        free_recording(in);
+        return fail(PWFA_ERR_ALLOC, buf);
+    }
+    int rc = reset_instance(in, s);
+    if (rc) return rc;
+    for (int32_t n = 0; n < nsteps; ++n) {
+        if (n % r.K == 0) {
+            rc = copy_state(in, state_at(in, (char*)r.cp + r.cp_stride * (n / r.K), false), true, s);
+            if (rc) return rc;
+        }
+        rc = step_instance(h, in);
+        if (rc) return rc;
+    }
+    rc = copy_state(in, state_at(in, (char*)r.cp + r.cp_stride * r.ncp, false), true, s);
+    if (rc) return rc;
+    r.valid = true;
+    return PWFA_OK;
+}
+
+int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* host_grad, int32_t n_grad) {
+    cudaStream_t s = h->stream;
+    auto& r = in.rec;
+    if (!r.valid) return fail(PWFA_ERR_STATE, "no recording: call pwfa_lbm_record first");
+    const int np = (int)in.profile.size();
+    if (n_grad < 3 + np) return fail(PWFA_ERR_PARAM, "n_grad must be >= 3 + n_profile");
+    if (np > 256) return fail(PWFA_ERR_PARAM, "the adjoint supports at most 256 profile points");
+    const int64_t N = in.g.N;
+    const size_t vb = vbytes_of(in);
+    const size_t sb = align_up((size_t)N * kPop * sizeof(float));
+    char* p = static_cast<char*>(r.adj);
+    float* Sbar[2] = {(float*)p, (float*)(p + sb)};
+    p += 2 * sb;
+    AdjArgs a{};
+    float* Ebar[3];
+    float* Bbar[3];
+    for (int c = 0; c < 3; ++c) { Ebar[c] = (float*)p; p += vb; }
+    for (int c = 0; c < 3; ++c) { Bbar[c] = (float*)p; p += vb; }
+    for (int c = 0; c < 3; ++c) { a.Bnp[c] = (float*)p; p += vb; }
+    for (int c = 0; c < 3; ++c) { a.Jbar[c] = (float*)p; p += vb; }
+    for (int c = 0; c < 3; ++c) { a.ebar[c] = (float*)p; p += vb; }
+    for (int c = 0; c < 3; ++c) { a.bbar[c] = (float*)p; p += vb; }
+    for (int l = 0; l < 4; ++l) { a.Abnd[l] = (float*)p; p += vb; }
+    double* grad = (double*)p;
+    for (int c = 0; c < 3; ++c) { a.Ebar[c] = Ebar[c]; a.Bbar[c] = Bbar[c]; }
+    a.grad = grad;
+    a.sr = (float)in.p.sigma_r;
+    a.sz = (float)in.p.sigma_z;
+    PWFA_CUDA(cudaMemsetAsync(r.adj, 0, (size_t)(p - (char*)r.adj) + sizeof(double) * 260, s), "cudaMemsetAsync");
+    for (int c = 0; c < 3; ++c)
+        PWFA_CUDA(cudaMemcpyAsync(Ebar[c], seed_E + c * N, sizeof(float) * N, cudaMemcpyDefault, s), "seed copy");
+    int cur = 0;
+    for (int seg = r.ncp - 1; seg >= 0; --seg) {
+        const int64_t s0 = (int64_t)seg * r.K, s1 = std::min<int64_t>(r.T, s0 + r.K);
+        int rc = copy_state(in, state_at(in, (char*)r.cp + r.cp_stride * seg, false), false, s);
+        if (rc) return rc;
+        in.steps = s0;
+        for (int64_t n = s0; n < s1; ++n) {
+            StateRef st = state_at(in, (char*)r.seg + r.seg_stride * (n - s0), true);
+            rc = copy_state(in, st, true, s);
+            if (rc) return rc;
+            rc = step_instance(h, in);
+            if (rc) return rc;
+            for (int c = 0; c < 3; ++c)
+                PWFA_CUDA(cudaMemcpyAsync(st.Bn[c], in.B[in.bcur][c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                          "segment copy");
+        }
+        for (int64_t n = s1 - 1; n >= s0; --n) {
+            StateRef st = state_at(in, (char*)r.seg + r.seg_stride * (n - s0), true);
+            const int64_t keep_steps = in.steps;  // forward arguments of step n
+            in.steps = n;
+            StepArgs f = make_args(in);
+            in.steps = keep_steps;
+            f.fin = st.f;
+            f.fout = nullptr;
+            for (int c = 0; c < 3; ++c) {
+                f.E[c] = st.E[c];
+                f.Bc[c] = st.B[c];
+                f.Bn[c] = st.Bn[c];
+                f.Eout[c] = nullptr;
+                f.J[c] = nullptr;
+            }
+            a.f = f;
+            a.Sbar_in = Sbar[cur];
+            a.Sbar_out = Sbar[1 - cur];
+            PWFA_CUDA(launch_adjoint_step(a, in.p.storage, in.p.collision, s), "adjoint step");
+            cur = 1 - cur;
+        }
+    }
+    PWFA_CUDA(launch_adjoint_profile(in.g, Sbar[cur], (float)in.p.n0, np, in.p.profile_rmax, in.p.dx, grad + 3, s),
+              "profile gradient");
+    PWFA_CUDA(cudaMemcpyAsync(host_grad, grad, sizeof(double) * (3 + np), cudaMemcpyDeviceToHost, s), "grad copy");
+    int rc = copy_state(in, state_at(in, (char*)r.cp + r.cp_stride * r.ncp, false), false, s);
+    if (rc) return rc;
+    in.steps = r.T;
+    PWFA_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return PWFA_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char* pwfa_lbm_last_error(void) { return g_err.c_str(); }
+
+int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckpt_every) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    if (nsteps < 1 || ckpt_every < 0) return fail(PWFA_ERR_PARAM, "nsteps must be >= 1 and ckpt_every >= 0");
+    h->batch_valid = false;
+    return record_instance(h, h->inst[instance], nsteps, ckpt_every);
+}
+
+int pwfa_lbm_adjoint_step(pwfa_lbm_t* h, int32_t instance, const float* seed_E, double* host_grad, int32_t n_grad) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    if (!seed_E || !host_grad) return fail(PWFA_ERR_PARAM, "seed_E and host_grad must not be NULL");
+    h->batch_valid = false;
+    return adjoint_instance(h, h->inst[instance], seed_E, host_grad, n_grad);
+}
 
 int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances, void* cuda_stream, pwfa_lbm_t** out) {
     if (!out) return fail(PWFA_ERR_PARAM, "out is NULL");
@@ -325,6 +685,7 @@ int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances, void* cu
 int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps) {
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
     if (nsteps < 0) return fail(PWFA_ERR_PARAM, "nsteps must be >= 0");
+    if (batch_eligible(h)) return batch_steps(h, nsteps);
     for (int32_t s = 0; s < nsteps; ++s)
         for (auto& in : h->inst) {
             int rc = step_instance(h, in);
@@ -406,6 +767,7 @@ int pwfa_lbm_get_state(pwfa_lbm_t* h, int32_t instance, float* f, float* E, floa
 int pwfa_lbm_set_state(pwfa_lbm_t* h, int32_t instance, const float* f, const float* E, const float* B) {
     int rc = check_instance(h, instance);
     if (rc) return rc;
+    h->batch_valid = false;
     Instance& in = h->inst[instance];
     const int64_t N = in.g.N;
     if (f) {
@@ -472,6 +834,7 @@ int pwfa_lbm_set_launch(pwfa_lbm_t* h, int32_t instance, int32_t bx, int32_t by)
     if (bx < 1 || by < 1 || bx * by > 256) return fail(PWFA_ERR_PARAM, "block shape must satisfy 1 <= bx*by <= 256");
     h->inst[instance].bx = bx;
     h->inst[instance].by = by;
+    h->batch_valid = false;
     return PWFA_OK;
 }
 
@@ -486,7 +849,12 @@ int pwfa_lbm_get_launch(pwfa_lbm_t* h, int32_t instance, int32_t* bx, int32_t* b
 int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
     if (reps < 1) return fail(PWFA_ERR_PARAM, "reps must be >= 1");
-    static const int cand[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+    static const int cand_all[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+    // the batched kernels take tiles of kBatchTile nodes
+    static const int cand_batch[][2] = {{32, 4}, {64, 2}, {128, 1}};
+    const bool batched = batch_eligible(h);
+    const int ncand = batched ? 3 : 7;
+    h->batch_valid = false;
     cudaEvent_t e0, e1;
     PWFA_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
     PWFA_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
@@ -494,7 +862,8 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
     for (auto& in : h->inst) {
         float best = 1e30f;
         int bb[2] = {in.bx, in.by};
-        for (const auto& c : cand) {
+        for (int ci = 0; ci < ncand; ++ci) {
+            const int* c = batched ? cand_batch[ci] : cand_all[ci];
             if (c[0] > 2 * in.g.nx && c[0] > 32) continue;  // mostly idle lanes
             in.bx = c[0];
             in.by = c[1];
@@ -518,6 +887,13 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
     return rc;
 }
 
+int pwfa_lbm_set_batching(pwfa_lbm_t* h, int32_t enable) {
+    if (!h) return fail(PWFA_ERR_PARAM, "null handle");
+    h->batching = enable != 0;
+    h->batch_valid = false;
+    return PWFA_OK;
+}
+
 int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream) {
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
     h->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -532,6 +908,10 @@ int pwfa_lbm_destroy(pwfa_lbm_t* h) {
     if (h->d_partials) cudaFree(h->d_partials);
     if (h->staging) cudaFree(h->staging);
     for (auto& e : h->events) cudaEventDestroy(e);
+    batch_release(h);
+    if (h->d_entries) cudaFree(h->d_entries);
+    if (h->d_steps) cudaFree(h->d_steps);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;
     return PWFA_OK;
 }

@@ -1,12 +1,7 @@
-// Yee FDTD field kernels (Eq. 5 in normalised units, Faraday with Maxwell's
-// sign): dB/dt = -curl E, dE/dt = curl B - J. One thread per node updates
-// the three components stored at that node's index.
-//
-// Staggering: E_x (i+1/2, j, k), E_y (i, j+1/2, k), E_z (i, j, k+1/2);
-// B_x (i, j+1/2, k+1/2), B_y (i+1/2, j, k+1/2), B_z (i+1/2, j+1/2, k).
-// Open grids are closed by perfectly conducting walls: tangential E and
-// normal B on the six outer planes (and components outside the grid) stay 0.
+// Yee FDTD field kernels of one step (bodies in fields_node.cuh) and the
+// wall-zeroing helper used after a state import.
 #include "lbm_kernels.h"
+#include "fields_node.cuh"
 
 namespace pwfa {
 
@@ -16,82 +11,19 @@ constexpr int kBX = 32;
 constexpr int kBY = 8;
 
 template <bool PER>
-__device__ __forceinline__ float at(const Grid& g, const float* a, int i, int j, int k) {
-    if (PER) { i = wrapi(i, g.nx); j = wrapi(j, g.ny); k = wrapi(k, g.nz); }
-    return __ldg(a + ((int64_t)k * g.ny + j) * g.nx + i);
-}
-
-// Bn = Bc - (dt/dx) curl_h E, curl at the face centres.
-template <bool PER>
 __global__ void __launch_bounds__(kBX * kBY) faraday_kernel(const StepArgs a) {
-    const Grid& g = a.g;
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
-    const float c = a.cdt;
-    const float *Ex = a.E[0], *Ey = a.E[1], *Ez = a.E[2];
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    float bx = 0.0f, by = 0.0f, bz = 0.0f;
-    if (PER || (i >= 1 && i <= nx - 2 && j <= ny - 2 && k <= nz - 2)) {
-        const float ez0 = at<PER>(g, Ez, i, j, k), ez1 = at<PER>(g, Ez, i, j + 1, k);
-        const float ey0 = at<PER>(g, Ey, i, j, k), ey1 = at<PER>(g, Ey, i, j, k + 1);
-        bx = __ldg(a.Bc[0] + o) - c * ((ez1 - ez0) - (ey1 - ey0));
-    }
-    if (PER || (i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2)) {
-        const float ex0 = at<PER>(g, Ex, i, j, k), ex1 = at<PER>(g, Ex, i, j, k + 1);
-        const float ez0 = at<PER>(g, Ez, i, j, k), ez1 = at<PER>(g, Ez, i + 1, j, k);
-        by = __ldg(a.Bc[1] + o) - c * ((ex1 - ex0) - (ez1 - ez0));
-    }
-    if (PER || (i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2)) {
-        const float ey0 = at<PER>(g, Ey, i, j, k), ey1 = at<PER>(g, Ey, i + 1, j, k);
-        const float ex0 = at<PER>(g, Ex, i, j, k), ex1 = at<PER>(g, Ex, i, j + 1, k);
-        bz = __ldg(a.Bc[2] + o) - c * ((ey1 - ey0) - (ex1 - ex0));
-    }
-    a.Bn[0][o] = bx;
-    a.Bn[1][o] = by;
-    a.Bn[2][o] = bz;
+    if (i >= a.g.nx || j >= a.g.ny) return;
+    faraday_node<PER>(a, i, j, blockIdx.z);
 }
 
-// E += (dt/dx) curl_h Bn - dt (J_e,edge + J_b), J_e,edge the mean of the two
-// node currents of the edge, J_b,z = -n_b of the rigid driver at t_{n+1}.
 template <bool PER>
 __global__ void __launch_bounds__(kBX * kBY) ampere_kernel(const StepArgs a) {
-    const Grid& g = a.g;
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
-    const float c = a.cdt, dt = a.dt;
-    const float *Bx = a.Bn[0], *By = a.Bn[1], *Bz = a.Bn[2];
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    if (PER || (i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2)) {
-        const float curl = (at<PER>(g, Bz, i, j, k) - at<PER>(g, Bz, i, j - 1, k))
-                         - (at<PER>(g, By, i, j, k) - at<PER>(g, By, i, j, k - 1));
-        const float je = 0.5f * (at<PER>(g, a.J[0], i, j, k) + at<PER>(g, a.J[0], i + 1, j, k));
-        a.Eout[0][o] = a.Eout[0][o] + c * curl - dt * je;
-    }
-    if (PER || (i >= 1 && i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2)) {
-        const float curl = (at<PER>(g, Bx, i, j, k) - at<PER>(g, Bx, i, j, k - 1))
-                         - (at<PER>(g, Bz, i, j, k) - at<PER>(g, Bz, i - 1, j, k));
-        const float je = 0.5f * (at<PER>(g, a.J[1], i, j, k) + at<PER>(g, a.J[1], i, j + 1, k));
-        a.Eout[1][o] = a.Eout[1][o] + c * curl - dt * je;
-    }
-    if (PER || (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2)) {
-        const float curl = (at<PER>(g, By, i, j, k) - at<PER>(g, By, i - 1, j, k))
-                         - (at<PER>(g, Bx, i, j, k) - at<PER>(g, Bx, i, j - 1, k));
-        const float je = 0.5f * (at<PER>(g, a.J[2], i, j, k) + at<PER>(g, a.J[2], i, j, k + 1));
-        float jb = 0.0f;
-        if (a.alpha != 0.0f) {
-            const float xr = ((float)i - 0.5f * (float)(nx - 1)) * a.dx;
-            const float yr = ((float)j - 0.5f * (float)(ny - 1)) * a.dx;
-            const float zeta = ((float)k + 0.5f) * a.dx - a.zc;
-            jb = -a.alpha * expf(-(xr * xr + yr * yr) * a.inv2sr2 - zeta * zeta * a.inv2sz2);
-        }
-        a.Eout[2][o] = a.Eout[2][o] + c * curl - dt * (je + jb);
-    }
+    if (i >= a.g.nx || j >= a.g.ny) return;
+    ampere_node<PER>(a, i, j, blockIdx.z);
 }
 
 __global__ void __launch_bounds__(kBX * kBY) zero_walls_kernel(const StepArgs a) {

@@ -1,0 +1,116 @@
+// Per-node body of the fused fluid step, shared by the single-instance
+// kernel (fluid.cu) and the batched persistent kernel (batch.cu).
+//
+// One thread per node. It pulls the 76 populations of the four advection-
+// diffusion lattices (Eq. 6), takes their moments (Eq. 8) and the relativistic
+// velocity beta(p) (Eq. 2), evaluates the Lorentz source F = -n (E + beta x B)
+// (Eq. 4) with the Yee fields averaged to the node, collides every lattice
+// towards the shared equilibrium of Eq. 9 (BGK Eq. 7, or the regularized
+// variant) adding S_i = w_i F dt (Eq. 10), and stores f* at its own node for
+// the next step's pull. Boundary nodes of open grids take f^eq of their
+// clamped interior node (Eq. 14). It also writes the node current
+// J = -n beta(p*) from the post-collision momentum p* = (A_k + F_k dt)/n,
+// which Ampere's law consumes.
+#pragma once
+
+#include "lbm_node.cuh"
+
+namespace pwfa {
+
+template <int ST, int COLL, bool PER>
+__device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int z) {
+    using T = typename Codec<ST>::T;
+    const Grid& g = a.g;
+    const uint32_t node = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x;
+
+    float f[kL][kQ];
+    bool bnd;
+    gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+
+    float A[kL], nn, beta[3];
+    node_moments(f, a.n_floor, A, nn, beta);
+    const float n = A[0];
+
+    // Lorentz source (Eq. 4): F_0 = 0, F_k = -n (E + beta x B)_k, with B the
+    // mean of its two time levels.
+    float F[3] = {0.0f, 0.0f, 0.0f};
+    if (COLL != 2 && a.couple) {
+        float e[3], bc[3], bn[3];
+        node_E<PER>(g, a.E, x, y, z, e);
+        node_B_sum<PER>(g, a.Bc, x, y, z, bc);
+        node_B_sum<PER>(g, a.Bn, x, y, z, bn);
+        const float b0 = 0.125f * (bc[0] + bn[0]);
+        const float b1 = 0.125f * (bc[1] + bn[1]);
+        const float b2 = 0.125f * (bc[2] + bn[2]);
+        F[0] = -n * (e[0] + beta[1] * b2 - beta[2] * b1);
+        F[1] = -n * (e[1] + beta[2] * b0 - beta[0] * b2);
+        F[2] = -n * (e[2] + beta[0] * b1 - beta[1] * b0);
+    }
+
+    const uint32_t N = (uint32_t)g.N;
+    T* const fo0 = static_cast<T*>(a.fout);
+    T* const fo[kL] = {fo0, fo0 + (size_t)kQ * N, fo0 + (size_t)2 * kQ * N, fo0 + (size_t)3 * kQ * N};
+    const float u[3] = {beta[0] * a.lat, beta[1] * a.lat, beta[2] * a.lat};
+    float phi[kQ];
+    eq_factors(u, phi);
+    if (!PER && bnd) {
+        // Eq. 14: a boundary node holds the equilibrium of the clamped node.
+#pragma unroll
+        for (int l = 0; l < kL; ++l)
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) f[l][q] = A[l] * phi[q];
+    }
+    const float om = a.omega;
+#pragma unroll
+    for (int l = 0; l < kL; ++l) {
+        const float Fl = l == 0 ? 0.0f : F[l - 1] * a.dt;
+        if (COLL == 2) {
+            // streaming only: f* = f
+#pragma unroll
+            for (int q = 0; q < kQ; ++q)
+                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, f[l][q], l == 0 ? wq(q) * a.n0 : 0.0f);
+        } else if (COLL == 0) {
+            // BGK, Eq. 7, plus the source of Eq. 10
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                const float fs = f[l][q] + om * (A[l] * phi[q] - f[l][q]) + wq(q) * Fl;
+                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l == 0 ? wq(q) * a.n0 : 0.0f);
+            }
+        } else {
+            // Regularized: relax only the first Hermite moment of f - f^eq,
+            // Pi = sum_i xi_i (f_i - A phi_i) = sum_i xi_i f_i - A u
+            // (sum_i xi_i phi_i = u exactly for the D3Q19 weights).
+            float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+#pragma unroll
+            for (int q = 1; q < kQ; ++q) {
+                if (xi_x(q) > 0) m0 += f[l][q]; else if (xi_x(q) < 0) m0 -= f[l][q];
+                if (xi_y(q) > 0) m1 += f[l][q]; else if (xi_y(q) < 0) m1 -= f[l][q];
+                if (xi_z(q) > 0) m2 += f[l][q]; else if (xi_z(q) < 0) m2 -= f[l][q];
+            }
+            const float k3 = 3.0f * (1.0f - om);
+            const float P0 = k3 * (m0 - A[l] * u[0]);
+            const float P1 = k3 * (m1 - A[l] * u[1]);
+            const float P2 = k3 * (m2 - A[l] * u[2]);
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                float xp = 0.0f;
+                if (xi_x(q)) xp += (float)xi_x(q) * P0;
+                if (xi_y(q)) xp += (float)xi_y(q) * P1;
+                if (xi_z(q)) xp += (float)xi_z(q) * P2;
+                const float fs = A[l] * phi[q] + wq(q) * (xp + Fl);
+                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l == 0 ? wq(q) * a.n0 : 0.0f);
+            }
+        }
+    }
+
+    // Node current for Ampere: J = -n beta(p*), p* = (A_k + F_k dt) / nn.
+    const float ps0 = (A[1] + F[0] * a.dt) / nn;
+    const float ps1 = (A[2] + F[1] * a.dt) / nn;
+    const float ps2 = (A[3] + F[2] * a.dt) / nn;
+    const float gs = sqrtf(1.0f + ps0 * ps0 + ps1 * ps1 + ps2 * ps2);
+    __stcs(a.J[0] + node, -n * ps0 / gs);
+    __stcs(a.J[1] + node, -n * ps1 / gs);
+    __stcs(a.J[2] + node, -n * ps2 / gs);
+}
+
+}  // namespace pwfa

@@ -59,7 +59,7 @@ EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_
            "pwfa_lbm_set_state", "pwfa_lbm_steps_done", "pwfa_lbm_set_stream",
            "pwfa_lbm_destroy", "pwfa_lbm_last_error", "pwfa_lbm_profile", "pwfa_lbm_kernel_times",
            "pwfa_lbm_set_launch", "pwfa_lbm_get_launch", "pwfa_lbm_autotune",
-           "pwfa_lbm_diag_noalloc")
+           "pwfa_lbm_diag_noalloc", "pwfa_lbm_record", "pwfa_lbm_adjoint_step", "pwfa_lbm_set_batching")
 
 
 def load(build: bool = True):
@@ -93,6 +93,12 @@ def load(build: bool = True):
         lib.pwfa_lbm_diag_noalloc.argtypes = [i32, i32, i32, ctypes.c_double, ctypes.c_double,
                                               vp, vp, vp, vp, vp]
         lib.pwfa_lbm_diag_noalloc.restype = ctypes.c_int
+        lib.pwfa_lbm_record.argtypes = [vp, i32, i32, i32]
+        lib.pwfa_lbm_record.restype = ctypes.c_int
+        lib.pwfa_lbm_adjoint_step.argtypes = [vp, i32, vp, dp, i32]
+        lib.pwfa_lbm_adjoint_step.restype = ctypes.c_int
+        lib.pwfa_lbm_set_batching.argtypes = [vp, i32]
+        lib.pwfa_lbm_set_batching.restype = ctypes.c_int
         lib.pwfa_lbm_last_error.restype = ctypes.c_char_p
         for name in ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_state",
                      "pwfa_lbm_set_state", "pwfa_lbm_set_stream", "pwfa_lbm_destroy",
@@ -234,15 +240,36 @@ class Simulation:
     def autotune(self, reps: int = 3):
         _check(self._lib.pwfa_lbm_autotune(self._h, reps))
 
+    def record(self, nsteps: int, ckpt_every: int = 0, instance: int = 0):
+        """Reset to t = 0 and run nsteps keeping checkpoints for the adjoint."""
+        _check(self._lib.pwfa_lbm_record(self._h, instance, int(nsteps), int(ckpt_every)))
+
+    def adjoint_step(self, seed_E, instance: int = 0) -> np.ndarray:
+        """Gradient of sum(seed_E * E) after the recorded steps with respect to
+        (alpha, sigma_r, sigma_z, profile...). seed_E: [3][z][y][x] float32."""
+        torch = self._torch
+        if isinstance(seed_E, np.ndarray):
+            seed_E = torch.from_numpy(np.ascontiguousarray(seed_E, dtype=np.float32))
+        seed_E = seed_E.contiguous().to(torch.float32)
+        w = self.works[instance]
+        ng = 3 + (0 if w.profile is None else len(w.profile))
+        g = np.zeros(ng, dtype=np.float64)
+        _check(self._lib.pwfa_lbm_adjoint_step(self._h, instance, _ptr(seed_E),
+                                               g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ng))
+        return g
+
     def profile(self, enable: bool = True):
         _check(self._lib.pwfa_lbm_profile(self._h, 1 if enable else 0))
 
-    KERNELS = ("faraday", "fluid", "ampere")
+    KERNELS = ("faraday", "fluid", "ampere", "aux")
+
+    def set_batching(self, enable: bool = True):
+        _check(self._lib.pwfa_lbm_set_batching(self._h, 1 if enable else 0))
 
     def kernel_times(self):
         """(ms, launches) per kernel kind since the previous call."""
-        ms = np.zeros(3, dtype=np.float64)
-        n = np.zeros(3, dtype=np.int64)
+        ms = np.zeros(4, dtype=np.float64)
+        n = np.zeros(4, dtype=np.int64)
         _check(self._lib.pwfa_lbm_kernel_times(
             self._h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
             n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))

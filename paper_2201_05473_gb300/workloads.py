@@ -128,3 +128,19 @@ def integer_populations(shape_zyx):
     if f.max() >= 2 ** 24:
         raise ValueError("grid too large for exact float32 integer populations")
     return f
+
+
+def witness_slab(w: Workload, steps: int, behind: float = 1.5 * 2 * math.pi, radius: float = 1.0):
+    """Witness region of the gradient objective: the single layer of E_z
+    edges (z = (k + 1/2) dx) nearest z_w = z0 + steps dt - behind, over the
+    transverse nodes with r <= radius of the axis (fixed, independent of the
+    driver parameters). Returns (k, mask[ny][nx] bool)."""
+    zw = w.z0 + steps * w.dt - behind
+    k = int(round(zw / w.dx - 0.5))
+    k = min(max(k, 1), w.nz - 2)
+    x = (np.arange(w.nx) - 0.5 * (w.nx - 1)) * w.dx
+    y = (np.arange(w.ny) - 0.5 * (w.ny - 1)) * w.dx
+    mask = (x[None, :] ** 2 + y[:, None] ** 2) <= radius ** 2
+    mask[0, :] = mask[-1, :] = False
+    mask[:, 0] = mask[:, -1] = False
+    return k, mask

@@ -1,0 +1,150 @@
+"""GPU adjoint against the oracle's forward-mode (dual-number) derivatives.
+
+The adjoint gives the full gradient g of L = <seed, E(T)> with respect to
+theta = (alpha, sigma_r, sigma_z, profile...); the oracle gives directional
+derivatives dL.v for a few directions v in FP64, independently of the
+reverse sweep. Bar: relative error <= 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_05473_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2201_05473_gb300 import lbm  # noqa: E402
+
+TOL = 1e-4
+
+
+def oracle_dirderiv(w, steps, dirs, seed):
+    oracle.build()
+    E, dE = oracle.tangent_run(steps, dirs, w.nx, w.ny, w.nz, w.dx, w.dt, w.tau, collision=w.collision,
+                               boundary=w.boundary, couple=w.couple, n0=w.n0, profile=w.profile,
+                               profile_rmax=w.profile_rmax, alpha=w.alpha, sigma_r=w.sigma_r,
+                               sigma_z=w.sigma_z, z0=w.z0, n_floor=w.n_floor)
+    L = float((seed * E).sum())
+    dL = np.array([(seed * dE[k]).sum() for k in range(dirs.shape[0])])
+    return L, dL
+
+
+def directions(np_prof, seed=11):
+    rng = np.random.default_rng(seed)
+    n = 3 + np_prof
+    d = np.zeros((4, n))
+    d[0, 0] = d[1, 1] = d[2, 2] = 1.0
+    if np_prof:
+        d[3, 3:] = rng.standard_normal(np_prof)
+    else:
+        d[3, :3] = rng.standard_normal(3)
+    return d
+
+
+def run_case(w, steps, ckpt, seed_arr, tol=TOL):
+    dirs = directions(0 if w.profile is None else len(w.profile))
+    L_o, dL_o = oracle_dirderiv(w, steps, dirs, seed_arr)
+    with lbm.Simulation(w) as sim:
+        sim.record(steps, ckpt)
+        E = sim.fields(lbm.FIELD_EX | lbm.FIELD_EY | lbm.FIELD_EZ | lbm.RAW_YEE).cpu().numpy().astype(np.float64)
+        L_g = float((seed_arr * E).sum())
+        g = sim.adjoint_step(seed_arr.astype(np.float32))
+        assert sim.steps_done() == steps
+    dL_g = dirs @ g
+    # the loss itself is an FP32 forward value (a local mean of E_z): 1e-4
+    assert abs(L_g - L_o) <= 1e-4 * abs(L_o) + 1e-12, (L_g, L_o)
+    err = np.abs(dL_g - dL_o) / np.maximum(np.abs(dL_o), 1e-30)
+    print("adjoint vs tangent:", dL_g, dL_o, err)
+    assert np.all(err <= tol), (dL_g, dL_o, err)
+    return g
+
+
+def random_seed(w, rng):
+    s = rng.standard_normal((3, w.nz, w.ny, w.nx))
+    return s
+
+
+@pytest.mark.parametrize("collision", [W.BGK, W.REGULARIZED])
+def test_adjoint_periodic_random_functional(collision):
+    w = W.parity_small().replace(nx=12, ny=10, nz=16, boundary=W.PERIODIC, collision=collision, alpha=0.4,
+                                 sigma_r=0.6, sigma_z=0.5, z0=0.8, tau=0.7)
+    rng = np.random.default_rng(2)
+    run_case(w, 30, 7, random_seed(w, rng))
+
+
+@pytest.mark.parametrize("collision", [W.BGK, W.REGULARIZED])
+def test_adjoint_open_with_profile(collision):
+    prof = np.linspace(1.0, 0.7, 8)
+    w = W.parity_small().replace(nx=14, ny=12, nz=24, collision=collision, alpha=0.5, sigma_r=0.5,
+                                 sigma_z=0.5, z0=-1.0, tau=0.6, profile=prof, profile_rmax=1.2)
+    rng = np.random.default_rng(3)
+    run_case(w, 40, 6, random_seed(w, rng))
+
+
+def test_adjoint_witness_loss_config_copy():
+    """Differentiable form on its 64x32x32 copy: n_b/n0 = 0.5, 500 steps,
+    checkpoints every 23 steps, loss -mean E_z on the witness slab 1.5
+    lambda_p behind the driver, 64-point radial profile = 1."""
+    w = W.parity_small().replace(alpha=0.5, profile=np.ones(64), profile_rmax=min(32, 32) * 0.2 / 2)
+    steps = 500
+    k, mask = W.witness_slab(w, steps)
+    seed = np.zeros((3, w.nz, w.ny, w.nx))
+    seed[2, k][mask] = -1.0 / mask.sum()
+    g = run_case(w, steps, 23, seed)
+    assert np.all(np.isfinite(g))
+
+
+def test_autograd_function_matches_adjoint():
+    from paper_2201_05473_gb300.autograd import witness_loss
+    w = W.parity_small().replace(nx=16, ny=16, nz=40, alpha=0.5, z0=-1.0, profile=np.ones(8),
+                                 profile_rmax=1.5)
+    steps = 120
+    theta = torch.tensor([0.5, 0.5, 0.5], dtype=torch.float64, requires_grad=True)
+    prof = torch.ones(8, dtype=torch.float64, requires_grad=True)
+    L = witness_loss(theta, prof, w, steps)
+    L.backward()
+    # same gradient through the raw ABI
+    k, mask = W.witness_slab(w, steps)
+    seed = np.zeros((3, w.nz, w.ny, w.nx), dtype=np.float32)
+    seed[2, k][mask] = -1.0 / mask.sum()
+    with lbm.Simulation(w) as sim:
+        sim.record(steps)
+        g = sim.adjoint_step(seed)
+    assert np.allclose(theta.grad.numpy(), g[:3], rtol=1e-6, atol=1e-12)
+    assert np.allclose(prof.grad.numpy(), g[3:], rtol=1e-6, atol=1e-12)
+
+
+def test_adjoint_against_fp32_finite_differences():
+    """Sanity check: central differences of the FP32 forward (h = 1e-3) agree
+    with the adjoint to ~1e-2 (FP32 noise ~ eps |L| / h)."""
+    w = W.parity_small().replace(nx=16, ny=16, nz=40, alpha=0.5, z0=-1.0)
+    steps = 120
+    k, mask = W.witness_slab(w, steps)
+
+    def loss(alpha):
+        with lbm.Simulation(w.replace(alpha=alpha)) as sim:
+            sim.step(steps)
+            ez = sim.fields(lbm.FIELD_EZ | lbm.RAW_YEE)[0, k].cpu().numpy().astype(np.float64)
+        return -ez[mask].mean()
+
+    seed = np.zeros((3, w.nz, w.ny, w.nx), dtype=np.float32)
+    seed[2, k][mask] = -1.0 / mask.sum()
+    with lbm.Simulation(w) as sim:
+        sim.record(steps)
+        g = sim.adjoint_step(seed)
+    h = 1e-3
+    fd = (loss(0.5 + h) - loss(0.5 - h)) / (2 * h)
+    assert abs(fd - g[0]) <= 2e-2 * abs(g[0]), (fd, g[0])
+
+
+def test_adjoint_requires_recording():
+    w = W.parity_small().replace(nz=16)
+    with lbm.Simulation(w) as sim:
+        with pytest.raises(lbm.LBMError):
+            sim.adjoint_step(np.zeros((3, w.nz, w.ny, w.nx), dtype=np.float32))

@@ -578,3 +578,41 @@ def test_qtilde_paper_values(oracle_mod):
         assert abs(q - float(q_paper)) / float(q_paper) < 0.02, (q, q_paper)
     q, alpha = oracle_mod.qtilde(0.024e-9, 8.9e-6, 8.9e-6, 17.7e-6, 1e22)
     assert abs(alpha - 0.68) < 0.01
+
+
+# ------------------------------------------------- forward-mode derivatives
+def test_tangent_mode_matches_central_differences(oracle_mod):
+    """Dual-number derivatives of E after the coupled step (driver, profile)
+    equal central finite differences of the FP64 primal at h = 1e-3 and 1e-5."""
+    nx, ny, nz, dx = 10, 10, 16, 0.2
+    dt = W.DT_OVER_DX * dx
+    prof = np.ones(8)
+    kw = dict(nx=nx, ny=ny, nz=nz, dx=dx, dt=dt, tau=0.6, profile=prof, profile_rmax=0.9,
+              alpha=0.5, sigma_r=0.5, sigma_z=0.5, z0=-0.5)
+    steps = 40
+    rng = np.random.default_rng(3)
+    dirs = np.zeros((4, 3 + len(prof)))
+    dirs[0, 0] = 1.0           # d/d alpha
+    dirs[1, 1] = 1.0           # d/d sigma_r
+    dirs[2, 2] = 1.0           # d/d sigma_z
+    dirs[3, 3:] = rng.standard_normal(len(prof))  # a profile direction
+    E, dE = oracle_mod.tangent_run(steps, dirs, **kw)
+    o = oracle_mod.Oracle(**kw)
+    o.step(steps)
+    E0, _ = o.get_fields()
+    assert np.array_equal(E, E0)  # same primal on dual numbers
+
+    def primal(theta):
+        a, sr, sz = theta[:3]
+        k = dict(kw, alpha=a, sigma_r=sr, sigma_z=sz, profile=np.array(theta[3:]))
+        oo = oracle_mod.Oracle(**k)
+        oo.step(steps)
+        return oo.get_fields()[0]
+
+    theta0 = np.array([0.5, 0.5, 0.5] + list(prof))
+    for k in range(4):
+        for h in (1e-3, 1e-5):
+            fd = (primal(theta0 + h * dirs[k]) - primal(theta0 - h * dirs[k])) / (2 * h)
+            err = np.linalg.norm(fd - dE[k]) / np.linalg.norm(dE[k])
+            # central differences: truncation O(h^2) at 1e-3, round-off O(eps/h) at 1e-5
+            assert err < (1e-5 if h == 1e-3 else 1e-7), (k, h, err)
