@@ -130,6 +130,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_over_ranks(ms, e2e_s, world, nodes, steps, dist=None, device="cpu"):
+    """Whole-job rates of replicas: every rank advanced its own instance of
+    `nodes` nodes for `steps` steps; the job time is the max over ranks.
+    Returns (GLUPS, e2e GLUPS, max device ms)."""
+    import torch
+    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_max = t.tolist()
+    value = world * nodes * steps / (ms_max * 1e-3) / 1e9
+    e2e = world * nodes * steps / e2e_max / 1e9
+    return value, e2e, ms_max
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -225,6 +239,7 @@ def run_ours(args):
         sim.step(args.warmup)
         sim.autotune(3)
         launch_shape = sim.get_launch()
+        fluid_variant = ["direct", "staged"][sim.get_fluid_variant()]
         sim.kernel_times()  # reset counters
         barrier()
         # ---- value: K steps, device-timed with CUDA events on the stream
@@ -256,9 +271,9 @@ def run_ours(args):
             host_diag = torch.zeros(8, dtype=torch.float64).pin_memory()
             t0 = time.perf_counter()
             sim = lbm.Simulation(w, stream=stream)
+            hd = host_diag.numpy()
             for _ in range(args.steps):
-                sim.step(1)
-                sim.diag_into(host_diag)
+                sim.step_diag(1, out=hd)
             sim.close()
             stream.synchronize()
             e2e_s = time.perf_counter() - t0
@@ -279,6 +294,7 @@ def run_ours(args):
                 e1.record(stream)
                 stream.synchronize()
                 ms2 = e0.elapsed_time(e1)
+                sim.kernel_times()  # reset the counters before the profiled pass
                 sim.profile(True)
                 sim.step(args.steps)
                 k2, l2 = sim.kernel_times()
@@ -292,6 +308,7 @@ def run_ours(args):
                     "ms_per_step": ms2 / args.steps, "bytes_per_node_step": STEP_BYTES[st],
                     "pct_hbm_step": glups * 1e9 * STEP_BYTES[st] / (hbm_peak()[0] * 1e9),
                     "fluid_kernel_GBs": (76 * 2 * 2 + 48) * N / (fl_ms * 1e-3) / 1e9,
+                    "kernel_ms_per_step": {k: k2[k] / max(l2[k], 1) for k in k2 if l2[k]},
                     "finite": bool(d2[7] == 0)}
         # ---- adjoint: the differentiable form (256x128x128, 500 steps,
         # checkpoints every 23 steps, witness loss)
@@ -355,12 +372,7 @@ def run_ours(args):
                           "launches_per_step": sum(lb.values()) / Kb,
                           "unbatched_glups": tot * Kb / (msu * 1e-3) / 1e9, "speedup_vs_unbatched": msu / msb,
                           "nonfinite_instances": int(sum(1 for v in db if v > 0))}
-    ms_t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max, e2e_max = ms_t.tolist()
-    value = world * N * args.steps / (ms_max * 1e-3) / 1e9
-    e2e_val = world * N * args.steps / e2e_max / 1e9
+    value, e2e_val, ms_max = aggregate_over_ranks(ms, e2e_s, world, N, args.steps, dist, "cuda")
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -380,7 +392,7 @@ def run_ours(args):
                    "storage": args.storage,
                    "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * 76 * (4 if w.storage == W.F32 else 2) * N / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "fluid_block": list(launch_shape)},
+                   "fluid_block": list(launch_shape), "fluid_variant": fluid_variant},
         "pct_hbm_step": {"of_" + peak_kind: value * 1e9 * step_bytes / (peak * 1e9),
                          "of_nominal_8000": value * 1e9 * step_bytes / (NOMINAL_HBM_GBS * 1e9),
                          "bytes_per_node_step": step_bytes},
@@ -393,7 +405,8 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": "GLUPS",
                 "h2d_bytes_per_step": lbm.ctypes.sizeof(lbm.Params) / args.steps,
                 "d2h_bytes_per_step": 64,
-                "note": "create from host params + per step pwfa_lbm_step and a D2H read of the FP64 diagnostics"},
+                "note": "create from host params, then per step pwfa_lbm_step_diag (step + fused FP64 "
+                        "diagnostics, D2H into pinned host memory), destroy"},
         "storage_forms": storage_lines or None,
         "adjoint": adjoint_line,
         "batched": batch_line,

@@ -139,6 +139,14 @@ int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckp
 int pwfa_lbm_adjoint_step(pwfa_lbm_t* h, int32_t instance, const float* seed_E, double* host_grad,
                           int32_t n_grad);
 
+/* Advance every instance by nsteps (>= 1) like pwfa_lbm_step and return the
+ * FP64 diagnostics of the state entering the last step, fused into that
+ * step's fluid kernel (no extra pass over the populations): host_diag
+ * receives 8 doubles per instance in the order of pwfa_lbm_fields'
+ * host_diag. Synchronises the stream; PWFA_ERR_UNSTABLE (after filling
+ * host_diag) if an instance has non-finite moments or n < 0. */
+int pwfa_lbm_step_diag(pwfa_lbm_t* h, int32_t nsteps, double* host_diag);
+
 /* Field export masks for pwfa_lbm_fields. */
 #define PWFA_FIELD_N (1u << 0)   /* electron density n = sum of lattice 0 */
 #define PWFA_FIELD_UX (1u << 1)  /* beta_x = p_x / sqrt(1 + p^2) */
@@ -172,6 +180,17 @@ int pwfa_lbm_adjoint_step(pwfa_lbm_t* h, int32_t instance, const float* seed_E, 
 int pwfa_lbm_fields(pwfa_lbm_t* h, int32_t instance, uint32_t mask, float* out,
                     int64_t out_elems, double* host_diag);
 
+/* Line cut and bubble length (Sec. IV observables). out (host or device,
+ * >= 2 nz floats) receives, along z, the electron density n and the
+ * node-averaged E_z at transverse offset r (c/omega_p) from the driver axis
+ * along +x, bilinear between the four surrounding nodes. bubble_length
+ * (nullable, host) receives L_b = dz * #{k : n_k < n_star} on that line: the
+ * paper's bubble length, counted with the threshold n* = 0.95 (pass r = 0
+ * for the axis). Synchronises the stream when out is host memory or
+ * bubble_length is given. */
+int pwfa_lbm_linecut(pwfa_lbm_t* h, int32_t instance, double r, double n_star, float* out, int64_t out_elems,
+                     double* bubble_length);
+
 /* Full state of one instance: pre-collision populations f^n
  * [4][19][z][y][x], raw Yee E (t_{n+1/2}) and B (t_n) [3][z][y][x]. Any of the
  * three pointers may be NULL. Host or device memory. In open mode the
@@ -204,17 +223,28 @@ int pwfa_lbm_profile(pwfa_lbm_t* h, int32_t enable);
 int pwfa_lbm_kernel_times(pwfa_lbm_t* h, double* ms, int64_t* launches);
 
 /* Thread-block shape (bx * by threads, bx along x) of the fused fluid kernel
- * for one instance. bx, by >= 1 and bx * by <= 256; PWFA_ERR_PARAM otherwise. */
+ * for one instance. bx, by >= 1, bx * by a multiple of 32 and at most 256;
+ * PWFA_ERR_PARAM otherwise. */
 int pwfa_lbm_set_launch(pwfa_lbm_t* h, int32_t instance, int32_t bx, int32_t by);
 int pwfa_lbm_get_launch(pwfa_lbm_t* h, int32_t instance, int32_t* bx, int32_t* by);
 
-/* Autotune the fluid kernel's block shape of every instance: time reps
+/* Fluid kernel variants. DIRECT: one thread per node, the 76 pulled values
+ * loaded straight into registers. STAGED (FP32 storage only): persistent
+ * 128-thread tiles, software pipelined: each thread's 76 values of its next
+ * tile arrive in shared memory by cp.async while it computes the current
+ * node; needs bx * by = 128. */
+#define PWFA_FLUID_DIRECT 0
+#define PWFA_FLUID_STAGED 1
+int pwfa_lbm_set_fluid_variant(pwfa_lbm_t* h, int32_t instance, int32_t variant);
+int pwfa_lbm_get_fluid_variant(pwfa_lbm_t* h, int32_t instance, int32_t* variant);
+
+/* Autotune the fluid kernel's block shape and variant of every instance: time reps
  * launches (>= 1) of each candidate shape with CUDA events and keep the
  * fastest. The kernel is re-run on the current state without advancing it,
  * so the simulation state is unchanged. Synchronises the stream. */
 int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps);
 
-/* Batched path, on by default. A handle with several instances that share
+/* Batched path, on by default. A handle with 2..96 instances that share
  * storage, collision, boundary and coupling advances them together: one
  * persistent launch per phase (Faraday, fluid, Ampere) strides over a work
  * list of 128-node tiles of every instance, and two steps at a time are

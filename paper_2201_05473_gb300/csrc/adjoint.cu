@@ -129,7 +129,10 @@ __device__ __forceinline__ int wall_candidates(int v, int n, int out[3]) {
 }
 
 template <int ST, int COLL, bool PER, bool BPASS>
-__global__ void __launch_bounds__(256, 1) adj_fluid_kernel(const AdjArgs a) {
+#ifndef PWFA_ADJ_MIN_BLOCKS
+#define PWFA_ADJ_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(256, PWFA_ADJ_MIN_BLOCKS) adj_fluid_kernel(const AdjArgs a) {
     using T = typename Codec<ST>::T;
     const StepArgs& s = a.f;
     const Grid& g = s.g;
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(256, 1) adj_fluid_kernel(const AdjArgs a) {
                 const int sx = x - xi_x(q), sy = y - xi_y(q), sz = z - xi_z(q);
                 if (!in_grid(g, sx, sy, sz)) continue;
                 const uint32_t so = ((uint32_t)sz * (uint32_t)g.ny + (uint32_t)sy) * (uint32_t)g.nx + (uint32_t)sx;
-                for (int l = 0; l < kL; ++l) a.Sbar_out[(size_t)(l * kQ + q) * N + so] = 0.0f;
+                for (int l = 0; l < kL; ++l) a.Sbar_out[(size_t)l * kQ * N + ((uint32_t)q * N + so)] = 0.0f;
             }
         }
         return;
@@ -161,22 +164,17 @@ __global__ void __launch_bounds__(256, 1) adj_fluid_kernel(const AdjArgs a) {
         zs = min(max(z, 1), g.nz - 2);
     }
     const T* fin = static_cast<const T*>(s.fin);
+    const T* finl[kL] = {fin, fin + (size_t)kQ * N, fin + (size_t)2 * kQ * N, fin + (size_t)3 * kQ * N};
+    const float* Sinl[kL] = {a.Sbar_in, a.Sbar_in + (size_t)kQ * N, a.Sbar_in + (size_t)2 * kQ * N,
+                             a.Sbar_in + (size_t)3 * kQ * N};
+    // (the regularized projection's first moments are not needed: the
+    // transpose of P = k3 (m - A u) with respect to m does not involve m)
     float A[kL] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float m[kL][3];
-    for (int l = 0; l < kL; ++l) m[l][0] = m[l][1] = m[l][2] = 0.0f;
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
         const uint32_t src = (uint32_t)src_index<PER>(g, xs, ys, zs, q);
 #pragma unroll
-        for (int l = 0; l < kL; ++l) {
-            const float v = Codec<ST>::load(fin + (size_t)(l * kQ + q) * N + src, l == 0 ? wq(q) * s.n0 : 0.0f);
-            A[l] += v;
-            if (COLL == 1 && !bnd) {
-                m[l][0] += (float)xi_x(q) * v;
-                m[l][1] += (float)xi_y(q) * v;
-                m[l][2] += (float)xi_z(q) * v;
-            }
-        }
+        for (int l = 0; l < kL; ++l) A[l] += Codec<ST>::load(finl[l] + ((uint32_t)q * N + src), l, q, s.n0);
     }
     const float n = A[0];
     const float nn = n > s.n_floor ? n : s.n_floor;
@@ -227,7 +225,6 @@ __global__ void __launch_bounds__(256, 1) adj_fluid_kernel(const AdjArgs a) {
     float mb[kL][3];
     const float om = s.omega;
     const float k3 = 3.0f * (1.0f - om);
-    const float* Sin = a.Sbar_in;
 #pragma unroll
     for (int l = 0; l < kL; ++l) {
         mb[l][0] = mb[l][1] = mb[l][2] = 0.0f;
@@ -236,7 +233,7 @@ __global__ void __launch_bounds__(256, 1) adj_fluid_kernel(const AdjArgs a) {
         const float wA = (COLL == 0 && !bnd) ? om : ((COLL == 2 && !bnd) ? 0.0f : 1.0f);
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-            const float fsb = Sin[(size_t)(l * kQ + q) * N + node];
+            const float fsb = Sinl[l][(uint32_t)q * N + node];
             Gb += wq(q) * fsb;
             sphi += phi[q] * fsb;
             phib[q] += wA * A[l] * fsb;
@@ -319,18 +316,22 @@ __global__ void __launch_bounds__(256, 1) adj_fluid_kernel(const AdjArgs a) {
                     for (int l = 0; l < kL; ++l) Ab[l] += a.Abnd[l][bo];
                 }
     }
+    // keep the second read of S_bar_in (BGK, stream-only) after the sums
+    // above instead of letting it be hoisted (register pressure)
+    asm volatile("" ::: "memory");
     // transposed pull: f_i(x) = S_i(x - xi_i)  =>  S_bar_i(x - xi_i) = f_bar_i(x)
-    float* Sout = a.Sbar_out;
+    float* const Soutl[kL] = {a.Sbar_out, a.Sbar_out + (size_t)kQ * N, a.Sbar_out + (size_t)2 * kQ * N,
+                              a.Sbar_out + (size_t)3 * kQ * N};
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
         const uint32_t src = (uint32_t)src_index<PER>(g, xs, ys, zs, q);
 #pragma unroll
         for (int l = 0; l < kL; ++l) {
             float fb = Ab[l];
-            if (COLL == 0) fb += (1.0f - om) * Sin[(size_t)(l * kQ + q) * N + node];
-            else if (COLL == 2) fb += Sin[(size_t)(l * kQ + q) * N + node];
+            if (COLL == 0) fb += (1.0f - om) * Sinl[l][(uint32_t)q * N + node];
+            else if (COLL == 2) fb += Sinl[l][(uint32_t)q * N + node];
             else fb += (float)xi_x(q) * mb[l][0] + (float)xi_y(q) * mb[l][1] + (float)xi_z(q) * mb[l][2];
-            Sout[(size_t)(l * kQ + q) * N + src] = fb;
+            Soutl[l][(uint32_t)q * N + src] = fb;
         }
     }
 }

@@ -53,6 +53,7 @@ struct Instance {
     double* d_profile = nullptr;
     int64_t steps = 0;
     int bx = 64, by = 2;  // fluid kernel block shape (pwfa_lbm_autotune refines it)
+    int variant = PWFA_FLUID_DIRECT;  // fluid kernel variant
     // recording for the adjoint: checkpoints every K steps (+ the final
     // state), one segment of per-step states, adjoint scratch
     struct Recording {
@@ -96,6 +97,10 @@ struct pwfa_lbm {
     BatchLaunch blaunch{};
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph2 = nullptr;  // two steps (both parities)
+    // fused per-step diagnostics: per-block records and per-instance results
+    double* d_step_partials = nullptr;
+    int64_t step_partials_cap = 0;
+    double* d_step_diag = nullptr;
 };
 
 namespace {
@@ -166,6 +171,7 @@ StepArgs make_args(const Instance& in) {
     a.dx = (float)p.dx;
     a.bx = in.bx;
     a.by = in.by;
+    a.staged = in.variant == PWFA_FLUID_STAGED && in.p.storage == PWFA_F32 && in.bx * in.by == 128;
     return a;
 }
 
@@ -298,7 +304,7 @@ int reset_instance(Instance& in, cudaStream_t s) {
 
 // ---------------------------------------------------------------- batched
 bool batch_eligible(const pwfa_lbm* h) {
-    if (!h->batching || h->inst.size() < 2) return false;
+    if (!h->batching || h->inst.size() < 2 || h->inst.size() > (size_t)kMaxBatch) return false;
     const auto& p0 = h->inst[0].p;
     for (const auto& in : h->inst)
         if (in.p.storage != p0.storage || in.p.collision != p0.collision || in.p.boundary != p0.boundary ||
@@ -355,6 +361,7 @@ int batch_build(pwfa_lbm* h) {
               "batch table copy");
     PWFA_CUDA(cudaMemcpyAsync(h->d_steps, steps.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream),
               "batch counters copy");
+    PWFA_CUDA(batch_upload_table(ent.data(), n, h->stream), "batch table upload");
     PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     const auto& p0 = h->inst[0].p;
     h->blaunch.entries = h->d_entries;
@@ -377,7 +384,7 @@ int batch_build(pwfa_lbm* h) {
     return PWFA_OK;
 }
 
-int step_instance(pwfa_lbm* h, Instance& in);
+int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag = nullptr);
 
 // One batched step of every instance with the given parity.
 int batch_launch_all(pwfa_lbm* h, int parity, cudaStream_t s, bool timed) {
@@ -434,7 +441,7 @@ int batch_steps(pwfa_lbm* h, int32_t nsteps) {
     return PWFA_OK;
 }
 
-int step_instance(pwfa_lbm* h, Instance& in) {
+int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
     cudaStream_t s = h->stream;
     StepArgs a = make_args(in);
     int rc;
@@ -443,7 +450,7 @@ int step_instance(pwfa_lbm* h, Instance& in) {
         if (rc) return rc;
     }
     rc = timed_launch(h, PWFA_KERNEL_FLUID, "fluid kernel",
-                      [&] { return launch_fluid(a, in.p.storage, in.p.collision, s); });
+                      [&] { return launch_fluid(a, in.p.storage, in.p.collision, s, diag); });
     if (rc) return rc;
     if (in.p.couple) {
         rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere kernel", [&] { return launch_ampere(a, s); });
@@ -506,11 +513,12 @@ int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_ever
     r.ncp = (int)((nsteps + r.K - 1) / r.K);
     const size_t fb = fbytes_of(in), vb = vbytes_of(in);
     r.cp_stride = fb + 6 * vb;
-    r.seg_stride = fb + 9 * vb;
+    r.seg_stride = fb + 6 * vb;  // per step: populations, E, B (plus one trailing B)
     const int64_t N = in.g.N;
     const size_t adj_bytes = 2 * align_up((size_t)N * kPop * sizeof(float)) + 22 * vb + align_up(sizeof(double) * 260);
     if (cudaMalloc(&r.cp, r.cp_stride * (r.ncp + 1)) != cudaSuccess ||
-        cudaMalloc(&r.seg, r.seg_stride * r.K) != cudaSuccess || cudaMalloc(&r.adj, adj_bytes) != cudaSuccess) {
+        cudaMalloc(&r.seg, r.seg_stride * r.K + 3 * vb) != cudaSuccess ||
+        cudaMalloc(&r.adj, adj_bytes) != cudaSuccess) {
         cudaGetLastError();
         char buf[200];
         std::snprintf(buf, sizeof buf, "recording needs %.2f GB (%d checkpoints + %d segment states)",
@@ -568,31 +576,73 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
     int cur = 0;
     for (int seg = r.ncp - 1; seg >= 0; --seg) {
         const int64_t s0 = (int64_t)seg * r.K, s1 = std::min<int64_t>(r.T, s0 + r.K);
-        int rc = copy_state(in, state_at(in, (char*)r.cp + r.cp_stride * seg, false), false, s);
-        if (rc) return rc;
-        in.steps = s0;
-        for (int64_t n = s0; n < s1; ++n) {
-            StateRef st = state_at(in, (char*)r.seg + r.seg_stride * (n - s0), true);
-            rc = copy_state(in, st, true, s);
+        // Segment storage: populations and E of each state j (K slots) and B
+        // of states 0..K (state j's B(t_{n+1}) is state j+1's B).
+        const size_t fbs = fbytes_of(in);
+        char* segp = static_cast<char*>(r.seg);
+        auto f_slot = [&](int64_t j) -> void* { return segp + fbs * j; };
+        auto E_slot = [&](int64_t j, int c) -> float* { return (float*)(segp + fbs * r.K + vb * (3 * j + c)); };
+        auto B_slot = [&](int64_t j, int c) -> float* {
+            return (float*)(segp + fbs * r.K + vb * 3 * r.K + vb * (3 * j + c));
+        };
+        // restore the checkpoint into state 0 of the segment
+        {
+            StateRef cp = state_at(in, (char*)r.cp + r.cp_stride * seg, false);
+            const size_t fb = (size_t)in.g.N * kPop * storage_bytes(in.p.storage);
+            PWFA_CUDA(cudaMemcpyAsync(f_slot(0), cp.f, fb, cudaMemcpyDeviceToDevice, s), "restore copy");
+            for (int c = 0; c < 3; ++c) {
+                PWFA_CUDA(cudaMemcpyAsync(E_slot(0, c), cp.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                          "restore copy");
+                PWFA_CUDA(cudaMemcpyAsync(B_slot(0, c), cp.B[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                          "restore copy");
+            }
+        }
+        // recompute the segment's steps straight into the slots
+        const int64_t len = s1 - s0;
+        for (int64_t j = 0; j < len; ++j) {
+            const int64_t keep_steps = in.steps;
+            in.steps = s0 + j;
+            StepArgs f = make_args(in);
+            in.steps = keep_steps;
+            const bool last = j + 1 == len;
+            f.fin = f_slot(j);
+            f.fout = last ? in.f[1 - in.fcur] : f_slot(j + 1);
+            for (int c = 0; c < 3; ++c) {
+                f.E[c] = E_slot(j, c);
+                f.Bc[c] = B_slot(j, c);
+                f.Bn[c] = B_slot(j + 1, c);
+                f.Eout[c] = last ? in.E[c] : E_slot(j + 1, c);
+                PWFA_CUDA(cudaMemcpyAsync(f.Eout[c], f.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                          "E copy");
+            }
+            if (in.p.couple) {
+                int rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(f, s); });
+                if (rc) return rc;
+            } else {
+                for (int c = 0; c < 3; ++c)
+                    PWFA_CUDA(cudaMemcpyAsync(f.Bn[c], f.Bc[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                              "B copy");
+            }
+            int rc = timed_launch(h, PWFA_KERNEL_FLUID, "fluid kernel",
+                                  [&] { return launch_fluid(f, in.p.storage, in.p.collision, s); });
             if (rc) return rc;
-            rc = step_instance(h, in);
-            if (rc) return rc;
-            for (int c = 0; c < 3; ++c)
-                PWFA_CUDA(cudaMemcpyAsync(st.Bn[c], in.B[in.bcur][c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
-                          "segment copy");
+            if (in.p.couple) {
+                rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere kernel", [&] { return launch_ampere(f, s); });
+                if (rc) return rc;
+            }
         }
         for (int64_t n = s1 - 1; n >= s0; --n) {
-            StateRef st = state_at(in, (char*)r.seg + r.seg_stride * (n - s0), true);
+            const int64_t j = n - s0;
             const int64_t keep_steps = in.steps;  // forward arguments of step n
             in.steps = n;
             StepArgs f = make_args(in);
             in.steps = keep_steps;
-            f.fin = st.f;
+            f.fin = f_slot(j);
             f.fout = nullptr;
             for (int c = 0; c < 3; ++c) {
-                f.E[c] = st.E[c];
-                f.Bc[c] = st.B[c];
-                f.Bn[c] = st.Bn[c];
+                f.E[c] = E_slot(j, c);
+                f.Bc[c] = B_slot(j, c);
+                f.Bn[c] = B_slot(j + 1, c);
                 f.Eout[c] = nullptr;
                 f.J[c] = nullptr;
             }
@@ -613,11 +663,67 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
     return PWFA_OK;
 }
 
+
+
+int ensure_step_diag(pwfa_lbm* h) {
+    int64_t need = 1;
+    for (const auto& in : h->inst) {
+        const int64_t b = (int64_t)((in.g.nx + in.bx - 1) / in.bx) * ((in.g.ny + in.by - 1) / in.by) * in.g.nz;
+        need = std::max(need, b);
+    }
+    if (!h->d_step_diag) {
+        if (cudaMalloc(&h->d_step_diag, sizeof(double) * 8 * h->inst.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics results failed");
+        }
+    }
+    if (need > h->step_partials_cap) {
+        if (h->d_step_partials) cudaFree(h->d_step_partials);
+        h->d_step_partials = nullptr;
+        h->step_partials_cap = 0;
+        if (cudaMalloc(&h->d_step_partials, sizeof(double) * 8 * need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics records failed");
+        }
+        h->step_partials_cap = need;
+    }
+    return PWFA_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char* pwfa_lbm_last_error(void) { return g_err.c_str(); }
+
+int pwfa_lbm_step_diag(pwfa_lbm_t* h, int32_t nsteps, double* host_diag) {
+    if (!h) return fail(PWFA_ERR_PARAM, "null handle");
+    if (nsteps < 1 || !host_diag) return fail(PWFA_ERR_PARAM, "nsteps must be >= 1 and host_diag not NULL");
+    int rc = pwfa_lbm_step(h, nsteps - 1);
+    if (rc) return rc;
+    rc = ensure_step_diag(h);
+    if (rc) return rc;
+    for (size_t i = 0; i < h->inst.size(); ++i) {
+        Instance& in = h->inst[i];
+        DiagOut d{h->d_step_partials, h->step_partials_cap, h->d_step_diag + 8 * i, in.p.dx * in.p.dx * in.p.dx};
+        rc = step_instance(h, in, &d);
+        if (rc) return rc;
+    }
+    h->batch_valid = false;  // the last step ran per instance
+    PWFA_CUDA(cudaMemcpyAsync(host_diag, h->d_step_diag, sizeof(double) * 8 * h->inst.size(),
+                              cudaMemcpyDeviceToHost, h->stream),
+              "cudaMemcpyAsync");
+    PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    for (size_t i = 0; i < h->inst.size(); ++i) {
+        const double* d = host_diag + 8 * i;
+        if (d[7] > 0 || d[5] < 0) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "instance %d unstable: %g non-finite nodes, min n = %g", (int)i, d[7], d[5]);
+            return fail(PWFA_ERR_UNSTABLE, buf);
+        }
+    }
+    return PWFA_OK;
+}
 
 int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckpt_every) {
     int rc = check_instance(h, instance);
@@ -736,6 +842,37 @@ int pwfa_lbm_fields(pwfa_lbm_t* h, int32_t instance, uint32_t mask, float* out, 
     return PWFA_OK;
 }
 
+int pwfa_lbm_linecut(pwfa_lbm_t* h, int32_t instance, double r, double n_star, float* out, int64_t out_elems,
+                     double* bubble_length) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    Instance& in = h->inst[instance];
+    const int nz = in.g.nz;
+    if (!out || out_elems < 2 * (int64_t)nz) return fail(PWFA_ERR_PARAM, "out must hold 2 * nz floats");
+    if (!std::isfinite(r)) return fail(PWFA_ERR_PARAM, "r must be finite");
+    const bool dev = is_device_ptr(out);
+    float* dst = out;
+    const size_t bytes = sizeof(float) * 2 * (size_t)nz;
+    if (!dev || bubble_length) {
+        rc = ensure_staging(h, bytes);
+        if (rc) return rc;
+        dst = static_cast<float*>(h->staging);
+    }
+    PWFA_CUDA(launch_linecut(make_args(in), in.p.storage, r, dst, h->stream), "linecut kernel");
+    if (dst != out) PWFA_CUDA(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDefault, h->stream), "cudaMemcpyAsync");
+    if (bubble_length) {
+        std::vector<float> hn(nz);
+        PWFA_CUDA(cudaMemcpyAsync(hn.data(), dst, sizeof(float) * nz, cudaMemcpyDeviceToHost, h->stream),
+                  "cudaMemcpyAsync");
+        PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        int64_t count = 0;
+        for (int k = 0; k < nz; ++k) count += hn[k] < n_star ? 1 : 0;
+        *bubble_length = count * in.p.dx;
+    }
+    if (!dev) PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return PWFA_OK;
+}
+
 int pwfa_lbm_get_state(pwfa_lbm_t* h, int32_t instance, float* f, float* E, float* B) {
     int rc = check_instance(h, instance);
     if (rc) return rc;
@@ -831,10 +968,29 @@ int pwfa_lbm_kernel_times(pwfa_lbm_t* h, double* ms, int64_t* launches) {
 int pwfa_lbm_set_launch(pwfa_lbm_t* h, int32_t instance, int32_t bx, int32_t by) {
     int rc = check_instance(h, instance);
     if (rc) return rc;
-    if (bx < 1 || by < 1 || bx * by > 256) return fail(PWFA_ERR_PARAM, "block shape must satisfy 1 <= bx*by <= 256");
+    if (bx < 1 || by < 1 || bx * by > 256 || (bx * by) % 32)
+        return fail(PWFA_ERR_PARAM, "block shape must be a multiple of 32 threads, at most 256");
     h->inst[instance].bx = bx;
     h->inst[instance].by = by;
     h->batch_valid = false;
+    return PWFA_OK;
+}
+
+int pwfa_lbm_set_fluid_variant(pwfa_lbm_t* h, int32_t instance, int32_t variant) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    if (variant != PWFA_FLUID_DIRECT && variant != PWFA_FLUID_STAGED) return fail(PWFA_ERR_PARAM, "unknown variant");
+    if (variant == PWFA_FLUID_STAGED && h->inst[instance].p.storage != PWFA_F32)
+        return fail(PWFA_ERR_PARAM, "the staged fluid kernel needs FP32 storage");
+    h->inst[instance].variant = variant;
+    h->batch_valid = false;
+    return PWFA_OK;
+}
+
+int pwfa_lbm_get_fluid_variant(pwfa_lbm_t* h, int32_t instance, int32_t* variant) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    if (variant) *variant = h->inst[instance].variant;
     return PWFA_OK;
 }
 
@@ -849,11 +1005,13 @@ int pwfa_lbm_get_launch(pwfa_lbm_t* h, int32_t instance, int32_t* bx, int32_t* b
 int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
     if (reps < 1) return fail(PWFA_ERR_PARAM, "reps must be >= 1");
-    static const int cand_all[][2] = {{32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+    // {bx, by, variant}: direct shapes, then the staged kernel's 128-thread tiles
+    static const int cand_all[][3] = {{32, 4, 0}, {32, 8, 0}, {64, 2, 0}, {64, 4, 0}, {128, 1, 0}, {128, 2, 0},
+                                      {256, 1, 0}, {32, 4, 1}, {64, 2, 1}, {128, 1, 1}};
     // the batched kernels take tiles of kBatchTile nodes
-    static const int cand_batch[][2] = {{32, 4}, {64, 2}, {128, 1}};
+    static const int cand_batch[][3] = {{32, 4, 0}, {64, 2, 0}, {128, 1, 0}};
     const bool batched = batch_eligible(h);
-    const int ncand = batched ? 3 : 7;
+    const int ncand = batched ? 3 : 10;
     h->batch_valid = false;
     cudaEvent_t e0, e1;
     PWFA_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
@@ -861,12 +1019,14 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
     int rc = PWFA_OK;
     for (auto& in : h->inst) {
         float best = 1e30f;
-        int bb[2] = {in.bx, in.by};
+        int bb[3] = {in.bx, in.by, in.variant};
         for (int ci = 0; ci < ncand; ++ci) {
             const int* c = batched ? cand_batch[ci] : cand_all[ci];
             if (c[0] > 2 * in.g.nx && c[0] > 32) continue;  // mostly idle lanes
+            if (c[2] == PWFA_FLUID_STAGED && in.p.storage != PWFA_F32) continue;
             in.bx = c[0];
             in.by = c[1];
+            in.variant = c[2];
             StepArgs a = make_args(in);
             cudaError_t e = launch_fluid(a, in.p.storage, in.p.collision, h->stream);  // warm
             if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
@@ -876,10 +1036,11 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
             float ms = 0.0f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (e != cudaSuccess) { rc = cuda_fail(e, "autotune"); break; }
-            if (ms < best) { best = ms; bb[0] = c[0]; bb[1] = c[1]; }
+            if (ms < best) { best = ms; bb[0] = c[0]; bb[1] = c[1]; bb[2] = c[2]; }
         }
         in.bx = bb[0];
         in.by = bb[1];
+        in.variant = bb[2];
         if (rc) break;
     }
     cudaEventDestroy(e0);
@@ -911,6 +1072,8 @@ int pwfa_lbm_destroy(pwfa_lbm_t* h) {
     batch_release(h);
     if (h->d_entries) cudaFree(h->d_entries);
     if (h->d_steps) cudaFree(h->d_steps);
+    if (h->d_step_partials) cudaFree(h->d_step_partials);
+    if (h->d_step_diag) cudaFree(h->d_step_diag);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;
     return PWFA_OK;

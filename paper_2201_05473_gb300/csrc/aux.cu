@@ -41,15 +41,19 @@ __global__ void init_kernel(Grid g, typename Codec<ST>::T* f, float n0, const do
     int x, y, z;
     node_xyz(g, node, x, y, z);
     const double xc = 0.5 * (g.nx - 1) * dx, yc = 0.5 * (g.ny - 1) * dx;
-#pragma unroll 1
+#pragma unroll
     for (int q = 0; q < kQ; ++q) {
-        int sx = x + xi_x(q), sy = y + xi_y(q);
-        if (g.periodic) { sx = wrapi(sx, g.nx); sy = wrapi(sy, g.ny); }
-        else { sx = min(max(sx, 1), g.nx - 2); sy = min(max(sy, 1), g.ny - 2); }
-        const double rx = sx * dx - xc, ry = sy * dx - yc;
-        const double n = (double)n0 * profile_at(prof, np, rmax, sqrt(rx * rx + ry * ry));
-        Codec<ST>::store(f + (int64_t)q * g.N + node, (float)(wq(q) * n), wq(q) * n0);
-        for (int l = 1; l < kL; ++l) Codec<ST>::store(f + (int64_t)(l * kQ + q) * g.N + node, 0.0f, 0.0f);
+        float n = n0;
+        if (np > 0) {  // FP64 only where a profile is given
+            int sx = x + xi_x(q), sy = y + xi_y(q);
+            if (g.periodic) { sx = wrapi(sx, g.nx); sy = wrapi(sy, g.ny); }
+            else { sx = min(max(sx, 1), g.nx - 2); sy = min(max(sy, 1), g.ny - 2); }
+            const double rx = sx * dx - xc, ry = sy * dx - yc;
+            n = (float)((double)n0 * profile_at(prof, np, rmax, sqrt(rx * rx + ry * ry)));
+        }
+        Codec<ST>::store(f + (int64_t)q * g.N + node, wq(q) * n, 0, q, n0);
+#pragma unroll
+        for (int l = 1; l < kL; ++l) Codec<ST>::store(f + (int64_t)(l * kQ + q) * g.N + node, 0.0f, l, q, n0);
     }
 }
 
@@ -94,8 +98,7 @@ __global__ void import_f_kernel(Grid g, const float* in, typename Codec<ST>::T* 
         else { sx = min(max(sx, 0), g.nx - 1); sy = min(max(sy, 0), g.ny - 1); sz = min(max(sz, 0), g.nz - 1); }
         const int64_t src = ((int64_t)sz * g.ny + sy) * g.nx + sx;
         for (int l = 0; l < kL; ++l)
-            Codec<ST>::store(f + (int64_t)(l * kQ + q) * g.N + node, in[(int64_t)(l * kQ + q) * g.N + src],
-                             l == 0 ? wq(q) * n0 : 0.0f);
+            Codec<ST>::store(f + (int64_t)(l * kQ + q) * g.N + node, in[(int64_t)(l * kQ + q) * g.N + src], l, q, n0);
     }
 }
 
@@ -132,6 +135,39 @@ __global__ void __launch_bounds__(kBX * kBY) export_fields_kernel(const StepArgs
     int slot = 0;
     for (int bit = 0; bit < 16; ++bit)
         if (mask & (1u << bit)) out[(int64_t)(slot++) * g.N + node] = vals[bit];
+}
+
+// ---------------------------------------------------------------- line cuts
+// Values along z at transverse offset r (c/omega_p) from the axis in +x,
+// bilinear between the four nodes around (x_c + r, y_c): slot 0 density n,
+// slot 1 node-averaged E_z (each thread one z).
+template <int ST, bool PER>
+__global__ void linecut_kernel(const StepArgs a, double xr, float* out) {
+    using T = typename Codec<ST>::T;
+    const Grid& g = a.g;
+    const int z = blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= g.nz) return;
+    const double xs = xr / a.dx + 0.5 * (g.nx - 1), ys = 0.5 * (g.ny - 1);
+    int x0 = (int)floor(xs), y0 = (int)floor(ys);
+    x0 = min(max(x0, 0), g.nx - 2);
+    y0 = min(max(y0, 0), g.ny - 2);
+    const float fx = (float)(xs - x0), fy = (float)(ys - y0);
+    float nsum = 0.0f, esum = 0.0f;
+    for (int c = 0; c < 4; ++c) {
+        const int x = x0 + (c & 1), y = y0 + (c >> 1);
+        const float wgt = ((c & 1) ? fx : 1.0f - fx) * ((c >> 1) ? fy : 1.0f - fy);
+        float f[kL][kQ];
+        bool bnd;
+        gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+        float A[kL], nn, beta[3];
+        node_moments(f, a.n_floor, A, nn, beta);
+        float e[3];
+        node_E<PER>(g, a.E, x, y, z, e);
+        nsum += wgt * A[0];
+        esum += wgt * e[2];
+    }
+    out[z] = nsum;
+    out[g.nz + z] = esum;
 }
 
 // ---------------------------------------------------------------- diagnostics
@@ -204,10 +240,10 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const StepArgs a, do
     diag_block_reduce(d, partials + 8 * (int64_t)blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kDiagThreads) diag_finish_kernel(const double* partials, int nparts, double* out) {
+__global__ void __launch_bounds__(kDiagThreads) diag_finish_kernel(const double* partials, int64_t nparts, double* out) {
     Diag d{0, 0, 0, 0, 0, 1e300, 0, 0};
-    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
-        const double* p = partials + 8 * (int64_t)b;
+    for (int64_t b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const double* p = partials + 8 * b;
         diag_combine(d, Diag{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7]});
     }
     diag_block_reduce(d, out);
@@ -216,6 +252,11 @@ __global__ void __launch_bounds__(kDiagThreads) diag_finish_kernel(const double*
 dim3 node_grid(const Grid& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz); }
 
 }  // namespace
+
+cudaError_t launch_diag_finish(const double* partials, int64_t nparts, double* out, cudaStream_t s) {
+    diag_finish_kernel<<<1, kDiagThreads, 0, s>>>(partials, nparts, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init(const Grid& g, void* f, int storage, float n0, const double* d_profile, int n_profile,
                         double profile_rmax, double dx, cudaStream_t s) {
@@ -261,6 +302,19 @@ cudaError_t launch_export_fields(const StepArgs& a, int storage, unsigned mask, 
         case 0: if (per) export_fields_kernel<0, true><<<grid, block, 0, s>>>(a, mask, out); else export_fields_kernel<0, false><<<grid, block, 0, s>>>(a, mask, out); break;
         case 1: if (per) export_fields_kernel<1, true><<<grid, block, 0, s>>>(a, mask, out); else export_fields_kernel<1, false><<<grid, block, 0, s>>>(a, mask, out); break;
         case 2: if (per) export_fields_kernel<2, true><<<grid, block, 0, s>>>(a, mask, out); else export_fields_kernel<2, false><<<grid, block, 0, s>>>(a, mask, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_linecut(const StepArgs& a, int storage, double r, float* out, cudaStream_t s) {
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((a.g.nz + threads - 1) / threads);
+    const bool per = a.g.periodic;
+    switch (storage) {
+        case 0: if (per) linecut_kernel<0, true><<<blocks, threads, 0, s>>>(a, r, out); else linecut_kernel<0, false><<<blocks, threads, 0, s>>>(a, r, out); break;
+        case 1: if (per) linecut_kernel<1, true><<<blocks, threads, 0, s>>>(a, r, out); else linecut_kernel<1, false><<<blocks, threads, 0, s>>>(a, r, out); break;
+        case 2: if (per) linecut_kernel<2, true><<<blocks, threads, 0, s>>>(a, r, out); else linecut_kernel<2, false><<<blocks, threads, 0, s>>>(a, r, out); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -2,8 +2,8 @@
 // one persistent launch per phase (Faraday, fused fluid, Ampere) over a
 // flattened work list of (instance, tile) items, replayed from a captured
 // CUDA graph. Each tile is 128 nodes of one z-plane in the instance's
-// autotuned shape (bx x by, bx * by = 128). CTAs stride over the items
-// (item = blockIdx.x, blockIdx.x + gridDim.x, ...): no inter-CTA waits.
+// autotuned shape (bx x by, bx * by = 128). CTAs take the items
+// in contiguous chunks: no inter-CTA waits.
 #include "lbm_batch.h"
 #include "fields_node.cuh"
 #include "fluid_node.cuh"
@@ -13,15 +13,6 @@ namespace pwfa {
 namespace {
 
 constexpr int kThreads = kBatchTile;
-
-// Copy one item's arguments into shared memory (all threads of the CTA work
-// on the same item).
-__device__ __forceinline__ void load_args(const BatchEntry& e, int parity, StepArgs& sa) {
-    const int nwords = (int)(sizeof(StepArgs) / sizeof(int));
-    const int* src = reinterpret_cast<const int*>(&e.args[parity]);
-    int* dst = reinterpret_cast<int*>(&sa);
-    for (int w = threadIdx.x; w < nwords; w += blockDim.x) dst[w] = src[w];
-}
 
 __device__ __forceinline__ int find_instance(const BatchEntry* ent, int ninst, int64_t item) {
     int lo = 0, hi = ninst - 1;
@@ -33,35 +24,55 @@ __device__ __forceinline__ int find_instance(const BatchEntry* ent, int ninst, i
     return lo;
 }
 
+// The instance table lives in constant memory: every thread of a CTA reads
+// the same entry (broadcast), so no shared-memory copy and no barrier is
+// needed anywhere in the kernel.
+__constant__ BatchEntry c_entries[kMaxBatch];
+
+// Resident blocks per SM: the fluid phase needs up to 128 registers (4 blocks
+// of 128 threads); the light field phases run 8 blocks (64 registers).
+template <int PHASE>
+struct PhaseOcc {
+    static constexpr int blocks = PHASE == 1 ? 4 : 8;
+};
+
+// Each CTA owns one contiguous chunk of the work list, so it crosses an
+// instance boundary at most a few times; consecutive items of the same
+// instance run back to back.
 template <int ST, int COLL, bool PER, int PHASE>
-__global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchEntry* __restrict__ ent, int ninst,
-                                                             int64_t nitems, int parity) {
-    __shared__ StepArgs sa;
-    __shared__ int s_inst;
-    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-        if (threadIdx.x == 0) s_inst = find_instance(ent, ninst, item);
-        __syncthreads();
-        const BatchEntry& e = ent[s_inst];
-        load_args(e, parity, sa);
-        __syncthreads();
-        if (PHASE == 2) {
-            if (threadIdx.x == 0) sa.zc = (float)(e.z0 + (double)(*e.step + 1) * e.dt);
-            __syncthreads();
+__global__ void __launch_bounds__(kThreads, PhaseOcc<PHASE>::blocks) batch_kernel(int ninst, int64_t nitems,
+                                                                                  int parity) {
+    const int64_t per = (nitems + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * per;
+    const int64_t i1 = i0 + per < nitems ? i0 + per : nitems;
+    int inst = 0;
+    int64_t begin = 0, end = 0;  // item range of the current instance
+    int tiles_x = 1, per_plane = 1, bx = 1;
+    float zc = 0.0f;
+    for (int64_t item = i0; item < i1; ++item) {
+        if (item >= end) {
+            inst = find_instance(c_entries, ninst, item);
+            const BatchEntry& e = c_entries[inst];
+            begin = e.item_begin;
+            end = inst + 1 < ninst ? c_entries[inst + 1].item_begin : nitems;
+            tiles_x = e.tiles_x;
+            per_plane = e.tiles_x * e.tiles_y;
+            bx = e.bx;
+            if (PHASE == 2) zc = (float)(e.z0 + (double)(*e.step + 1) * e.dt);
         }
-        const int64_t local = item - e.item_begin;
-        const int per_plane = e.tiles_x * e.tiles_y;
+        const StepArgs& a = c_entries[inst].args[parity];
+        const int64_t local = item - begin;
         const int z = (int)(local / per_plane);
         const int r = (int)(local - (int64_t)z * per_plane);
-        const int ty = r / e.tiles_x;
-        const int tx = r - ty * e.tiles_x;
-        const int x = tx * e.bx + (int)threadIdx.x % e.bx;
-        const int y = ty * e.by + (int)threadIdx.x / e.bx;
-        if (x < sa.g.nx && y < sa.g.ny) {
-            if (PHASE == 0) faraday_node<PER>(sa, x, y, z);
-            else if (PHASE == 1) fluid_node<ST, COLL, PER>(sa, x, y, z);
-            else ampere_node<PER>(sa, x, y, z);
+        const int ty = r / tiles_x;
+        const int tx = r - ty * tiles_x;
+        const int x = tx * bx + (int)threadIdx.x % bx;
+        const int y = ty * (kThreads / bx) + (int)threadIdx.x / bx;
+        if (x < a.g.nx && y < a.g.ny) {
+            if (PHASE == 0) faraday_node<PER>(a, x, y, z);
+            else if (PHASE == 1) fluid_node<ST, COLL, PER>(a, x, y, z);
+            else ampere_node<PER>(a, x, y, z, zc);
         }
-        __syncthreads();
     }
 }
 
@@ -72,10 +83,12 @@ __global__ void batch_advance_kernel(const BatchEntry* ent, int ninst) {
 
 template <int ST, int COLL, bool PER>
 cudaError_t launch_phase(const BatchLaunch& b, int phase, int parity, cudaStream_t s) {
+    const int g1 = b.grid;                                     // fluid phase
+    const int gf = b.grid / PhaseOcc<1>::blocks * PhaseOcc<0>::blocks;  // field phases
     switch (phase) {
-        case 0: batch_kernel<ST, COLL, PER, 0><<<b.grid, kThreads, 0, s>>>(b.entries, b.ninst, b.nitems, parity); break;
-        case 1: batch_kernel<ST, COLL, PER, 1><<<b.grid, kThreads, 0, s>>>(b.entries, b.ninst, b.nitems, parity); break;
-        case 2: batch_kernel<ST, COLL, PER, 2><<<b.grid, kThreads, 0, s>>>(b.entries, b.ninst, b.nitems, parity); break;
+        case 0: batch_kernel<ST, COLL, PER, 0><<<gf, kThreads, 0, s>>>(b.ninst, b.nitems, parity); break;
+        case 1: batch_kernel<ST, COLL, PER, 1><<<g1, kThreads, 0, s>>>(b.ninst, b.nitems, parity); break;
+        case 2: batch_kernel<ST, COLL, PER, 2><<<gf, kThreads, 0, s>>>(b.ninst, b.nitems, parity); break;
         default: batch_advance_kernel<<<(b.ninst + 127) / 128, 128, 0, s>>>(b.entries, b.ninst); break;
     }
     return cudaGetLastError();
@@ -107,6 +120,11 @@ cudaError_t launch_batch_phase(const BatchLaunch& b, int phase, int parity, int 
         case 2: return launch_phase_c<2>(b, phase, parity, collision, periodic, s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_upload_table(const BatchEntry* host, int n, cudaStream_t s) {
+    if (n > kMaxBatch) return cudaErrorInvalidValue;
+    return cudaMemcpyToSymbolAsync(c_entries, host, sizeof(BatchEntry) * n, 0, cudaMemcpyHostToDevice, s);
 }
 
 cudaError_t batch_grid_size(int storage, int collision, bool periodic, int* grid) {

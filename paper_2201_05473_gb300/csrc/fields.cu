@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kBX * kBY) ampere_kernel(const StepArgs a) {
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
     if (i >= a.g.nx || j >= a.g.ny) return;
-    ampere_node<PER>(a, i, j, blockIdx.z);
+    ampere_node<PER>(a, i, j, blockIdx.z, a.zc);
 }
 
 __global__ void __launch_bounds__(kBX * kBY) zero_walls_kernel(const StepArgs a) {

@@ -52,7 +52,7 @@ __device__ __forceinline__ void faraday_node(const StepArgs& a, int i, int j, in
 // E += (dt/dx) curl_h Bn - dt (J_e,edge + J_b), J_e,edge the mean of the two
 // node currents of the edge, J_b,z = -n_b of the rigid driver at t_{n+1}.
 template <bool PER>
-__device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int k) {
+__device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int k, float zc) {
     const Grid& g = a.g;
     const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
     const float c = a.cdt, dt = a.dt;
@@ -78,7 +78,7 @@ __device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int
         if (a.alpha != 0.0f) {
             const float xr = ((float)i - 0.5f * (float)(nx - 1)) * a.dx;
             const float yr = ((float)j - 0.5f * (float)(ny - 1)) * a.dx;
-            const float zeta = ((float)k + 0.5f) * a.dx - a.zc;
+            const float zeta = ((float)k + 0.5f) * a.dx - zc;
             jb = -a.alpha * expf(-(xr * xr + yr * yr) * a.inv2sr2 - zeta * zeta * a.inv2sz2);
         }
         a.Eout[2][o] = a.Eout[2][o] + c * curl - dt * (je + jb);

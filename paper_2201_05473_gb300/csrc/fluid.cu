@@ -4,6 +4,8 @@
 // Memory traffic per node: 76 population reads + 76 writes (FP32: 608 B),
 // E (one edge per component) + two B time levels (36 B) read, J (12 B)
 // written; neighbouring edge/face reads hit L1/L2.
+#include <algorithm>
+
 #include "lbm_kernels.h"
 #include "fluid_node.cuh"
 
@@ -26,34 +28,215 @@ __global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
     fluid_node<ST, COLL, PER>(a, x, y, blockIdx.z);
 }
 
+// The same step with the FP64 diagnostics of the entering state fused in:
+// each block writes one record (sum n, sum n p_k, field energy, min n,
+// max |beta|, non-finite count) to partials[block]; launch_diag_finish
+// reduces the records.
+template <int ST, int COLL, bool PER>
+__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
+    fluid_diag_kernel(const StepArgs a, double dxcube, double* partials) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    // per-node values and the warp-level reduction in FP32 (FP64 is slow on
+    // this part); warps are combined in FP64 by one thread per block
+    float v[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 3.0e38f, 0.0f, 0.0f};
+    if (x < a.g.nx && y < a.g.ny) {
+        NodeDiag nd;
+        fluid_node<ST, COLL, PER, true>(a, x, y, z, &nd);
+        const int64_t o = ((int64_t)z * a.g.ny + y) * a.g.nx + x;
+        float e2 = 0.0f;
+        for (int c = 0; c < 3; ++c) {
+            const float ev = __ldg(a.E[c] + o), bv = __ldg(a.Bc[c] + o);
+            e2 += ev * ev + bv * bv;
+        }
+        const bool fin = isfinite(nd.n) && isfinite(nd.a1) && isfinite(nd.a2) && isfinite(nd.a3);
+        v[0] = nd.n; v[1] = nd.a1; v[2] = nd.a2; v[3] = nd.a3;
+        v[4] = 0.5f * e2;
+        v[5] = nd.n;
+        v[6] = sqrtf(nd.beta2);
+        v[7] = fin ? 0.0f : 1.0f;
+    }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    __shared__ double sh[PWFA_FLUID_MAX_THREADS / 32][8];
+    for (int off = 16; off > 0; off >>= 1) {
+        for (int c = 0; c < 8; ++c) {
+            const float o2 = __shfl_down_sync(0xffffffffu, v[c], off);
+            if (c == 5) v[c] = fminf(v[c], o2);
+            else if (c == 6) v[c] = fmaxf(v[c], o2);
+            else v[c] += o2;
+        }
+    }
+    if ((tid & 31) == 0)
+        for (int c = 0; c < 8; ++c) sh[tid >> 5][c] = (double)v[c];
+    __syncthreads();
+    if (tid == 0) {
+        double d[8];
+        for (int c = 0; c < 8; ++c) d[c] = sh[0][c];
+        for (int w = 1; w < (nthr + 31) / 32; ++w)
+            for (int c = 0; c < 8; ++c) {
+                if (c == 5) d[c] = fmin(d[c], sh[w][c]);
+                else if (c == 6) d[c] = fmax(d[c], sh[w][c]);
+                else d[c] += sh[w][c];
+            }
+        d[4] *= dxcube;
+        if (d[5] >= 3.0e38) d[5] = 1e300;
+        const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        for (int c = 0; c < 8; ++c) partials[8 * b + c] = d[c];
+    }
+}
+
+// ---------------------------------------------------------------- staged
+// Software-pipelined variant (FP32 storage): persistent CTAs of 128 threads
+// walk the node tiles; while a thread computes its node of tile k from
+// registers, the 76 pulled populations of its node of tile k+1 are already
+// in flight into its own column of shared memory through 4-byte cp.async
+// copies. A thread reads back only the values it copied itself, so the only
+// wait is cp.async.wait_group on its own copies (no barrier, no spin).
+constexpr int kStageThreads = 128;
+
+__device__ __forceinline__ void cp_async4(uint32_t smem, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct TileNode {
+    int x, y, z;
+    bool valid;
+};
+
+__device__ __forceinline__ TileNode tile_node(const StepArgs& a, int64_t tile, int tiles_x, int tiles_y) {
+    const int64_t per_plane = (int64_t)tiles_x * tiles_y;
+    const int z = (int)(tile / per_plane);
+    const int r = (int)(tile - (int64_t)z * per_plane);
+    const int ty = r / tiles_x;
+    const int tx = r - ty * tiles_x;
+    TileNode n;
+    n.x = tx * a.bx + (int)threadIdx.x % a.bx;
+    n.y = ty * (kStageThreads / a.bx) + (int)threadIdx.x / a.bx;
+    n.z = z;
+    n.valid = n.x < a.g.nx && n.y < a.g.ny;
+    return n;
+}
+
+template <bool PER>
+__device__ __forceinline__ void stage_copies(const StepArgs& a, const TileNode& n, uint32_t col) {
+    const Grid& g = a.g;
+    int xs = n.x, ys = n.y, zs = n.z;
+    if (!PER) {
+        xs = min(max(n.x, 1), g.nx - 2);
+        ys = min(max(n.y, 1), g.ny - 2);
+        zs = min(max(n.z, 1), g.nz - 2);
+    }
+    const float* fin = static_cast<const float*>(a.fin);
+    const uint32_t N = (uint32_t)g.N;
+    const float* fl[kL] = {fin, fin + (size_t)kQ * N, fin + (size_t)2 * kQ * N, fin + (size_t)3 * kQ * N};
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        const uint32_t off = (uint32_t)q * N + (uint32_t)src_index<PER>(g, xs, ys, zs, q);
+#pragma unroll
+        for (int l = 0; l < kL; ++l)
+            cp_async4(col + 4u * (uint32_t)((l * kQ + q) * kStageThreads), fl[l] + off);
+    }
+}
+
+template <int COLL, bool PER>
+__global__ void __launch_bounds__(kStageThreads, 4) fluid_staged_kernel(const StepArgs a, int tiles_x, int tiles_y,
+                                                                         int64_t ntiles) {
+    extern __shared__ float stage[];  // [76][kStageThreads]
+    const uint32_t col = (uint32_t)__cvta_generic_to_shared(stage + threadIdx.x);
+    int64_t tile = blockIdx.x;
+    TileNode cur = tile_node(a, tile, tiles_x, tiles_y);
+    if (tile < ntiles && cur.valid) stage_copies<PER>(a, cur, col);
+    cp_async_commit();
+    while (tile < ntiles) {
+        cp_async_wait_all();
+        float f[kL][kQ];
+#pragma unroll
+        for (int l = 0; l < kL; ++l)
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) f[l][q] = stage[(l * kQ + q) * kStageThreads + threadIdx.x];
+        const int64_t nxt = tile + gridDim.x;
+        const TileNode nn = tile_node(a, nxt, tiles_x, tiles_y);
+        if (nxt < ntiles && nn.valid) stage_copies<PER>(a, nn, col);
+        cp_async_commit();
+        if (cur.valid) {
+            bool bnd = false;
+            if (!PER)
+                bnd = cur.x == 0 || cur.y == 0 || cur.z == 0 || cur.x == a.g.nx - 1 || cur.y == a.g.ny - 1 ||
+                      cur.z == a.g.nz - 1;
+            fluid_compute<0, COLL, PER>(a, cur.x, cur.y, cur.z, f, bnd);
+        }
+        tile = nxt;
+        cur = nn;
+    }
+}
+
+template <int COLL>
+cudaError_t launch_staged_t(const StepArgs& a, cudaStream_t s) {
+    const int bx = a.bx;
+    if (bx <= 0 || kStageThreads % bx) return cudaErrorInvalidConfiguration;
+    const int by = kStageThreads / bx;
+    const int tiles_x = (a.g.nx + bx - 1) / bx, tiles_y = (a.g.ny + by - 1) / by;
+    const int64_t ntiles = (int64_t)tiles_x * tiles_y * a.g.nz;
+    static int grid_cache[2] = {0, 0};
+    int& grid = grid_cache[a.g.periodic ? 1 : 0];
+    const size_t smem = sizeof(float) * kPop * kStageThreads;
+    if (grid == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = a.g.periodic
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_staged_kernel<COLL, true>, kStageThreads, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_staged_kernel<COLL, false>, kStageThreads, smem);
+        if (e != cudaSuccess) return e;
+        grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int blocks = (int)std::min<int64_t>(grid, ntiles);
+    if (a.g.periodic) fluid_staged_kernel<COLL, true><<<blocks, kStageThreads, smem, s>>>(a, tiles_x, tiles_y, ntiles);
+    else fluid_staged_kernel<COLL, false><<<blocks, kStageThreads, smem, s>>>(a, tiles_x, tiles_y, ntiles);
+    return cudaGetLastError();
+}
+
 template <int ST, int COLL>
-cudaError_t launch_fluid_t(const StepArgs& a, cudaStream_t s) {
+cudaError_t launch_fluid_t(const StepArgs& a, cudaStream_t s, const DiagOut* d) {
+    if (ST == 0 && a.staged && !d) return launch_staged_t<COLL>(a, s);
     const int bx = a.bx, by = a.by;
-    if (bx * by > PWFA_FLUID_MAX_THREADS || bx <= 0 || by <= 0) return cudaErrorInvalidConfiguration;
+    if (bx * by > PWFA_FLUID_MAX_THREADS || bx <= 0 || by <= 0 || (bx * by) % 32) return cudaErrorInvalidConfiguration;
     dim3 block(bx, by, 1);
     dim3 grid((a.g.nx + bx - 1) / bx, (a.g.ny + by - 1) / by, a.g.nz);
+    if (d) {
+        if ((int64_t)grid.x * grid.y * grid.z > d->capacity) return cudaErrorInvalidValue;
+        if (a.g.periodic) fluid_diag_kernel<ST, COLL, true><<<grid, block, 0, s>>>(a, d->dxcube, d->partials);
+        else fluid_diag_kernel<ST, COLL, false><<<grid, block, 0, s>>>(a, d->dxcube, d->partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_diag_finish(d->partials, (int64_t)grid.x * grid.y * grid.z, d->out, s);
+    }
     if (a.g.periodic) fluid_kernel<ST, COLL, true><<<grid, block, 0, s>>>(a);
     else fluid_kernel<ST, COLL, false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int ST>
-cudaError_t launch_fluid_s(const StepArgs& a, int collision, cudaStream_t s) {
+cudaError_t launch_fluid_s(const StepArgs& a, int collision, cudaStream_t s, const DiagOut* d) {
     switch (collision) {
-        case 0: return launch_fluid_t<ST, 0>(a, s);
-        case 1: return launch_fluid_t<ST, 1>(a, s);
-        case 2: return launch_fluid_t<ST, 2>(a, s);
+        case 0: return launch_fluid_t<ST, 0>(a, s, d);
+        case 1: return launch_fluid_t<ST, 1>(a, s, d);
+        case 2: return launch_fluid_t<ST, 2>(a, s, d);
     }
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_fluid(const StepArgs& a, int storage, int collision, cudaStream_t s) {
+cudaError_t launch_fluid(const StepArgs& a, int storage, int collision, cudaStream_t s, const DiagOut* d) {
     switch (storage) {
-        case 0: return launch_fluid_s<0>(a, collision, s);
-        case 1: return launch_fluid_s<1>(a, collision, s);
-        case 2: return launch_fluid_s<2>(a, collision, s);
+        case 0: return launch_fluid_s<0>(a, collision, s, d);
+        case 1: return launch_fluid_s<1>(a, collision, s, d);
+        case 2: return launch_fluid_s<2>(a, collision, s, d);
     }
     return cudaErrorInvalidValue;
 }

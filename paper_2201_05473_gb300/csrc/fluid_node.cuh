@@ -17,19 +17,30 @@
 
 namespace pwfa {
 
-template <int ST, int COLL, bool PER>
-__device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int z) {
+// Node quantities handed to the fused diagnostics (state entering the step).
+struct NodeDiag {
+    float n, a1, a2, a3, beta2;
+};
+
+// Everything after the gather: moments, source, collision, stores, current.
+// f holds the pulled populations f^n(x) (of the clamped node when bnd).
+template <int ST, int COLL, bool PER, bool DIAG = false>
+__device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, int z, float (&f)[kL][kQ], bool bnd,
+                                              NodeDiag* nd = nullptr) {
     using T = typename Codec<ST>::T;
     const Grid& g = a.g;
     const uint32_t node = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x;
 
-    float f[kL][kQ];
-    bool bnd;
-    gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
-
     float A[kL], nn, beta[3];
     node_moments(f, a.n_floor, A, nn, beta);
     const float n = A[0];
+    if (DIAG) {
+        nd->n = A[0];
+        nd->a1 = A[1];
+        nd->a2 = A[2];
+        nd->a3 = A[3];
+        nd->beta2 = beta[0] * beta[0] + beta[1] * beta[1] + beta[2] * beta[2];
+    }
 
     // Lorentz source (Eq. 4): F_0 = 0, F_k = -n (E + beta x B)_k, with B the
     // mean of its two time levels.
@@ -68,13 +79,13 @@ __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int 
             // streaming only: f* = f
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, f[l][q], l == 0 ? wq(q) * a.n0 : 0.0f);
+                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, f[l][q], l, q, a.n0);
         } else if (COLL == 0) {
             // BGK, Eq. 7, plus the source of Eq. 10
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
                 const float fs = f[l][q] + om * (A[l] * phi[q] - f[l][q]) + wq(q) * Fl;
-                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l == 0 ? wq(q) * a.n0 : 0.0f);
+                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l, q, a.n0);
             }
         } else {
             // Regularized: relax only the first Hermite moment of f - f^eq,
@@ -98,7 +109,7 @@ __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int 
                 if (xi_y(q)) xp += (float)xi_y(q) * P1;
                 if (xi_z(q)) xp += (float)xi_z(q) * P2;
                 const float fs = A[l] * phi[q] + wq(q) * (xp + Fl);
-                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l == 0 ? wq(q) * a.n0 : 0.0f);
+                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l, q, a.n0);
             }
         }
     }
@@ -111,6 +122,15 @@ __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int 
     __stcs(a.J[0] + node, -n * ps0 / gs);
     __stcs(a.J[1] + node, -n * ps1 / gs);
     __stcs(a.J[2] + node, -n * ps2 / gs);
+}
+
+template <int ST, int COLL, bool PER, bool DIAG = false>
+__device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int z, NodeDiag* nd = nullptr) {
+    using T = typename Codec<ST>::T;
+    float f[kL][kQ];
+    bool bnd;
+    gather<ST, PER>(a.g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+    fluid_compute<ST, COLL, PER, DIAG>(a, x, y, z, f, bnd, nd);
 }
 
 }  // namespace pwfa

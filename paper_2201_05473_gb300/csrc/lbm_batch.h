@@ -6,6 +6,7 @@
 namespace pwfa {
 
 constexpr int kBatchTile = 128;  // nodes (threads) per work item
+constexpr int kMaxBatch = 96;    // instances per batched launch (constant-memory table)
 
 // One instance of the batch, in device memory.
 struct BatchEntry {
@@ -28,6 +29,9 @@ struct BatchLaunch {
 // 3 advance the step counters.
 cudaError_t launch_batch_phase(const BatchLaunch& b, int phase, int parity, int storage, int collision,
                                bool periodic, cudaStream_t s);
+
+// Copy the instance table into the kernels' constant-memory copy.
+cudaError_t batch_upload_table(const BatchEntry* host, int n, cudaStream_t s);
 
 // Persistent grid size for the given kernel variant.
 cudaError_t batch_grid_size(int storage, int collision, bool periodic, int* grid);

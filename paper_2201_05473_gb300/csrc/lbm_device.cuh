@@ -38,31 +38,39 @@ __host__ __device__ __forceinline__ constexpr float wq(int q) {
 
 // ------------------------------------------------------------ storage codecs
 // FP32 stores f itself. BF16/FP16 store the deviation from the plasma at rest
-// (w_i n0 for lattice 0, 0 for the momentum lattices) so that the 8/11-bit
-// mantissa resolves the perturbation rather than the background.
+// (w_i n0 for lattice 0, 0 for the momentum lattices) so that the short
+// mantissa resolves the perturbation rather than the background. FP16 also
+// scales the deviation by 2^10 / w_i: without it the small deviations of
+// lattice 0 (w_i dn ~ 1e-6) fall into FP16's subnormal range; with it FP16
+// holds |deviation / w_i| up to ~64 (n p <= 64) at full relative precision.
+__host__ __device__ __forceinline__ constexpr float dev_base(int l, int q, float n0) {
+    return l == 0 ? wq(q) * n0 : 0.0f;
+}
+constexpr float kF16Scale = 1024.0f;
+
 template <int ST> struct Codec;
 
 template <> struct Codec<0> {
     using T = float;
-    static __device__ __forceinline__ float load(const T* p, float) { return __ldg(p); }
-    static __device__ __forceinline__ void store(T* p, float v, float) { __stcs(p, v); }
+    static __device__ __forceinline__ float load(const T* p, int, int, float) { return __ldg(p); }
+    static __device__ __forceinline__ void store(T* p, float v, int, int, float) { __stcs(p, v); }
 };
 template <> struct Codec<1> {
     using T = __nv_bfloat16;
-    static __device__ __forceinline__ float load(const T* p, float base) {
-        return __bfloat162float(__ldg(p)) + base;
+    static __device__ __forceinline__ float load(const T* p, int l, int q, float n0) {
+        return __bfloat162float(__ldg(p)) + dev_base(l, q, n0);
     }
-    static __device__ __forceinline__ void store(T* p, float v, float base) {
-        *p = __float2bfloat16_rn(v - base);
+    static __device__ __forceinline__ void store(T* p, float v, int l, int q, float n0) {
+        *p = __float2bfloat16_rn(v - dev_base(l, q, n0));
     }
 };
 template <> struct Codec<2> {
     using T = __half;
-    static __device__ __forceinline__ float load(const T* p, float base) {
-        return __half2float(__ldg(p)) + base;
+    static __device__ __forceinline__ float load(const T* p, int l, int q, float n0) {
+        return __half2float(__ldg(p)) * (wq(q) / kF16Scale) + dev_base(l, q, n0);
     }
-    static __device__ __forceinline__ void store(T* p, float v, float base) {
-        *p = __float2half_rn(v - base);
+    static __device__ __forceinline__ void store(T* p, float v, int l, int q, float n0) {
+        *p = __float2half_rn((v - dev_base(l, q, n0)) * (kF16Scale / wq(q)));
     }
 };
 
@@ -93,6 +101,7 @@ struct StepArgs {
     // driver: J_b,z = -alpha exp(-r^2/(2 sr^2) - (z - zc)^2/(2 sz^2)) at t_{n+1}
     float alpha, inv2sr2, inv2sz2, zc, dx;
     int bx, by;           // fluid kernel block shape (autotuned per instance)
+    int staged;           // 1: software-pipelined fluid kernel (FP32 storage), 128-thread tiles
 };
 
 __device__ __forceinline__ int wrapi(int a, int n) {

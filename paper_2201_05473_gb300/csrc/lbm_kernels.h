@@ -8,9 +8,23 @@
 
 namespace pwfa {
 
+// Where the fused diagnostics of a fluid launch go: one record of 8 doubles
+// per thread block (capacity records), reduced into out[8].
+struct DiagOut {
+    double* partials;
+    int64_t capacity;
+    double* out;
+    double dxcube;
+};
+
 // Fused fluid step: pull streaming (Eq. 6), moments, Lorentz source (Eqs. 4,
 // 10), collision (Eq. 7 or regularized), Eq. 14 boundary nodes, node current.
-cudaError_t launch_fluid(const StepArgs& a, int storage, int collision, cudaStream_t s);
+// With d != NULL it also reduces the FP64 diagnostics of the entering state.
+cudaError_t launch_fluid(const StepArgs& a, int storage, int collision, cudaStream_t s,
+                         const DiagOut* d = nullptr);
+
+// Reduce nparts diagnostics records into out[8].
+cudaError_t launch_diag_finish(const double* partials, int64_t nparts, double* out, cudaStream_t s);
 
 // Faraday, dB/dt = -curl E: Bn = Bc - dt curl_h E (Yee, Eq. 5).
 cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s);
@@ -35,6 +49,10 @@ cudaError_t launch_import_f(const Grid& g, const float* in, void* f, int storage
 
 // Node fields selected by a PWFA_FIELD_* mask into out, one block of N per bit.
 cudaError_t launch_export_fields(const StepArgs& a, int storage, unsigned mask, float* out, cudaStream_t s);
+
+// Line cut along z at offset r from the axis: out[0..nz) density,
+// out[nz..2nz) node-averaged E_z (bilinear in x, y).
+cudaError_t launch_linecut(const StepArgs& a, int storage, double r, float* out, cudaStream_t s);
 
 // FP64 diagnostics: partial sums per block into partials (nblocks x 8), then
 // reduced into out[8] (device).

@@ -46,7 +46,7 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
         }
         const uint32_t off = (uint32_t)q * N + src;
 #pragma unroll
-        for (int l = 0; l < kL; ++l) f[l][q] = Codec<ST>::load(fl[l] + off, l == 0 ? wq(q) * n0 : 0.0f);
+        for (int l = 0; l < kL; ++l) f[l][q] = Codec<ST>::load(fl[l] + off, l, q, n0);
     }
 }
 

@@ -59,7 +59,8 @@ EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_
            "pwfa_lbm_set_state", "pwfa_lbm_steps_done", "pwfa_lbm_set_stream",
            "pwfa_lbm_destroy", "pwfa_lbm_last_error", "pwfa_lbm_profile", "pwfa_lbm_kernel_times",
            "pwfa_lbm_set_launch", "pwfa_lbm_get_launch", "pwfa_lbm_autotune",
-           "pwfa_lbm_diag_noalloc", "pwfa_lbm_record", "pwfa_lbm_adjoint_step", "pwfa_lbm_set_batching")
+           "pwfa_lbm_diag_noalloc", "pwfa_lbm_record", "pwfa_lbm_adjoint_step", "pwfa_lbm_set_batching",
+           "pwfa_lbm_step_diag", "pwfa_lbm_linecut", "pwfa_lbm_set_fluid_variant", "pwfa_lbm_get_fluid_variant")
 
 
 def load(build: bool = True):
@@ -90,6 +91,10 @@ def load(build: bool = True):
         lib.pwfa_lbm_set_launch.argtypes = [vp, i32, i32, i32]
         lib.pwfa_lbm_get_launch.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         lib.pwfa_lbm_autotune.argtypes = [vp, i32]
+        lib.pwfa_lbm_set_fluid_variant.argtypes = [vp, i32, i32]
+        lib.pwfa_lbm_set_fluid_variant.restype = ctypes.c_int
+        lib.pwfa_lbm_get_fluid_variant.argtypes = [vp, i32, ctypes.POINTER(i32)]
+        lib.pwfa_lbm_get_fluid_variant.restype = ctypes.c_int
         lib.pwfa_lbm_diag_noalloc.argtypes = [i32, i32, i32, ctypes.c_double, ctypes.c_double,
                                               vp, vp, vp, vp, vp]
         lib.pwfa_lbm_diag_noalloc.restype = ctypes.c_int
@@ -97,6 +102,10 @@ def load(build: bool = True):
         lib.pwfa_lbm_record.restype = ctypes.c_int
         lib.pwfa_lbm_adjoint_step.argtypes = [vp, i32, vp, dp, i32]
         lib.pwfa_lbm_adjoint_step.restype = ctypes.c_int
+        lib.pwfa_lbm_linecut.argtypes = [vp, i32, ctypes.c_double, ctypes.c_double, vp, i64, dp]
+        lib.pwfa_lbm_linecut.restype = ctypes.c_int
+        lib.pwfa_lbm_step_diag.argtypes = [vp, i32, dp]
+        lib.pwfa_lbm_step_diag.restype = ctypes.c_int
         lib.pwfa_lbm_set_batching.argtypes = [vp, i32]
         lib.pwfa_lbm_set_batching.restype = ctypes.c_int
         lib.pwfa_lbm_last_error.restype = ctypes.c_char_p
@@ -189,6 +198,16 @@ class Simulation:
     def step(self, n: int = 1):
         _check(self._lib.pwfa_lbm_step(self._h, int(n)))
 
+    def step_diag(self, n: int = 1, out=None) -> np.ndarray:
+        """Advance n steps; FP64 diagnostics of the state entering the last
+        step, fused into it ([n_instances][8], or into a caller-owned host
+        float64 buffer)."""
+        if out is None:
+            out = np.zeros((len(self.works), 8), dtype=np.float64)
+        _check(self._lib.pwfa_lbm_step_diag(self._h, int(n),
+                                            ctypes.cast(_ptr(out), ctypes.POINTER(ctypes.c_double))))
+        return out
+
     def steps_done(self, instance: int = 0) -> int:
         r = self._lib.pwfa_lbm_steps_done(self._h, instance)
         if r < 0:
@@ -222,6 +241,17 @@ class Simulation:
             _check(rc)
         return d
 
+    def linecut(self, r: float = 0.0, n_star: float = 0.95, instance: int = 0):
+        """(n[z], E_z[z], bubble length) along z at offset r from the axis."""
+        w = self.works[instance] if 0 <= instance < len(self.works) else None
+        if w is None:
+            raise LBMError(-1, f"instance {instance} out of range")
+        out = np.zeros(2 * w.nz, dtype=np.float32)
+        lb = ctypes.c_double()
+        _check(self._lib.pwfa_lbm_linecut(self._h, instance, float(r), float(n_star), _ptr(out), out.size,
+                                          ctypes.byref(lb)))
+        return out[:w.nz], out[w.nz:], lb.value
+
     def diag_into(self, host_buf, instance: int = 0):
         """FP64 diagnostics into a caller-owned host float64 tensor/array of 8."""
         ptr = _ptr(host_buf)
@@ -236,6 +266,16 @@ class Simulation:
         bx, by = ctypes.c_int32(), ctypes.c_int32()
         _check(self._lib.pwfa_lbm_get_launch(self._h, instance, ctypes.byref(bx), ctypes.byref(by)))
         return bx.value, by.value
+
+    DIRECT, STAGED = 0, 1
+
+    def set_fluid_variant(self, variant: int, instance: int = 0):
+        _check(self._lib.pwfa_lbm_set_fluid_variant(self._h, instance, int(variant)))
+
+    def get_fluid_variant(self, instance: int = 0) -> int:
+        v = ctypes.c_int32()
+        _check(self._lib.pwfa_lbm_get_fluid_variant(self._h, instance, ctypes.byref(v)))
+        return v.value
 
     def autotune(self, reps: int = 3):
         _check(self._lib.pwfa_lbm_autotune(self._h, reps))

