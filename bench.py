@@ -40,8 +40,8 @@ FLUID_BYTES_F32 = 76 * 4 * 2 + 12 + 24 + 12
 # plus E and B read+write.
 STEP_BYTES = {W.F32: 608 + 48, W.BF16: 304 + 48, W.F16: 304 + 48}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fluid_kernel_traffic.json")
-KERNEL_SOURCES = ["paper_2201_05473_gb300/csrc/fluid.cu", "paper_2201_05473_gb300/csrc/lbm_node.cuh",
-                  "paper_2201_05473_gb300/csrc/lbm_device.cuh"]
+KERNEL_SOURCES = ["paper_2201_05473_gb300/csrc/fluid.cu", "paper_2201_05473_gb300/csrc/fluid_node.cuh",
+                  "paper_2201_05473_gb300/csrc/lbm_node.cuh", "paper_2201_05473_gb300/csrc/lbm_device.cuh"]
 
 
 def kernel_source_hash() -> str:
@@ -279,7 +279,7 @@ def run_ours(args):
             e2e_s = time.perf_counter() - t0
         # ---- reduced-precision storage: same workload, BF16 / FP16 deviations
         storage_lines = {}
-        if not args.no_extra:
+        if not args.no_extra and args.only in ("", "storage"):
             for name, st in (("bf16", W.BF16), ("f16", W.F16)):
                 w2 = w.replace(storage=st)
                 torch.cuda.empty_cache()
@@ -313,7 +313,7 @@ def run_ours(args):
         # ---- adjoint: the differentiable form (256x128x128, 500 steps,
         # checkpoints every 23 steps, witness loss)
         adjoint_line = None
-        if not args.no_extra:
+        if not args.no_extra and args.only in ("", "adjoint"):
             torch.cuda.empty_cache()
             wa = W.differentiable().replace(profile=__import__("numpy").ones(64), profile_rmax=128 * 0.2 / 2)
             Ta = args.adjoint_steps
@@ -339,7 +339,7 @@ def run_ours(args):
         # graph-replayed launch per phase, against the same instances stepped
         # one after another
         batch_line = None
-        if not args.no_extra:
+        if not args.no_extra and args.only in ("", "batched"):
             torch.cuda.empty_cache()
             ws = W.batched_scan(64, seed=0)
             tot = sum(x.nodes for x in ws)
@@ -469,6 +469,8 @@ def main():
     ap.add_argument("--grid", default="", help="override the grid as ZxYxX (profiling captures)")
     ap.add_argument("--no-extra", action="store_true", help="skip the BF16/FP16 and adjoint lines")
     ap.add_argument("--adjoint-steps", type=int, default=500)
+    ap.add_argument("--only", default="", choices=["", "storage", "adjoint", "batched"],
+                    help="with a small --steps: run the main pass and one extra section (profiling captures)")
     ap.add_argument("--report", default="", choices=["", "precision"],
                     help="precision: error table of BF16/FP16/FP32 storage against the oracle")
     args = ap.parse_args()

@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(256, PWFA_ADJ_MIN_BLOCKS) adj_fluid_kernel(con
         zs = min(max(z, 1), g.nz - 2);
     }
     const T* fin = static_cast<const T*>(s.fin);
-    const T* finl[kL] = {fin, fin + (size_t)kQ * N, fin + (size_t)2 * kQ * N, fin + (size_t)3 * kQ * N};
+    const int64_t LS = lattice_stride(g);
+    const T* finl[kL] = {fin, fin + LS, fin + 2 * LS, fin + 3 * LS};
     const float* Sinl[kL] = {a.Sbar_in, a.Sbar_in + (size_t)kQ * N, a.Sbar_in + (size_t)2 * kQ * N,
                              a.Sbar_in + (size_t)3 * kQ * N};
     // (the regularized projection's first moments are not needed: the
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(256, PWFA_ADJ_MIN_BLOCKS) adj_fluid_kernel(con
     for (int q = 0; q < kQ; ++q) {
         const uint32_t src = (uint32_t)src_index<PER>(g, xs, ys, zs, q);
 #pragma unroll
-        for (int l = 0; l < kL; ++l) A[l] += Codec<ST>::load(finl[l] + ((uint32_t)q * N + src), l, q, s.n0);
+        for (int l = 0; l < kL; ++l) A[l] += Codec<ST>::load(finl[l] + pop_off(q, src), l, q, s.n0);
     }
     const float n = A[0];
     const float nn = n > s.n_floor ? n : s.n_floor;

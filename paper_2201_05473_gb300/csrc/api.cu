@@ -114,7 +114,8 @@ int validate(const pwfa_lbm_params& p, int idx) {
     if (p.nx < 3 || p.ny < 3 || p.nz < 3) return bad("nx, ny, nz must be >= 3");
     if ((int64_t)p.nx * p.ny > (int64_t)1 << 30 || p.nz > 65535) return bad("grid too large");
     // one lattice's 19 planes are addressed with 32-bit element offsets
-    if ((int64_t)p.nx * p.ny * p.nz * 19 >= ((int64_t)1 << 32)) return bad("grid too large (nodes * 19 >= 2^32)");
+    if (((int64_t)p.nx * p.ny * p.nz + 31) / 32 * 32 * 19 >= ((int64_t)1 << 32))
+        return bad("grid too large (nodes * 19 >= 2^32)");
     if (!(p.dx > 0) || !std::isfinite(p.dx)) return bad("dx must be > 0");
     if (!(p.dt >= 0) || !std::isfinite(p.dt)) return bad("dt must be >= 0 (0 = default)");
     const double dt = p.dt > 0 ? p.dt : 0.17628 * p.dx;
@@ -212,7 +213,7 @@ void free_instance(Instance& in) {
 
 int alloc_instance(Instance& in, cudaStream_t s) {
     const int64_t N = in.g.N;
-    const size_t fbytes = align_up((size_t)N * kPop * storage_bytes(in.p.storage));
+    const size_t fbytes = align_up((size_t)in.g.Np * kPop * storage_bytes(in.p.storage));
     // Each Yee/current array is preceded by one zero x-y plane: in open mode the
     // node averages read index -1 / -nx / -nx*ny without bounds checks.
     const size_t pad = align_up((size_t)in.g.nx * in.g.ny * sizeof(float));
@@ -463,7 +464,7 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
 }
 
 // ---------------------------------------------------------------- adjoint
-size_t fbytes_of(const Instance& in) { return align_up((size_t)in.g.N * kPop * storage_bytes(in.p.storage)); }
+size_t fbytes_of(const Instance& in) { return align_up((size_t)in.g.Np * kPop * storage_bytes(in.p.storage)); }
 size_t vbytes_of(const Instance& in) { return align_up((size_t)in.g.N * sizeof(float)); }
 
 struct StateRef {  // one stored state inside a recording buffer
@@ -485,7 +486,7 @@ StateRef state_at(const Instance& in, void* base, bool with_bn) {
 }
 
 int copy_state(const Instance& in, const StateRef& dst, bool to_rec, cudaStream_t s) {
-    const size_t fb = (size_t)in.g.N * kPop * storage_bytes(in.p.storage);
+    const size_t fb = (size_t)in.g.Np * kPop * storage_bytes(in.p.storage);
     const size_t vb = sizeof(float) * (size_t)in.g.N;
     if (to_rec) {
         PWFA_CUDA(cudaMemcpyAsync(dst.f, in.f[in.fcur], fb, cudaMemcpyDeviceToDevice, s), "checkpoint copy");
@@ -588,7 +589,7 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
         // restore the checkpoint into state 0 of the segment
         {
             StateRef cp = state_at(in, (char*)r.cp + r.cp_stride * seg, false);
-            const size_t fb = (size_t)in.g.N * kPop * storage_bytes(in.p.storage);
+            const size_t fb = (size_t)in.g.Np * kPop * storage_bytes(in.p.storage);
             PWFA_CUDA(cudaMemcpyAsync(f_slot(0), cp.f, fb, cudaMemcpyDeviceToDevice, s), "restore copy");
             for (int c = 0; c < 3; ++c) {
                 PWFA_CUDA(cudaMemcpyAsync(E_slot(0, c), cp.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
@@ -763,6 +764,7 @@ int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances, void* cu
         in.p.profile = nullptr;
         in.g.nx = in.p.nx; in.g.ny = in.p.ny; in.g.nz = in.p.nz;
         in.g.N = (int64_t)in.p.nx * in.p.ny * in.p.nz;
+        in.g.Np = (in.g.N + 31) / 32 * 32;
         in.g.periodic = in.p.boundary == PWFA_PERIODIC;
         rc = alloc_instance(in, h->stream);
     }

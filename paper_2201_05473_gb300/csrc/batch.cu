@@ -46,32 +46,42 @@ __global__ void __launch_bounds__(kThreads, PhaseOcc<PHASE>::blocks) batch_kerne
     const int64_t i0 = (int64_t)blockIdx.x * per;
     const int64_t i1 = i0 + per < nitems ? i0 + per : nitems;
     int inst = 0;
-    int64_t begin = 0, end = 0;  // item range of the current instance
-    int tiles_x = 1, per_plane = 1, bx = 1;
+    int64_t end = 0;  // end of the current instance's items
+    int tiles_x = 1, tiles_y = 1, bx = 1, by = 1, lx = 0, ly = 0;
+    int tx = 0, ty = 0, z = 0;  // tile coordinates of the current item
     float zc = 0.0f;
     for (int64_t item = i0; item < i1; ++item) {
         if (item >= end) {
+            // entering an instance: decode the item once (divisions only here)
             inst = find_instance(c_entries, ninst, item);
             const BatchEntry& e = c_entries[inst];
-            begin = e.item_begin;
             end = inst + 1 < ninst ? c_entries[inst + 1].item_begin : nitems;
             tiles_x = e.tiles_x;
-            per_plane = e.tiles_x * e.tiles_y;
+            tiles_y = e.tiles_y;
             bx = e.bx;
+            by = kThreads / bx;
+            lx = (int)threadIdx.x % bx;
+            ly = (int)threadIdx.x / bx;
+            const int64_t local = item - e.item_begin;
+            const int64_t per_plane = (int64_t)tiles_x * tiles_y;
+            z = (int)(local / per_plane);
+            const int r = (int)(local - (int64_t)z * per_plane);
+            ty = r / tiles_x;
+            tx = r - ty * tiles_x;
             if (PHASE == 2) zc = (float)(e.z0 + (double)(*e.step + 1) * e.dt);
         }
         const StepArgs& a = c_entries[inst].args[parity];
-        const int64_t local = item - begin;
-        const int z = (int)(local / per_plane);
-        const int r = (int)(local - (int64_t)z * per_plane);
-        const int ty = r / tiles_x;
-        const int tx = r - ty * tiles_x;
-        const int x = tx * bx + (int)threadIdx.x % bx;
-        const int y = ty * (kThreads / bx) + (int)threadIdx.x / bx;
+        const int x = tx * bx + lx;
+        const int y = ty * by + ly;
         if (x < a.g.nx && y < a.g.ny) {
             if (PHASE == 0) faraday_node<PER>(a, x, y, z);
             else if (PHASE == 1) fluid_node<ST, COLL, PER>(a, x, y, z);
             else ampere_node<PER>(a, x, y, z, zc);
+        }
+        // next item of the same instance: x tiles fastest, then y, then z
+        if (++tx == tiles_x) {
+            tx = 0;
+            if (++ty == tiles_y) { ty = 0; ++z; }
         }
     }
 }

@@ -131,11 +131,11 @@ __device__ __forceinline__ void stage_copies(const StepArgs& a, const TileNode& 
         zs = min(max(n.z, 1), g.nz - 2);
     }
     const float* fin = static_cast<const float*>(a.fin);
-    const uint32_t N = (uint32_t)g.N;
-    const float* fl[kL] = {fin, fin + (size_t)kQ * N, fin + (size_t)2 * kQ * N, fin + (size_t)3 * kQ * N};
+    const int64_t LS = lattice_stride(g);
+    const float* fl[kL] = {fin, fin + LS, fin + 2 * LS, fin + 3 * LS};
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
-        const uint32_t off = (uint32_t)q * N + (uint32_t)src_index<PER>(g, xs, ys, zs, q);
+        const uint32_t off = pop_off(q, (uint32_t)src_index<PER>(g, xs, ys, zs, q));
 #pragma unroll
         for (int l = 0; l < kL; ++l)
             cp_async4(col + 4u * (uint32_t)((l * kQ + q) * kStageThreads), fl[l] + off);

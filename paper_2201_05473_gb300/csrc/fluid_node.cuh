@@ -58,9 +58,9 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
         F[2] = -n * (e[2] + beta[0] * b1 - beta[1] * b0);
     }
 
-    const uint32_t N = (uint32_t)g.N;
+    const int64_t LS = lattice_stride(g);
     T* const fo0 = static_cast<T*>(a.fout);
-    T* const fo[kL] = {fo0, fo0 + (size_t)kQ * N, fo0 + (size_t)2 * kQ * N, fo0 + (size_t)3 * kQ * N};
+    T* const fo[kL] = {fo0, fo0 + LS, fo0 + 2 * LS, fo0 + 3 * LS};
     const float u[3] = {beta[0] * a.lat, beta[1] * a.lat, beta[2] * a.lat};
     float phi[kQ];
     eq_factors(u, phi);
@@ -79,13 +79,13 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
             // streaming only: f* = f
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, f[l][q], l, q, a.n0);
+                Codec<ST>::store(fo[l] + pop_off(q, node), f[l][q], l, q, a.n0);
         } else if (COLL == 0) {
             // BGK, Eq. 7, plus the source of Eq. 10
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
                 const float fs = f[l][q] + om * (A[l] * phi[q] - f[l][q]) + wq(q) * Fl;
-                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l, q, a.n0);
+                Codec<ST>::store(fo[l] + pop_off(q, node), fs, l, q, a.n0);
             }
         } else {
             // Regularized: relax only the first Hermite moment of f - f^eq,
@@ -109,7 +109,7 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
                 if (xi_y(q)) xp += (float)xi_y(q) * P1;
                 if (xi_z(q)) xp += (float)xi_z(q) * P2;
                 const float fs = A[l] * phi[q] + wq(q) * (xp + Fl);
-                Codec<ST>::store(fo[l] + (uint32_t)q * N + node, fs, l, q, a.n0);
+                Codec<ST>::store(fo[l] + pop_off(q, node), fs, l, q, a.n0);
             }
         }
     }

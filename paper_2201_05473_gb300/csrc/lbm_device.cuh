@@ -78,8 +78,19 @@ template <> struct Codec<2> {
 struct Grid {
     int nx, ny, nz;
     int64_t N;        // nx * ny * nz
+    int64_t Np;       // N rounded up to a multiple of 32 (population chunks)
     int periodic;     // 1: every axis wraps; 0: open (Eq. 14) + conducting walls
 };
+
+// Population layout in HBM: four lattice blocks of 19 * Np elements; inside
+// a block, nodes are grouped in chunks of 32 and a chunk holds its 19
+// populations one after another: (q, node) sits at
+// (node / 32) * 19 * 32 + q * 32 + node % 32. A warp's 19 loads of one lattice
+// thus fall in one 2.4 KB region (FP32) instead of 19 far-apart planes.
+__host__ __device__ __forceinline__ uint32_t pop_off(int q, uint32_t node) {
+    return (node >> 5) * (uint32_t)(kQ * 32) + (uint32_t)q * 32u + (node & 31u);
+}
+__host__ __device__ __forceinline__ int64_t lattice_stride(const Grid& g) { return (int64_t)kQ * g.Np; }
 
 // One instance's device state as the step kernels see it.
 struct StepArgs {

@@ -16,9 +16,9 @@ __device__ __forceinline__ int64_t src_index(const Grid& g, int x, int y, int z,
 
 // Pull the 76 populations f^n(x) = f*(x - xi_i) of node (x,y,z). Open grids
 // gather at the clamped interior node instead and flag the node as a boundary
-// node: its state is then f^eq of those moments (Eq. 14). Each lattice's 19
-// planes form one block of 19 N elements addressed with 32-bit offsets
-// (the host limits N so that 19 N < 2^32).
+// node: its state is then f^eq of those moments (Eq. 14). Each lattice's
+// block of 19 Np elements is addressed with 32-bit offsets (the host limits
+// the grid so that 19 Np < 2^32).
 template <int ST, bool PER>
 __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::T* __restrict__ fin,
                                        float n0, int x, int y, int z, float f[kL][kQ], bool& bnd) {
@@ -31,8 +31,8 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
         zs = min(max(z, 1), g.nz - 2);
         bnd = (xs != x) | (ys != y) | (zs != z);
     }
-    const uint32_t N = (uint32_t)g.N;
-    const T* __restrict__ fl[kL] = {fin, fin + (size_t)kQ * N, fin + (size_t)2 * kQ * N, fin + (size_t)3 * kQ * N};
+    const int64_t LS = lattice_stride(g);
+    const T* __restrict__ fl[kL] = {fin, fin + LS, fin + 2 * LS, fin + 3 * LS};
     const uint32_t sxy = (uint32_t)g.nx * (uint32_t)g.ny;
     const uint32_t nodec = ((uint32_t)zs * (uint32_t)g.ny + (uint32_t)ys) * (uint32_t)g.nx + (uint32_t)xs;
 #pragma unroll
@@ -44,7 +44,7 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
             const int d = xi_x(q) + xi_y(q) * g.nx;
             src = nodec - (uint32_t)d - (uint32_t)(xi_z(q)) * sxy;
         }
-        const uint32_t off = (uint32_t)q * N + src;
+        const uint32_t off = pop_off(q, src);
 #pragma unroll
         for (int l = 0; l < kL; ++l) f[l][q] = Codec<ST>::load(fl[l] + off, l, q, n0);
     }
