@@ -89,17 +89,19 @@ __global__ void __launch_bounds__(kBX * kBY) adj_ampere_kernel(const AdjArgs a) 
         a.Jbar[0][o] = -0.5f * dt * (ex + rdE<PER>(g, Ex, 0, i - 1, j, k));
         a.Jbar[1][o] = -0.5f * dt * (ey + rdE<PER>(g, Ey, 1, i, j - 1, k));
         a.Jbar[2][o] = -0.5f * dt * (ez + rdE<PER>(g, Ez, 2, i, j, k - 1));
-        // driver: E_z += dt alpha gauss  =>  d/d(alpha, sigma_r, sigma_z)
+        // driver: E_z += dt alpha gauss  =>  d/d(alpha, sigma_r, sigma_z).
+        // The node term is the derivative of the forward's FP32 Gaussian,
+        // evaluated the same way; only the sum over nodes is FP64.
         if (ez != 0.0f) {
-            const double xr = ((double)i - 0.5 * (g.nx - 1)) * a.f.dx;
-            const double yr = ((double)j - 0.5 * (g.ny - 1)) * a.f.dx;
-            const double zeta = ((double)k + 0.5) * a.f.dx - a.f.zc;
-            const double r2 = xr * xr + yr * yr;
-            const double ga = exp(-r2 * a.f.inv2sr2 - zeta * zeta * a.f.inv2sz2);
-            const double w = (double)dt * ez * ga;
-            g3[0] = w;
-            g3[1] = w * a.f.alpha * r2 / ((double)a.sr * a.sr * a.sr);
-            g3[2] = w * a.f.alpha * zeta * zeta / ((double)a.sz * a.sz * a.sz);
+            const float xr = ((float)i - 0.5f * (float)(g.nx - 1)) * a.f.dx;
+            const float yr = ((float)j - 0.5f * (float)(g.ny - 1)) * a.f.dx;
+            const float zeta = ((float)k + 0.5f) * a.f.dx - a.f.zc;
+            const float r2 = xr * xr + yr * yr;
+            const float ga = expf(-r2 * a.f.inv2sr2 - zeta * zeta * a.f.inv2sz2);
+            const float w = dt * ez * ga;
+            g3[0] = (double)w;
+            g3[1] = (double)(w * (a.f.alpha / (a.sr * a.sr * a.sr)) * r2);
+            g3[2] = (double)(w * (a.f.alpha / (a.sz * a.sz * a.sz)) * (zeta * zeta));
         }
     }
     // block reduction of the three driver partials, one FP64 atomic each
@@ -128,182 +130,277 @@ __device__ __forceinline__ int wall_candidates(int v, int n, int out[3]) {
     return m;
 }
 
-template <int ST, int COLL, bool PER, bool BPASS>
+// Lattice-split form: a block of four warps takes 32 nodes of one x-row and
+// warp l owns lattice l. Each warp issues its lattice's 19 pulled populations
+// and 19 stored-population adjoints together (one memory round per node); the
+// lattice sums, the per-lattice reductions and the node-level adjoint (done
+// once, by warp 0) meet in shared memory.
+constexpr int kAdjThreads = 32 * kL;
 #ifndef PWFA_ADJ_MIN_BLOCKS
-#define PWFA_ADJ_MIN_BLOCKS 2
+#define PWFA_ADJ_MIN_BLOCKS 8
 #endif
-__global__ void __launch_bounds__(256, PWFA_ADJ_MIN_BLOCKS) adj_fluid_kernel(const AdjArgs a) {
-    using T = typename Codec<ST>::T;
-    const StepArgs& s = a.f;
-    const Grid& g = s.g;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= g.nx || y >= g.ny) return;
-    const uint32_t N = (uint32_t)g.N;
-    const uint32_t node = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x;
-    const bool bnd = !PER && (x == 0 || y == 0 || z == 0 || x == g.nx - 1 || y == g.ny - 1 || z == g.nz - 1);
-    if (BPASS != bnd) {
-        if (!BPASS) {
-            // A boundary node's own pull slots are never read by the forward
-            // step: their adjoint is zero.
-            for (int q = 0; q < kQ; ++q) {
-                const int sx = x - xi_x(q), sy = y - xi_y(q), sz = z - xi_z(q);
-                if (!in_grid(g, sx, sy, sz)) continue;
-                const uint32_t so = ((uint32_t)sz * (uint32_t)g.ny + (uint32_t)sy) * (uint32_t)g.nx + (uint32_t)sx;
-                for (int l = 0; l < kL; ++l) a.Sbar_out[(size_t)l * kQ * N + ((uint32_t)q * N + so)] = 0.0f;
-            }
-        }
+
+// The x = nx - 1 wall node of a row shares its block with the node it clamps
+// to (x = nx - 2) unless it opens a new block of 32.
+__host__ __device__ __forceinline__ bool xwall_split(int nx) { return (nx & 31) == 1; }
+
+// Boundary nodes whose moment adjoints are produced by the shell pass: the
+// two z walls (nx ny each), then per interior plane the rows y = 0 and
+// y = ny - 1 (nx each) and, when the x = nx - 1 wall sits alone in its
+// block, the column x = nx - 1 of the interior rows (ny - 2). The other
+// x-wall nodes of interior rows are handled inside the interior pass, in
+// the block of the node they clamp to.
+__host__ __device__ __forceinline__ uint32_t shell_count(const Grid& g) {
+    const uint32_t ring = 2u * (uint32_t)g.nx + (xwall_split(g.nx) ? (uint32_t)(g.ny - 2) : 0u);
+    return 2u * (uint32_t)g.nx * (uint32_t)g.ny + (uint32_t)(g.nz - 2) * ring;
+}
+
+__device__ __forceinline__ void shell_node(const Grid& g, uint32_t idx, int& x, int& y, int& z) {
+    const uint32_t nx = (uint32_t)g.nx, P = nx * (uint32_t)g.ny;
+    if (idx < 2u * P) {
+        z = idx < P ? 0 : g.nz - 1;
+        const uint32_t r = idx < P ? idx : idx - P;
+        y = (int)(r / nx);
+        x = (int)(r - (uint32_t)y * nx);
         return;
     }
-    // ---- forward recompute: moments at the (clamped) node
+    idx -= 2u * P;
+    const uint32_t M = 2u * nx + (xwall_split(g.nx) ? (uint32_t)(g.ny - 2) : 0u);
+    const uint32_t k = idx / M;
+    const uint32_t r = idx - k * M;
+    z = 1 + (int)k;
+    if (r < 2u * nx) {
+        y = r < nx ? 0 : g.ny - 1;
+        x = (int)(r < nx ? r : r - nx);
+    } else {
+        x = g.nx - 1;
+        y = 1 + (int)(r - 2u * nx);
+    }
+}
+
+// SHELL: the shell nodes above (open grids), writing their moment adjoints
+// A_bar. Otherwise one block per 32 nodes of a row: interior nodes scatter
+// their population adjoints, boundary nodes zero the slots they pulled.
+template <int ST, int COLL, bool PER, bool SHELL>
+__global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_kernel(const AdjArgs a,
+                                                                                    uint32_t nshell) {
+    using T = typename Codec<ST>::T;
+    __shared__ float sA[kL][32];     // lattice sums A_l
+    __shared__ float sG[kL][32];     // sum_i w_i S_bar_l,i
+    __shared__ float sU[kL][3][32];  // lattice l's share of u_bar
+    __shared__ float sN[4][3][32];   // node E, B sums at t_n and t_{n+1}, J_bar
+    __shared__ float sAb[kL][32];    // node-level part of A_bar; then x-wall A_bar
+    const StepArgs& s = a.f;
+    const Grid& g = s.g;
+    const int l = (int)(threadIdx.x >> 5);
+    const int lane = (int)(threadIdx.x & 31);
+    int x, y, z;
+    bool live;
+    if (SHELL) {
+        const uint32_t item = blockIdx.x * 32u + (uint32_t)lane;
+        live = item < nshell;
+        x = y = z = 0;
+        if (live) shell_node(g, item, x, y, z);
+    } else {
+        x = (int)blockIdx.x * 32 + lane;
+        y = (int)blockIdx.y;
+        z = (int)blockIdx.z;
+        live = x < g.nx;
+    }
+    const uint32_t sxy = (uint32_t)g.nx * (uint32_t)g.ny;
+    const uint32_t node = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x;
+    const bool bnd = !PER && (x == 0 || y == 0 || z == 0 || x == g.nx - 1 || y == g.ny - 1 || z == g.nz - 1);
+    const bool row_in = y >= 1 && y <= g.ny - 2 && z >= 1 && z <= g.nz - 2;
+    const bool xwall = !PER && !SHELL && live && row_in && (x == 0 || (x == g.nx - 1 && lane != 0));
+    const int64_t LS = lattice_stride(g);
+    const T* __restrict__ fin = static_cast<const T*>(s.fin) + l * LS;
+    const float* __restrict__ Sin = a.Sbar_in + l * LS;
+    float* __restrict__ Sout = a.Sbar_out + l * LS;
+    if (!SHELL && live && bnd) {
+        // a boundary node's own pull slots are never read by the forward
+        // step: their adjoint is zero
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const int sx = x - xi_x(q), sy = y - xi_y(q), sz = z - xi_z(q);
+            if (!in_grid(g, sx, sy, sz)) continue;
+            const uint32_t so = ((uint32_t)sz * (uint32_t)g.ny + (uint32_t)sy) * (uint32_t)g.nx + (uint32_t)sx;
+            Sout[pop_off(q, so)] = 0.0f;
+        }
+    }
+    const bool act = live && (SHELL || !bnd || xwall);
+    // pulled node: the clamped interior node on open grids (Eq. 14)
     int xs = x, ys = y, zs = z;
     if (!PER) {
         xs = min(max(x, 1), g.nx - 2);
         ys = min(max(y, 1), g.ny - 2);
         zs = min(max(z, 1), g.nz - 2);
     }
-    const T* fin = static_cast<const T*>(s.fin);
-    const int64_t LS = lattice_stride(g);
-    const T* finl[kL] = {fin, fin + LS, fin + 2 * LS, fin + 3 * LS};
-    const float* Sinl[kL] = {a.Sbar_in, a.Sbar_in + (size_t)kQ * N, a.Sbar_in + (size_t)2 * kQ * N,
-                             a.Sbar_in + (size_t)3 * kQ * N};
-    // (the regularized projection's first moments are not needed: the
-    // transpose of P = k3 (m - A u) with respect to m does not involve m)
-    float A[kL] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int q = 0; q < kQ; ++q) {
-        const uint32_t src = (uint32_t)src_index<PER>(g, xs, ys, zs, q);
-#pragma unroll
-        for (int l = 0; l < kL; ++l) A[l] += Codec<ST>::load(finl[l] + pop_off(q, src), l, q, s.n0);
-    }
-    const float n = A[0];
-    const float nn = n > s.n_floor ? n : s.n_floor;
-    const float p[3] = {A[1] / nn, A[2] / nn, A[3] / nn};
-    const float gam = sqrtf(1.0f + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    const float beta[3] = {p[0] / gam, p[1] / gam, p[2] / gam};
-    const float u[3] = {beta[0] * s.lat, beta[1] * s.lat, beta[2] * s.lat};
-    float phi[kQ];
-    eq_factors(u, phi);
-    float e[3] = {0.0f, 0.0f, 0.0f}, b[3] = {0.0f, 0.0f, 0.0f}, F[3] = {0.0f, 0.0f, 0.0f};
-    const bool forced = (COLL != 2) && s.couple;
-    if (forced) {
-        float bc[3], bn[3];
-        node_E<PER>(g, s.E, x, y, z, e);
-        node_B_sum<PER>(g, s.Bc, x, y, z, bc);
-        node_B_sum<PER>(g, s.Bn, x, y, z, bn);
-        for (int c = 0; c < 3; ++c) b[c] = 0.125f * (bc[c] + bn[c]);
-        F[0] = -n * (e[0] + beta[1] * b[2] - beta[2] * b[1]);
-        F[1] = -n * (e[1] + beta[2] * b[0] - beta[0] * b[2]);
-        F[2] = -n * (e[2] + beta[0] * b[1] - beta[1] * b[0]);
-    }
-    const float ps[3] = {(A[1] + F[0] * s.dt) / nn, (A[2] + F[1] * s.dt) / nn, (A[3] + F[2] * s.dt) / nn};
-    const float gs = sqrtf(1.0f + ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2]);
-    const float bs[3] = {ps[0] / gs, ps[1] / gs, ps[2] / gs};
+    const uint32_t nodec = ((uint32_t)zs * (uint32_t)g.ny + (uint32_t)ys) * (uint32_t)g.nx + (uint32_t)xs;
 
-    // ---- reverse
-    float Ab[kL] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float Fb[3] = {0.0f, 0.0f, 0.0f};
-    float nb = 0.0f, nnb = 0.0f;
-    // J = -n beta(p*)
-    {
-        const float Jb[3] = {a.Jbar[0][node], a.Jbar[1][node], a.Jbar[2][node]};
-        nb -= Jb[0] * bs[0] + Jb[1] * bs[1] + Jb[2] * bs[2];
-        const float v[3] = {-n * Jb[0], -n * Jb[1], -n * Jb[2]};
-        const float bv = bs[0] * v[0] + bs[1] * v[1] + bs[2] * v[2];
-        for (int c = 0; c < 3; ++c) {
-            const float psb = (v[c] - bs[c] * bv) / gs;
-            Ab[c + 1] += psb / nn;
-            Fb[c] += psb * s.dt / nn;
-            nnb -= psb * ps[c] / nn;
-        }
-    }
-    // collision (and the Eq. 14 replacement f := A phi on boundary nodes)
-    float phib[kQ];
-#pragma unroll
-    for (int q = 0; q < kQ; ++q) phib[q] = 0.0f;
-    float ub[3] = {0.0f, 0.0f, 0.0f};
-    float mb[kL][3];
-    const float om = s.omega;
-    const float k3 = 3.0f * (1.0f - om);
-#pragma unroll
-    for (int l = 0; l < kL; ++l) {
-        mb[l][0] = mb[l][1] = mb[l][2] = 0.0f;
-        float Gb = 0.0f, sphi = 0.0f, P0 = 0.0f, P1 = 0.0f, P2 = 0.0f;
-        // weight of d fs / d(A phi): omega for interior BGK, 1 otherwise
-        const float wA = (COLL == 0 && !bnd) ? om : ((COLL == 2 && !bnd) ? 0.0f : 1.0f);
+    // ---- one memory round: this lattice's pulled populations and S_bar,
+    // plus one of the node's field sums (or J_bar) per warp
+    float S[kQ];
+    float Al = 0.0f;
+    const bool forced = (COLL != 2) && s.couple;
+    if (act) {
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-            const float fsb = Sinl[l][(uint32_t)q * N + node];
-            Gb += wq(q) * fsb;
-            sphi += phi[q] * fsb;
-            phib[q] += wA * A[l] * fsb;
-            if (COLL == 1 && !bnd) {
-                P0 += wq(q) * (float)xi_x(q) * fsb;
-                P1 += wq(q) * (float)xi_y(q) * fsb;
-                P2 += wq(q) * (float)xi_z(q) * fsb;
+            uint32_t src;
+            if (PER) src = (uint32_t)src_index<true>(g, xs, ys, zs, q);
+            else src = nodec - (uint32_t)(xi_x(q) + xi_y(q) * g.nx) - (uint32_t)xi_z(q) * sxy;
+            Al += Codec<ST>::load(fin + pop_off(q, src), l, q, s.n0);
+            S[q] = __ldg(Sin + pop_off(q, node));
+        }
+        float v[3] = {0.0f, 0.0f, 0.0f};
+        if (l == 0) { if (forced) node_E<PER>(g, s.E, x, y, z, v); }
+        else if (l == 1) { if (forced) node_B_sum<PER>(g, s.Bc, x, y, z, v); }
+        else if (l == 2) { if (forced) node_B_sum<PER>(g, s.Bn, x, y, z, v); }
+        else { v[0] = a.Jbar[0][node]; v[1] = a.Jbar[1][node]; v[2] = a.Jbar[2][node]; }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sN[l][c][lane] = v[c];
+    } else {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) S[q] = 0.0f;
+    }
+    sA[l][lane] = Al;
+    __syncthreads();
+
+    // ---- forward recompute of the node's velocity (every warp)
+    const float A[kL] = {sA[0][lane], sA[1][lane], sA[2][lane], sA[3][lane]};
+    const float n = A[0];
+    const float nn = n > s.n_floor ? n : s.n_floor;
+    const float inn = 1.0f / nn;
+    const float p[3] = {A[1] * inn, A[2] * inn, A[3] * inn};
+    const float gam = sqrtf(1.0f + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    const float igam = 1.0f / gam;
+    const float beta[3] = {p[0] * igam, p[1] * igam, p[2] * igam};
+    const float u[3] = {beta[0] * s.lat, beta[1] * s.lat, beta[2] * s.lat};
+    const float om = s.omega;
+    const float k3 = 3.0f * (1.0f - om);
+    // weight of d fs / d(A phi): omega for interior BGK, 0 for interior
+    // stream-only, 1 for the regularized form and for boundary nodes
+    const float wA = (COLL == 0 && !bnd) ? om : ((COLL == 2 && !bnd) ? 0.0f : 1.0f);
+    const bool proj = COLL == 1 && !bnd;
+
+    // ---- this lattice's reductions over the 19 directions
+    float Gb = 0.0f, sphi = 0.0f, P[3] = {0.0f, 0.0f, 0.0f}, W[3] = {0.0f, 0.0f, 0.0f};
+    {
+        const float base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const float xu = (float)xi_x(q) * u[0] + (float)xi_y(q) * u[1] + (float)xi_z(q) * u[2];
+            const float ws = wq(q) * S[q];
+            Gb += ws;
+            sphi += ws * (base + 3.0f * xu + 4.5f * xu * xu);
+            if (xi_x(q)) { P[0] += (float)xi_x(q) * ws; W[0] += (float)xi_x(q) * ws * xu; }
+            if (xi_y(q)) { P[1] += (float)xi_y(q) * ws; W[1] += (float)xi_y(q) * ws * xu; }
+            if (xi_z(q)) { P[2] += (float)xi_z(q) * ws; W[2] += (float)xi_z(q) * ws * xu; }
+        }
+    }
+    // u_bar share: d(A_l phi_i)/du through phi_i = w_i (base + 3 xi.u + 4.5 (xi.u)^2),
+    // plus the regularized projection's -k3 A_l P_l
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float v = wA * Al * (3.0f * P[c] + 9.0f * W[c] - 3.0f * u[c] * Gb);
+        if (proj) v -= k3 * Al * P[c];
+        sU[l][c][lane] = v;
+    }
+    sG[l][lane] = Gb;
+    // this lattice's own part of its moment adjoint
+    float own = wA * sphi;
+    if (proj) own -= k3 * (P[0] * u[0] + P[1] * u[1] + P[2] * u[2]);
+    __syncthreads();
+
+    // ---- node-level reverse, once per node (warp 0)
+    if (l == 0 && act) {
+        float e[3] = {0.0f, 0.0f, 0.0f}, b[3] = {0.0f, 0.0f, 0.0f}, F[3] = {0.0f, 0.0f, 0.0f};
+        if (forced) {
+            for (int c = 0; c < 3; ++c) {
+                e[c] = sN[0][c][lane];
+                b[c] = 0.125f * (sN[1][c][lane] + sN[2][c][lane]);
+            }
+            F[0] = -n * (e[0] + beta[1] * b[2] - beta[2] * b[1]);
+            F[1] = -n * (e[1] + beta[2] * b[0] - beta[0] * b[2]);
+            F[2] = -n * (e[2] + beta[0] * b[1] - beta[1] * b[0]);
+        }
+        const float ps[3] = {(A[1] + F[0] * s.dt) * inn, (A[2] + F[1] * s.dt) * inn, (A[3] + F[2] * s.dt) * inn};
+        const float gs = sqrtf(1.0f + ps[0] * ps[0] + ps[1] * ps[1] + ps[2] * ps[2]);
+        const float igs = 1.0f / gs;
+        const float bs[3] = {ps[0] * igs, ps[1] * igs, ps[2] * igs};
+        float Am[3], Fb[3];
+        float nb, nnb = 0.0f;
+        {
+            // J = -n beta(p*)
+            const float Jb[3] = {sN[3][0][lane], sN[3][1][lane], sN[3][2][lane]};
+            nb = -(Jb[0] * bs[0] + Jb[1] * bs[1] + Jb[2] * bs[2]);
+            const float v[3] = {-n * Jb[0], -n * Jb[1], -n * Jb[2]};
+            const float bv = bs[0] * v[0] + bs[1] * v[1] + bs[2] * v[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float psb = (v[c] - bs[c] * bv) * igs;
+                Am[c] = psb * inn;
+                Fb[c] = psb * s.dt * inn;
+                nnb -= psb * ps[c] * inn;
             }
         }
-        Ab[l] += wA * sphi;
-        if (l > 0 && COLL != 2) Fb[l - 1] += Gb * s.dt;
-        if (COLL == 1 && !bnd) {
-            mb[l][0] = k3 * P0;
-            mb[l][1] = k3 * P1;
-            mb[l][2] = k3 * P2;
-            Ab[l] -= k3 * (P0 * u[0] + P1 * u[1] + P2 * u[2]);
-            ub[0] -= k3 * A[l] * P0;
-            ub[1] -= k3 * A[l] * P1;
-            ub[2] -= k3 * A[l] * P2;
-        }
-    }
-    // phi_i = w_i (1 - 1.5 u.u + 3 xi.u + 4.5 (xi.u)^2)
+        // source w_i F dt of lattices 1..3
+        if (COLL != 2) {
 #pragma unroll
-    for (int q = 0; q < kQ; ++q) {
-        const float xu = (float)xi_x(q) * u[0] + (float)xi_y(q) * u[1] + (float)xi_z(q) * u[2];
-        const float c1 = wq(q) * phib[q];
-        const float cx = c1 * (3.0f + 9.0f * xu);
-        ub[0] += cx * (float)xi_x(q) - 3.0f * c1 * u[0];
-        ub[1] += cx * (float)xi_y(q) - 3.0f * c1 * u[1];
-        ub[2] += cx * (float)xi_z(q) - 3.0f * c1 * u[2];
-    }
-    float betab[3] = {s.lat * ub[0], s.lat * ub[1], s.lat * ub[2]};
-    float eb[3] = {0.0f, 0.0f, 0.0f}, bb[3] = {0.0f, 0.0f, 0.0f};
-    if (forced) {
-        // F = -n (e + beta x b)
-        const float bxb[3] = {beta[1] * b[2] - beta[2] * b[1], beta[2] * b[0] - beta[0] * b[2],
-                              beta[0] * b[1] - beta[1] * b[0]};
-        nb -= Fb[0] * (e[0] + bxb[0]) + Fb[1] * (e[1] + bxb[1]) + Fb[2] * (e[2] + bxb[2]);
-        for (int c = 0; c < 3; ++c) eb[c] = -n * Fb[c];
-        // d/dbeta [Fb . (beta x b)] = b x Fb ;  d/db = Fb x beta
-        betab[0] += -n * (b[1] * Fb[2] - b[2] * Fb[1]);
-        betab[1] += -n * (b[2] * Fb[0] - b[0] * Fb[2]);
-        betab[2] += -n * (b[0] * Fb[1] - b[1] * Fb[0]);
-        bb[0] = -n * (Fb[1] * beta[2] - Fb[2] * beta[1]);
-        bb[1] = -n * (Fb[2] * beta[0] - Fb[0] * beta[2]);
-        bb[2] = -n * (Fb[0] * beta[1] - Fb[1] * beta[0]);
-    }
-    // beta = p / gamma
-    {
-        const float bbv = beta[0] * betab[0] + beta[1] * betab[1] + beta[2] * betab[2];
+            for (int c = 0; c < 3; ++c) Fb[c] += sG[c + 1][lane] * s.dt;
+        }
+        float betab[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            betab[c] = s.lat * (sU[0][c][lane] + sU[1][c][lane] + sU[2][c][lane] + sU[3][c][lane]);
+        float eb[3] = {0.0f, 0.0f, 0.0f}, bb[3] = {0.0f, 0.0f, 0.0f};
+        if (forced) {
+            // F = -n (e + beta x b)
+            const float bxb[3] = {beta[1] * b[2] - beta[2] * b[1], beta[2] * b[0] - beta[0] * b[2],
+                                  beta[0] * b[1] - beta[1] * b[0]};
+            nb -= Fb[0] * (e[0] + bxb[0]) + Fb[1] * (e[1] + bxb[1]) + Fb[2] * (e[2] + bxb[2]);
+            for (int c = 0; c < 3; ++c) eb[c] = -n * Fb[c];
+            // d/dbeta [Fb . (beta x b)] = b x Fb ;  d/db = Fb x beta
+            betab[0] += -n * (b[1] * Fb[2] - b[2] * Fb[1]);
+            betab[1] += -n * (b[2] * Fb[0] - b[0] * Fb[2]);
+            betab[2] += -n * (b[0] * Fb[1] - b[1] * Fb[0]);
+            bb[0] = -n * (Fb[1] * beta[2] - Fb[2] * beta[1]);
+            bb[1] = -n * (Fb[2] * beta[0] - Fb[0] * beta[2]);
+            bb[2] = -n * (Fb[0] * beta[1] - Fb[1] * beta[0]);
+        }
+        {
+            // beta = p / gamma
+            const float bbv = beta[0] * betab[0] + beta[1] * betab[1] + beta[2] * betab[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float pb = (betab[c] - beta[c] * bbv) * igam;
+                Am[c] += pb * inn;
+                nnb -= pb * p[c] * inn;
+            }
+        }
+        if (n > s.n_floor) nb += nnb;
+        sAb[0][lane] = nb;
+        sAb[1][lane] = Am[0];
+        sAb[2][lane] = Am[1];
+        sAb[3][lane] = Am[2];
         for (int c = 0; c < 3; ++c) {
-            const float pb = (betab[c] - beta[c] * bbv) / gam;
-            Ab[c + 1] += pb / nn;
-            nnb -= pb * p[c] / nn;
+            a.ebar[c][node] = eb[c];
+            a.bbar[c][node] = bb[c];
         }
     }
-    if (n > s.n_floor) nb += nnb;
-    Ab[0] += nb;
+    __syncthreads();
 
-    for (int c = 0; c < 3; ++c) {
-        a.ebar[c][node] = eb[c];
-        a.bbar[c][node] = bb[c];
-    }
-    if (BPASS) {
-        for (int l = 0; l < kL; ++l) a.Abnd[l][node] = Ab[l];
+    // ---- this lattice's moment adjoint
+    float Ab = sAb[l][lane] + own;
+    if (SHELL) {
+        if (act) a.Abnd[l][node] = Ab;
         return;
     }
+    if (xwall) sAb[l][lane] = Ab;  // handed to the node it clamps to
+    __syncthreads();
+    if (!act || bnd) return;
     // Boundary nodes that gathered at this node add their A_bar to every
-    // population of the corresponding lattice.
+    // population of the corresponding lattice: x-wall nodes of this row from
+    // shared memory, the shell nodes from the shell pass.
     if (!PER && (x == 1 || y == 1 || z == 1 || x == g.nx - 2 || y == g.ny - 2 || z == g.nz - 2)) {
         int cx_[3], cy_[3], cz_[3];
         const int mx = wall_candidates(x, g.nx, cx_), my = wall_candidates(y, g.ny, cy_),
@@ -312,28 +409,28 @@ __global__ void __launch_bounds__(256, PWFA_ADJ_MIN_BLOCKS) adj_fluid_kernel(con
             for (int iy = 0; iy < my; ++iy)
                 for (int ix = 0; ix < mx; ++ix) {
                     if (ix == 0 && iy == 0 && iz == 0) continue;
-                    const uint32_t bo =
-                        ((uint32_t)cz_[iz] * (uint32_t)g.ny + (uint32_t)cy_[iy]) * (uint32_t)g.nx + (uint32_t)cx_[ix];
-                    for (int l = 0; l < kL; ++l) Ab[l] += a.Abnd[l][bo];
+                    const int cx = cx_[ix];
+                    if (iy == 0 && iz == 0 && !(cx == g.nx - 1 && xwall_split(g.nx))) {
+                        Ab += sAb[l][cx == 0 ? lane - 1 : lane + 1];
+                    } else {
+                        const uint32_t bo =
+                            ((uint32_t)cz_[iz] * (uint32_t)g.ny + (uint32_t)cy_[iy]) * (uint32_t)g.nx + (uint32_t)cx;
+                        Ab += a.Abnd[l][bo];
+                    }
                 }
     }
-    // keep the second read of S_bar_in (BGK, stream-only) after the sums
-    // above instead of letting it be hoisted (register pressure)
-    asm volatile("" ::: "memory");
     // transposed pull: f_i(x) = S_i(x - xi_i)  =>  S_bar_i(x - xi_i) = f_bar_i(x)
-    float* const Soutl[kL] = {a.Sbar_out, a.Sbar_out + (size_t)kQ * N, a.Sbar_out + (size_t)2 * kQ * N,
-                              a.Sbar_out + (size_t)3 * kQ * N};
+    const float mk[3] = {k3 * P[0], k3 * P[1], k3 * P[2]};
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
-        const uint32_t src = (uint32_t)src_index<PER>(g, xs, ys, zs, q);
-#pragma unroll
-        for (int l = 0; l < kL; ++l) {
-            float fb = Ab[l];
-            if (COLL == 0) fb += (1.0f - om) * Sinl[l][(uint32_t)q * N + node];
-            else if (COLL == 2) fb += Sinl[l][(uint32_t)q * N + node];
-            else fb += (float)xi_x(q) * mb[l][0] + (float)xi_y(q) * mb[l][1] + (float)xi_z(q) * mb[l][2];
-            Soutl[l][(uint32_t)q * N + src] = fb;
-        }
+        uint32_t src;
+        if (PER) src = (uint32_t)src_index<true>(g, xs, ys, zs, q);
+        else src = nodec - (uint32_t)(xi_x(q) + xi_y(q) * g.nx) - (uint32_t)xi_z(q) * sxy;
+        float fb = Ab;
+        if (COLL == 0) fb += (1.0f - om) * S[q];
+        else if (COLL == 2) fb += S[q];
+        else fb += (float)xi_x(q) * mk[0] + (float)xi_y(q) * mk[1] + (float)xi_z(q) * mk[2];
+        Sout[pop_off(q, src)] = fb;
     }
 }
 
@@ -426,7 +523,7 @@ __global__ void __launch_bounds__(256) adj_profile_kernel(Grid g, const float* S
         const double xc = 0.5 * (g.nx - 1) * dx, yc = 0.5 * (g.ny - 1) * dx;
         const double h = np > 1 ? rmax / (np - 1) : 1.0;
         for (int q = 0; q < kQ; ++q) {
-            const float sb = Sbar0[(int64_t)q * g.N + node];
+            const float sb = Sbar0[pop_off(q, (uint32_t)node)];
             if (sb == 0.0f) continue;
             int sx = x + xi_x(q), sy = y + xi_y(q);
             if (g.periodic) { sx = wrapi(sx, g.nx); sy = wrapi(sy, g.ny); }
@@ -458,15 +555,16 @@ dim3 grid_of(const Grid& g, int bx, int by) { return dim3((g.nx + bx - 1) / bx, 
 
 template <int ST, int COLL>
 cudaError_t launch_adj_fluid_t(const AdjArgs& a, cudaStream_t s) {
-    const int bx = a.f.bx, by = a.f.by;
-    const dim3 grid = grid_of(a.f.g, bx, by), block(bx, by, 1);
-    if (a.f.g.periodic) {
-        adj_fluid_kernel<ST, COLL, true, false><<<grid, block, 0, s>>>(a);
+    const Grid& g = a.f.g;
+    const dim3 rows((unsigned)(g.nx + 31) / 32, (unsigned)g.ny, (unsigned)g.nz);
+    if (g.periodic) {
+        adj_fluid_kernel<ST, COLL, true, false><<<rows, kAdjThreads, 0, s>>>(a, 0u);
     } else {
-        adj_fluid_kernel<ST, COLL, false, true><<<grid, block, 0, s>>>(a);
+        const uint32_t nb = shell_count(g);
+        adj_fluid_kernel<ST, COLL, false, true><<<(nb + 31) / 32, kAdjThreads, 0, s>>>(a, nb);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        adj_fluid_kernel<ST, COLL, false, false><<<grid, block, 0, s>>>(a);
+        adj_fluid_kernel<ST, COLL, false, false><<<rows, kAdjThreads, 0, s>>>(a, 0u);
     }
     return cudaGetLastError();
 }

@@ -329,7 +329,7 @@ int batch_build(pwfa_lbm* h) {
     const int n = (int)h->inst.size();
     if (!h->d_entries) {
         if (cudaMalloc(&h->d_entries, sizeof(BatchEntry) * n) != cudaSuccess ||
-            cudaMalloc(&h->d_steps, sizeof(int64_t) * n) != cudaSuccess) {
+            cudaMalloc(&h->d_steps, sizeof(int64_t) * (n + 2)) != cudaSuccess) {
             cudaGetLastError();
             return fail(PWFA_ERR_ALLOC, "cudaMalloc of the batch table failed");
         }
@@ -358,6 +358,7 @@ int batch_build(pwfa_lbm* h) {
         e.step = h->d_steps + i;
         steps[i] = in.steps;
     }
+    if (items > INT32_MAX) return fail(PWFA_ERR_PARAM, "batched work list longer than 2^31 tiles");
     PWFA_CUDA(cudaMemcpyAsync(h->d_entries, ent.data(), sizeof(BatchEntry) * n, cudaMemcpyHostToDevice, h->stream),
               "batch table copy");
     PWFA_CUDA(cudaMemcpyAsync(h->d_steps, steps.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream),
@@ -368,6 +369,9 @@ int batch_build(pwfa_lbm* h) {
     h->blaunch.entries = h->d_entries;
     h->blaunch.ninst = n;
     h->blaunch.nitems = items;
+    // the work counters sit after the step counters
+    h->blaunch.counters = reinterpret_cast<int*>(h->d_steps + n);
+    PWFA_CUDA(cudaMemsetAsync(h->blaunch.counters, 0, sizeof(int) * kBatchCounters, h->stream), "cudaMemsetAsync");
     PWFA_CUDA(batch_grid_size(p0.storage, p0.collision, p0.boundary == PWFA_PERIODIC, &h->blaunch.grid),
               "batch occupancy");
     if (!h->capture_stream) PWFA_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -515,8 +519,7 @@ int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_ever
     const size_t fb = fbytes_of(in), vb = vbytes_of(in);
     r.cp_stride = fb + 6 * vb;
     r.seg_stride = fb + 6 * vb;  // per step: populations, E, B (plus one trailing B)
-    const int64_t N = in.g.N;
-    const size_t adj_bytes = 2 * align_up((size_t)N * kPop * sizeof(float)) + 22 * vb + align_up(sizeof(double) * 260);
+    const size_t adj_bytes = 2 * align_up((size_t)in.g.Np * kPop * sizeof(float)) + 22 * vb + align_up(sizeof(double) * 260);
     if (cudaMalloc(&r.cp, r.cp_stride * (r.ncp + 1)) != cudaSuccess ||
         cudaMalloc(&r.seg, r.seg_stride * r.K + 3 * vb) != cudaSuccess ||
         cudaMalloc(&r.adj, adj_bytes) != cudaSuccess) {
@@ -552,7 +555,7 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
     if (np > 256) return fail(PWFA_ERR_PARAM, "the adjoint supports at most 256 profile points");
     const int64_t N = in.g.N;
     const size_t vb = vbytes_of(in);
-    const size_t sb = align_up((size_t)N * kPop * sizeof(float));
+    const size_t sb = align_up((size_t)in.g.Np * kPop * sizeof(float));
     char* p = static_cast<char*>(r.adj);
     float* Sbar[2] = {(float*)p, (float*)(p + sb)};
     p += 2 * sb;

@@ -2,8 +2,7 @@
 // one persistent launch per phase (Faraday, fused fluid, Ampere) over a
 // flattened work list of (instance, tile) items, replayed from a captured
 // CUDA graph. Each tile is 128 nodes of one z-plane in the instance's
-// autotuned shape (bx x by, bx * by = 128). CTAs take the items
-// in contiguous chunks: no inter-CTA waits.
+// autotuned shape (bx x by, bx * by = 128). No inter-CTA waits.
 #include "lbm_batch.h"
 #include "fields_node.cuh"
 #include "fluid_node.cuh"
@@ -13,16 +12,6 @@ namespace pwfa {
 namespace {
 
 constexpr int kThreads = kBatchTile;
-
-__device__ __forceinline__ int find_instance(const BatchEntry* ent, int ninst, int64_t item) {
-    int lo = 0, hi = ninst - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (ent[mid].item_begin <= item) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 // The instance table lives in constant memory: every thread of a CTA reads
 // the same entry (broadcast), so no shared-memory copy and no barrier is
@@ -36,59 +25,67 @@ struct PhaseOcc {
     static constexpr int blocks = PHASE == 1 ? 4 : 8;
 };
 
-// Each CTA owns one contiguous chunk of the work list, so it crosses an
-// instance boundary at most a few times; consecutive items of the same
-// instance run back to back.
+// Work items are handed out in order by a global counter (one atomic per
+// grab, prefetched one grab ahead), so the items in flight always form one
+// short window of the work list, as with a hardware-scheduled grid: the
+// planes pulled across (z - 1, z + 1) are still in L2 when their neighbours
+// run, however unevenly the CTAs progress. Items only grow within a CTA, so
+// each CTA walks the instance table forward. The fluid phase grabs one item
+// at a time; the light field phases grab kFieldGrab consecutive items.
+constexpr int kFieldGrab = 4;
+
 template <int ST, int COLL, bool PER, int PHASE>
-__global__ void __launch_bounds__(kThreads, PhaseOcc<PHASE>::blocks) batch_kernel(int ninst, int64_t nitems,
-                                                                                  int parity) {
-    const int64_t per = (nitems + gridDim.x - 1) / gridDim.x;
-    const int64_t i0 = (int64_t)blockIdx.x * per;
-    const int64_t i1 = i0 + per < nitems ? i0 + per : nitems;
-    int inst = 0;
-    int64_t end = 0;  // end of the current instance's items
-    int tiles_x = 1, tiles_y = 1, bx = 1, by = 1, lx = 0, ly = 0;
-    int tx = 0, ty = 0, z = 0;  // tile coordinates of the current item
+__global__ void __launch_bounds__(kThreads, PhaseOcc<PHASE>::blocks) batch_kernel(int ninst, int nitems,
+                                                                                  int parity, int* counter) {
+    constexpr int grab = PHASE == 1 ? 1 : kFieldGrab;
+    __shared__ int s_next[2];
+    if (threadIdx.x == 0) s_next[0] = atomicAdd(counter, grab);
+    __syncthreads();
+    // only the instance range is carried between items; the tile shape is
+    // re-read from the (broadcast) constant table to keep registers free
+    int inst = -1, begin = 0, end = 0;
     float zc = 0.0f;
-    for (int64_t item = i0; item < i1; ++item) {
-        if (item >= end) {
-            // entering an instance: decode the item once (divisions only here)
-            inst = find_instance(c_entries, ninst, item);
+    for (int buf = 0;; buf ^= 1) {
+        const int first = s_next[buf];
+        if (first >= nitems) break;
+        if (threadIdx.x == 0) s_next[buf ^ 1] = atomicAdd(counter, grab);
+        const int last = first + grab < nitems ? first + grab : nitems;
+        for (int item = first; item < last; ++item) {
+            if (item >= end) {
+                do {
+                    ++inst;
+                    begin = (int)c_entries[inst].item_begin;
+                    end = inst + 1 < ninst ? (int)c_entries[inst + 1].item_begin : nitems;
+                } while (item >= end);
+                if (PHASE == 2)
+                    zc = (float)(c_entries[inst].z0 + (double)(*c_entries[inst].step + 1) * c_entries[inst].dt);
+            }
             const BatchEntry& e = c_entries[inst];
-            end = inst + 1 < ninst ? c_entries[inst + 1].item_begin : nitems;
-            tiles_x = e.tiles_x;
-            tiles_y = e.tiles_y;
-            bx = e.bx;
-            by = kThreads / bx;
-            lx = (int)threadIdx.x % bx;
-            ly = (int)threadIdx.x / bx;
-            const int64_t local = item - e.item_begin;
-            const int64_t per_plane = (int64_t)tiles_x * tiles_y;
-            z = (int)(local / per_plane);
-            const int r = (int)(local - (int64_t)z * per_plane);
-            ty = r / tiles_x;
-            tx = r - ty * tiles_x;
-            if (PHASE == 2) zc = (float)(e.z0 + (double)(*e.step + 1) * e.dt);
+            const int local = item - begin;
+            const int per_plane = e.tiles_x * e.tiles_y;
+            const int z = local / per_plane;
+            const int r = local - z * per_plane;
+            const int ty = r / e.tiles_x;
+            const int bx = e.bx;
+            const int x = (r - ty * e.tiles_x) * bx + (int)threadIdx.x % bx;
+            const int y = ty * (kThreads / bx) + (int)threadIdx.x / bx;
+            const StepArgs& a = c_entries[inst].args[parity];
+            if (x < a.g.nx && y < a.g.ny) {
+                if (PHASE == 0) faraday_node<PER>(a, x, y, z);
+                else if (PHASE == 1) fluid_node<ST, COLL, PER>(a, x, y, z);
+                else ampere_node<PER>(a, x, y, z, zc);
+            }
         }
-        const StepArgs& a = c_entries[inst].args[parity];
-        const int x = tx * bx + lx;
-        const int y = ty * by + ly;
-        if (x < a.g.nx && y < a.g.ny) {
-            if (PHASE == 0) faraday_node<PER>(a, x, y, z);
-            else if (PHASE == 1) fluid_node<ST, COLL, PER>(a, x, y, z);
-            else ampere_node<PER>(a, x, y, z, zc);
-        }
-        // next item of the same instance: x tiles fastest, then y, then z
-        if (++tx == tiles_x) {
-            tx = 0;
-            if (++ty == tiles_y) { ty = 0; ++z; }
-        }
+        // every thread has read s_next[buf]; the next grab is visible
+        __syncthreads();
     }
 }
 
-__global__ void batch_advance_kernel(const BatchEntry* ent, int ninst) {
+// Advance the step counters and re-arm the phases' work counters.
+__global__ void batch_advance_kernel(const BatchEntry* ent, int ninst, int* counters) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < ninst) *ent[i].step += 1;
+    if (i < kBatchCounters) counters[i] = 0;
 }
 
 template <int ST, int COLL, bool PER>
@@ -96,10 +93,11 @@ cudaError_t launch_phase(const BatchLaunch& b, int phase, int parity, cudaStream
     const int g1 = b.grid;                                     // fluid phase
     const int gf = b.grid / PhaseOcc<1>::blocks * PhaseOcc<0>::blocks;  // field phases
     switch (phase) {
-        case 0: batch_kernel<ST, COLL, PER, 0><<<gf, kThreads, 0, s>>>(b.ninst, b.nitems, parity); break;
-        case 1: batch_kernel<ST, COLL, PER, 1><<<g1, kThreads, 0, s>>>(b.ninst, b.nitems, parity); break;
-        case 2: batch_kernel<ST, COLL, PER, 2><<<gf, kThreads, 0, s>>>(b.ninst, b.nitems, parity); break;
-        default: batch_advance_kernel<<<(b.ninst + 127) / 128, 128, 0, s>>>(b.entries, b.ninst); break;
+        case 0: batch_kernel<ST, COLL, PER, 0><<<gf, kThreads, 0, s>>>(b.ninst, (int)b.nitems, parity, b.counters); break;
+        case 1: batch_kernel<ST, COLL, PER, 1><<<g1, kThreads, 0, s>>>(b.ninst, (int)b.nitems, parity, b.counters + 1); break;
+        case 2: batch_kernel<ST, COLL, PER, 2><<<gf, kThreads, 0, s>>>(b.ninst, (int)b.nitems, parity, b.counters + 2); break;
+        case 3: batch_advance_kernel<<<(b.ninst + 127) / 128, 128, 0, s>>>(b.entries, b.ninst, b.counters); break;
+        default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

@@ -8,8 +8,8 @@ namespace pwfa {
 struct AdjArgs {
     StepArgs f;           // forward state of the reversed step: fin = S^{n-1},
                           // E = E^n, Bc = B(t_n), Bn = B(t_{n+1}), driver at t_{n+1}
-    const float* Sbar_in; // adjoint of the stored populations S^n, [76][N]
-    float* Sbar_out;      // adjoint of S^{n-1}, [76][N]
+    const float* Sbar_in; // adjoint of the stored populations S^n, population layout (FP32)
+    float* Sbar_out;      // adjoint of S^{n-1}, population layout (FP32)
     float* Ebar[3];       // in: adjoint of E^{n+1}; out: adjoint of E^n
     float* Bbar[3];       // in: adjoint of B(t_{n+1}); out: adjoint of B(t_n)
     float* Bnp[3];        // scratch: adjoint of Bn at faces
@@ -25,7 +25,7 @@ struct AdjArgs {
 cudaError_t launch_adjoint_step(const AdjArgs& a, int storage, int collision, cudaStream_t s);
 
 // Profile gradient from the adjoint of the initial stored populations
-// (lattice 0 planes Sbar, [19][N]); n_profile <= 256.
+// (lattice 0 block of Sbar, population layout); n_profile <= 256.
 cudaError_t launch_adjoint_profile(const Grid& g, const float* Sbar, float n0, int n_profile, double rmax,
                                    double dx, double* grad_profile, cudaStream_t s);
 

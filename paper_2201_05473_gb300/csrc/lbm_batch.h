@@ -7,6 +7,7 @@ namespace pwfa {
 
 constexpr int kBatchTile = 128;  // nodes (threads) per work item
 constexpr int kMaxBatch = 96;    // instances per batched launch (constant-memory table)
+constexpr int kBatchCounters = 3; // work counters of the Faraday, fluid and Ampere phases
 
 // One instance of the batch, in device memory.
 struct BatchEntry {
@@ -23,10 +24,12 @@ struct BatchLaunch {
     int ninst;
     int64_t nitems;
     int grid;            // persistent CTAs (SMs x resident blocks)
+    int* counters;       // kBatchCounters work counters, zero before each phase
+                         // (re-armed by the step-counter kernel)
 };
 
 // One phase of a step of every instance: 0 Faraday, 1 fluid, 2 Ampere,
-// 3 advance the step counters.
+// 3 advance the step counters and re-arm the work counters.
 cudaError_t launch_batch_phase(const BatchLaunch& b, int phase, int parity, int storage, int collision,
                                bool periodic, cudaStream_t s);
 
