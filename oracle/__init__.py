@@ -56,6 +56,7 @@ class _Params(ctypes.Structure):
         ("alpha", ctypes.c_double), ("sigma_r", ctypes.c_double), ("sigma_z", ctypes.c_double),
         ("z0", ctypes.c_double),
         ("n_floor", ctypes.c_double),
+        ("moving_window", ctypes.c_int32), ("window_z", ctypes.c_double),
     ]
 
 
@@ -69,6 +70,10 @@ def _load():
             lib.oracle_create.argtypes = [ctypes.POINTER(_Params)]
             lib.oracle_destroy.argtypes = [ctypes.c_void_p]
             lib.oracle_step.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+            lib.oracle_step.restype = ctypes.c_int
+            lib.oracle_window_planes.restype = ctypes.c_int64
+            lib.oracle_window_planes.argtypes = [ctypes.c_void_p]
+            lib.oracle_set_source.argtypes = [ctypes.c_void_p, dp]
             lib.oracle_steps_done.restype = ctypes.c_int64
             lib.oracle_steps_done.argtypes = [ctypes.c_void_p]
             for name in ("oracle_get_f", "oracle_set_f", "oracle_set_equilibrium",
@@ -96,7 +101,7 @@ class Oracle:
 
     def __init__(self, nx, ny, nz, dx, dt, tau, collision=COLL_BGK, boundary=BND_OPEN,
                  couple=1, n0=1.0, profile=None, profile_rmax=0.0, alpha=0.0,
-                 sigma_r=0.5, sigma_z=0.5, z0=0.0, n_floor=1e-6):
+                 sigma_r=0.5, sigma_z=0.5, z0=0.0, n_floor=1e-6, moving_window=0, window_z=0.0):
         self._lib = _load()
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -105,13 +110,14 @@ class Oracle:
         p = _Params(nx, ny, nz, dx, dt, tau, collision, boundary, couple, n0,
                     _ptr(prof) if prof is not None else None,
                     0 if prof is None else len(prof), profile_rmax,
-                    alpha, sigma_r, sigma_z, z0, n_floor)
+                    alpha, sigma_r, sigma_z, z0, n_floor, int(moving_window), window_z)
         self._h = self._lib.oracle_create(ctypes.byref(p))
         if not self._h:
             raise ValueError("oracle_create rejected the parameters")
         self.params = dict(nx=nx, ny=ny, nz=nz, dx=dx, dt=dt, tau=tau, collision=collision,
                            boundary=boundary, couple=couple, n0=n0, alpha=alpha,
-                           sigma_r=sigma_r, sigma_z=sigma_z, z0=z0, n_floor=n_floor)
+                           sigma_r=sigma_r, sigma_z=sigma_z, z0=z0, n_floor=n_floor,
+                           moving_window=moving_window, window_z=window_z)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -125,7 +131,20 @@ class Oracle:
             pass
 
     def step(self, n: int = 1):
-        self._lib.oracle_step(self._h, int(n))
+        if self._lib.oracle_step(self._h, int(n)) != 0:
+            raise RuntimeError("oracle step failed: a window move needs the streaming source "
+                               "(not available after set_f / set_equilibrium)")
+
+    @property
+    def window_planes(self) -> int:
+        """Planes the moving window has advanced (0 without a window)."""
+        return int(self._lib.oracle_window_planes(self._h))
+
+    def set_source(self, fs: np.ndarray):
+        """Set the streaming source (post-collision populations) and pull the
+        pre-collision state from it."""
+        fs = np.ascontiguousarray(fs, dtype=np.float64).reshape((4, 19) + self.shape)
+        self._lib.oracle_set_source(self._h, _ptr(fs))
 
     @property
     def steps_done(self) -> int:
@@ -185,7 +204,7 @@ def tangent_run(nsteps, dirs, nx, ny, nz, dx, dt, tau, collision=COLL_BGK, bound
     prof = None if profile is None else np.ascontiguousarray(profile, dtype=np.float64)
     p = _Params(nx, ny, nz, dx, dt, tau, collision, boundary, couple, n0,
                 _ptr(prof) if prof is not None else None, 0 if prof is None else len(prof),
-                profile_rmax, alpha, sigma_r, sigma_z, z0, n_floor)
+                profile_rmax, alpha, sigma_r, sigma_z, z0, n_floor, 0, 0.0)
     nd = dirs.shape[0]
     assert dirs.shape[1] == 3 + (0 if prof is None else len(prof))
     E = np.empty((3, nz, ny, nx))

@@ -45,6 +45,18 @@
  * perfectly conducting walls for the fields (tangential E and normal B stay
  * zero on the six outer planes); "periodic" wraps every axis.
  *
+ * Moving window (Sec. II: the simulation box moves with the driver; open
+ * mode only). After n steps the box has moved W_n = max(0, floor((z0 + n dt
+ * - window_z) / dx)) planes along +z, so the driver centre, once it reaches
+ * window_z, stays within one cell of it. A step n with W_{n+1} > W_n first
+ * moves the box one plane: the streaming source (the post-collision
+ * populations of the previous step), E and the current B level move down one
+ * plane, the bottom plane leaves the box, the top plane is filled with
+ * unperturbed plasma at rest (the streaming source of the initial state,
+ * zero fields), the conducting walls are imposed on the moved fields, and the
+ * pre-collision populations are pulled again from the moved source. The
+ * step then runs as usual, the driver evaluated at lab position z + W dx.
+ *
  * The scalar type is a template parameter so that the same step can run on
  * forward-mode dual numbers for derivatives.
  */
@@ -130,6 +142,8 @@ typedef struct {
     double profile_rmax;
     double alpha, sigma_r, sigma_z, z0; /* driver: peak n_b/n0, rms sizes, centre at t=0 */
     double n_floor;
+    int32_t moving_window; /* 1: the box follows the driver (open mode only) */
+    double window_z;       /* box position held by the driver centre once reached */
 } oracle_params;
 }
 
@@ -149,6 +163,8 @@ struct Sim {
     std::vector<S> Jn[3];              // node current of the last step
     std::vector<S> Fn[4];              // node source of the last step
     std::vector<S> EN[3], BN[3];       // node fields used by the last step
+    bool fs_valid = true;              // fs is the streaming source of f
+    bool shift_failed = false;         // a window move found no valid source
 
     int64_t idx(int i, int j, int k) const { return ((int64_t)k * ny + j) * nx + i; }
     bool periodic() const { return p.boundary == BND_PERIODIC; }
@@ -231,7 +247,31 @@ struct Sim {
                     S n = S(p.n0) * profile_at(radius(ic, jc));
                     S* fnode = &f[idx(i, j, k) * NL * NQ];
                     for (int q = 0; q < NQ; ++q) fnode[q] = S(weight(q)) * n;
+                    fresh_source(i, j, &fs[idx(i, j, k) * NL * NQ]);
                 }
+        fs_valid = true;
+    }
+
+    // Streaming source of the plasma at rest: the post-collision populations
+    // whose pull gives f = w_i n0 prof(r) at every node, i.e. f*_i(x) =
+    // w_i n0 prof(r(x + xi_i)) on lattice 0 (transverse position wrapped, or
+    // clamped to the interior on open grids) and zero on the momentum lattices.
+    void fresh_source(int i, int j, S* fnode) const {
+        for (int l = 0; l < NL; ++l)
+            for (int q = 0; q < NQ; ++q) fnode[l * NQ + q] = S(0.0);
+        for (int q = 0; q < NQ; ++q) {
+            int si = i + XI[q][0], sj = j + XI[q][1];
+            if (periodic()) { si = wrap(si, nx); sj = wrap(sj, ny); }
+            else { si = clampi(si, 1, nx - 2); sj = clampi(sj, 1, ny - 2); }
+            fnode[q] = S(weight(q)) * S(p.n0) * profile_at(radius(si, sj));
+        }
+    }
+
+    // Planes the moving window has advanced after n steps.
+    int64_t window_planes(int64_t n) const {
+        if (!p.moving_window) return 0;
+        const double v = std::floor((p.z0 + (double)n * p.dt - p.window_z) / p.dx);
+        return v > 0.0 ? (int64_t)v : 0;
     }
 
     // Driver density n_b at (x, y, z) and time t: alpha * exp(-r^2/2 sr^2 - (z - z0 - t)^2 / 2 sz^2).
@@ -386,6 +426,7 @@ struct Sim {
         const S c(p.dt / p.dx);
         const S dt(p.dt);
         const double t1 = (step_count + 1) * p.dt;
+        const int64_t zshift = window_planes(step_count + 1);  // box position at t_{n+1}
 #pragma omp parallel for schedule(static)
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
@@ -404,13 +445,49 @@ struct Sim {
                     if (act_ez(i, j, k)) {
                         S curl = (at(Bn[1], i, j, k) - at(Bn[1], i - 1, j, k)) - (at(Bn[0], i, j, k) - at(Bn[0], i, j - 1, k));
                         S Je = S(0.5) * (at(Jn[2], i, j, k) + at(Jn[2], i, j, k + 1));
-                        S Jb = -driver(i * p.dx, j * p.dx, (k + 0.5) * p.dx, t1);
+                        S Jb = -driver(i * p.dx, j * p.dx, (k + 0.5 + (double)zshift) * p.dx, t1);
                         E[2][o] = E[2][o] + c * curl - dt * (Je + Jb);
                     }
                 }
     }
 
+    // Move the box one plane along +z (see the header).
+    void shift_window() {
+        std::vector<S> src(fs.size());
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    S* d = &src[idx(i, j, k) * NL * NQ];
+                    if (k + 1 < nz) {
+                        const S* s = &fs[idx(i, j, k + 1) * NL * NQ];
+                        for (int m = 0; m < NL * NQ; ++m) d[m] = s[m];
+                    } else {
+                        fresh_source(i, j, d);
+                    }
+                }
+        fs.swap(src);
+        stream();
+        f.swap(fn);
+        for (int c = 0; c < 3; ++c) {
+            std::vector<S> e(N, S(0.0)), b(N, S(0.0));
+            for (int k = 0; k + 1 < nz; ++k)
+                for (int j = 0; j < ny; ++j)
+                    for (int i = 0; i < nx; ++i) {
+                        const bool ae = c == 0 ? act_ex(i, j, k) : (c == 1 ? act_ey(i, j, k) : act_ez(i, j, k));
+                        const bool ab = c == 0 ? act_bx(i, j, k) : (c == 1 ? act_by(i, j, k) : act_bz(i, j, k));
+                        if (ae) e[idx(i, j, k)] = E[c][idx(i, j, k + 1)];
+                        if (ab) b[idx(i, j, k)] = B[c][idx(i, j, k + 1)];
+                    }
+            E[c].swap(e);
+            B[c].swap(b);
+        }
+    }
+
     void step() {
+        if (p.moving_window && window_planes(step_count + 1) > window_planes(step_count)) {
+            if (!fs_valid || periodic()) { shift_failed = true; return; }
+            shift_window();
+        }
         if (p.couple) faraday();
         else for (int c = 0; c < 3; ++c) Bn[c] = B[c];
         collide();
@@ -418,6 +495,7 @@ struct Sim {
         if (p.couple) ampere();
         for (int c = 0; c < 3; ++c) B[c].swap(Bn[c]);
         f.swap(fn);
+        fs_valid = true;
         ++step_count;
     }
 };
@@ -450,8 +528,29 @@ void oracle_destroy(void* h) { delete static_cast<Sim<double>*>(h); }
 
 int oracle_step(void* h, int32_t nsteps) {
     Sim<double>* s = static_cast<Sim<double>*>(h);
-    for (int n = 0; n < nsteps; ++n) s->step();
+    for (int n = 0; n < nsteps; ++n) {
+        s->step();
+        if (s->shift_failed) return -1;
+    }
     return 0;
+}
+
+/* Planes the moving window has advanced so far (0 without a window). */
+int64_t oracle_window_planes(void* h) {
+    Sim<double>* s = static_cast<Sim<double>*>(h);
+    return s->window_planes(s->step_count);
+}
+
+/* Set the streaming source (post-collision populations, [lattice][q][z][y][x])
+ * and pull the pre-collision state from it (Eq. 6, Eq. 14). */
+void oracle_set_source(void* h, const double* in) {
+    Sim<double>* s = static_cast<Sim<double>*>(h);
+    for (int l = 0; l < NL; ++l)
+        for (int q = 0; q < NQ; ++q)
+            for (int64_t o = 0; o < s->N; ++o) s->fs[o * NL * NQ + l * NQ + q] = in[(int64_t)(l * NQ + q) * s->N + o];
+    s->stream();
+    s->f.swap(s->fn);
+    s->fs_valid = true;
 }
 
 int64_t oracle_steps_done(void* h) { return static_cast<Sim<double>*>(h)->step_count; }
@@ -461,6 +560,7 @@ void oracle_get_f(void* h, double* out) { export_f(*static_cast<Sim<double>*>(h)
 
 void oracle_set_f(void* h, const double* in) {
     Sim<double>* s = static_cast<Sim<double>*>(h);
+    s->fs_valid = false;  // the streaming source of this state is unknown
     for (int l = 0; l < NL; ++l)
         for (int q = 0; q < NQ; ++q)
             for (int64_t o = 0; o < s->N; ++o) s->f[o * NL * NQ + l * NQ + q] = in[(int64_t)(l * NQ + q) * s->N + o];
@@ -469,6 +569,7 @@ void oracle_set_f(void* h, const double* in) {
 /* f = f^eq(A, u(A)) at every node, A given as [4][z][y][x]. */
 void oracle_set_equilibrium(void* h, const double* A) {
     Sim<double>* s = static_cast<Sim<double>*>(h);
+    s->fs_valid = false;
     const double lat = s->p.dt / s->p.dx;
     for (int64_t o = 0; o < s->N; ++o) {
         double Al[NL];
