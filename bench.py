@@ -310,6 +310,38 @@ def run_ours(args):
                     "fluid_kernel_GBs": (76 * 2 * 2 + 48) * N / (fl_ms * 1e-3) / 1e9,
                     "kernel_ms_per_step": {k: k2[k] / max(l2[k], 1) for k in k2 if l2[k]},
                     "finite": bool(d2[7] == 0)}
+        # ---- moving window: the same workload with the box following the
+        # driver from the first step (one plane every dx / dt = 5.67 steps)
+        window_line = None
+        if not args.no_extra and args.only in ("", "window"):
+            torch.cuda.empty_cache()
+            ww = w.replace(moving_window=1, window_z=w.z0)
+            sim = lbm.Simulation(ww, stream=stream)
+            sim.step(args.warmup)
+            sim.autotune(3)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0 = sim.window_planes()
+            e0.record(stream)
+            sim.step(args.steps)
+            e1.record(stream)
+            stream.synchronize()
+            msw = e0.elapsed_time(e1)
+            moved = sim.window_planes() - p0
+            sim.kernel_times()
+            sim.profile(True)
+            sim.step(args.steps)
+            kw_, lw_ = sim.kernel_times()
+            sim.profile(False)
+            dw = sim.diag(check=False)
+            sim.close()
+            window_line = {"value": N * args.steps / (msw * 1e-3) / 1e9, "unit": "GLUPS",
+                           "vs_fixed_box": ms / msw, "planes_moved": moved, "steps": args.steps,
+                           "move_kernel_ms": kw_["aux"] / max(lw_["aux"], 1),
+                           "fluid_kernel_ms": kw_["fluid"] / max(lw_["fluid"], 1),
+                           "note": "box follows the driver; each move: E and B moved by a kernel "
+                                   "(24 B/node), populations read one plane up inside the fluid kernel",
+                           "finite": bool(dw[7] == 0)}
         # ---- adjoint: the differentiable form (256x128x128, 500 steps,
         # checkpoints every 23 steps, witness loss)
         adjoint_line = None
@@ -410,6 +442,7 @@ def run_ours(args):
         "storage_forms": storage_lines or None,
         "adjoint": adjoint_line,
         "batched": batch_line,
+        "moving_window": window_line,
         "clocks": clk.summary(),
         "diag_after": {"sum_n": diag[0], "min_n": diag[5], "max_beta": diag[6], "nonfinite": diag[7]},
     }
@@ -469,7 +502,7 @@ def main():
     ap.add_argument("--grid", default="", help="override the grid as ZxYxX (profiling captures)")
     ap.add_argument("--no-extra", action="store_true", help="skip the BF16/FP16 and adjoint lines")
     ap.add_argument("--adjoint-steps", type=int, default=500)
-    ap.add_argument("--only", default="", choices=["", "storage", "adjoint", "batched"],
+    ap.add_argument("--only", default="", choices=["", "storage", "adjoint", "batched", "window"],
                     help="with a small --steps: run the main pass and one extra section (profiling captures)")
     ap.add_argument("--report", default="", choices=["", "precision"],
                     help="precision: error table of BF16/FP16/FP32 storage against the oracle")

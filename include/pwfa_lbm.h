@@ -97,6 +97,19 @@ typedef struct {
     double sigma_z;        /* driver rms length, > 0 */
     double z0;             /* driver centre at t = 0; it moves as z0 + t */
     double n_floor;        /* p = A / max(n, n_floor); 0 selects 1e-6 */
+    int32_t moving_window; /* 1: the box follows the driver (Sec. II's moving
+                              window; open boundary, single-instance stepping
+                              and no adjoint recording). After n steps it has
+                              moved W_n = max(0, floor((z0 + n dt - window_z)
+                              / dx)) planes along +z: a step with W_{n+1} >
+                              W_n first moves the streaming source, E and B
+                              down one plane, drops the bottom plane and
+                              fills the top plane with the initial plasma at
+                              rest and zero fields (conducting walls imposed
+                              on the moved fields), then steps as usual with
+                              the driver at its lab position. 0: fixed box. */
+    double window_z;       /* box coordinate at which the driver centre is held
+                              once the window moves (c/omega_p) */
 } pwfa_lbm_params;
 
 typedef struct pwfa_lbm pwfa_lbm_t;
@@ -203,11 +216,15 @@ int pwfa_lbm_set_state(pwfa_lbm_t* h, int32_t instance, const float* f,
 /* Steps taken by an instance so far (>= 0), or a negative error code. */
 int64_t pwfa_lbm_steps_done(pwfa_lbm_t* h, int32_t instance);
 
+/* Planes the moving window of an instance has advanced so far (0 for a fixed
+ * box), or a negative error code: box node k sits at lab z = (k + W) dx. */
+int64_t pwfa_lbm_window_planes(pwfa_lbm_t* h, int32_t instance);
+
 /* Kernel kinds reported by pwfa_lbm_kernel_times. */
 #define PWFA_KERNEL_FARADAY 0 /* Yee B update */
 #define PWFA_KERNEL_FLUID 1   /* fused stream + moments + source + collide */
 #define PWFA_KERNEL_AMPERE 2  /* Yee E update with plasma and driver current */
-#define PWFA_KERNEL_AUX 3     /* batched path: per-instance step counters */
+#define PWFA_KERNEL_AUX 3     /* step counters of the batched path, moving-window field moves */
 #define PWFA_KERNEL_KINDS 4
 
 /* Per-kernel device timing, off by default. While enabled, each step records

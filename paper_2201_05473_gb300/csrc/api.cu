@@ -47,6 +47,7 @@ struct Instance {
     void* f[2] = {nullptr, nullptr};
     int fcur = 0;
     float* E[3] = {nullptr, nullptr, nullptr};
+    float* Ealt[3] = {nullptr, nullptr, nullptr};  // moving window: E is moved into it
     float* B[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int bcur = 0;
     float* J[3] = {nullptr, nullptr, nullptr};
@@ -105,6 +106,14 @@ struct pwfa_lbm {
 
 namespace {
 
+// Planes the moving window has advanced after n steps: the window starts
+// when the driver centre z0 + t passes window_z and then keeps it there.
+int64_t window_planes_at(const pwfa_lbm_params& p, int64_t n) {
+    if (!p.moving_window) return 0;
+    const double v = std::floor((p.z0 + (double)n * p.dt - p.window_z) / p.dx);
+    return v > 0.0 ? (int64_t)v : 0;
+}
+
 int validate(const pwfa_lbm_params& p, int idx) {
     char buf[256];
     auto bad = [&](const char* what) {
@@ -113,8 +122,9 @@ int validate(const pwfa_lbm_params& p, int idx) {
     };
     if (p.nx < 3 || p.ny < 3 || p.nz < 3) return bad("nx, ny, nz must be >= 3");
     if ((int64_t)p.nx * p.ny > (int64_t)1 << 30 || p.nz > 65535) return bad("grid too large");
-    // one lattice's 19 planes are addressed with 32-bit element offsets
-    if (((int64_t)p.nx * p.ny * p.nz + 31) / 32 * 32 * 19 >= ((int64_t)1 << 32))
+    // one lattice's 19 planes (plus the window's fresh plane) are addressed
+    // with 32-bit element offsets
+    if (((int64_t)p.nx * p.ny * (p.nz + 1) + 31) / 32 * 32 * 19 >= ((int64_t)1 << 32))
         return bad("grid too large (nodes * 19 >= 2^32)");
     if (!(p.dx > 0) || !std::isfinite(p.dx)) return bad("dx must be > 0");
     if (!(p.dt >= 0) || !std::isfinite(p.dt)) return bad("dt must be >= 0 (0 = default)");
@@ -135,6 +145,9 @@ int validate(const pwfa_lbm_params& p, int idx) {
     if (!(p.sigma_r > 0) || !(p.sigma_z > 0)) return bad("sigma_r and sigma_z must be > 0");
     if (!std::isfinite(p.z0)) return bad("z0 must be finite");
     if (!(p.n_floor >= 0)) return bad("n_floor must be >= 0");
+    if (p.moving_window < 0 || p.moving_window > 1) return bad("moving_window must be 0 or 1");
+    if (p.moving_window && p.boundary != PWFA_OPEN) return bad("the moving window needs the open boundary");
+    if (p.moving_window && !std::isfinite(p.window_z)) return bad("window_z must be finite");
     return PWFA_OK;
 }
 
@@ -168,7 +181,10 @@ StepArgs make_args(const Instance& in) {
     a.alpha = (float)p.alpha;
     a.inv2sr2 = (float)(1.0 / (2.0 * p.sigma_r * p.sigma_r));
     a.inv2sz2 = (float)(1.0 / (2.0 * p.sigma_z * p.sigma_z));
-    a.zc = (float)(p.z0 + (double)(in.steps + 1) * p.dt);  // driver centre at t_{n+1}
+    // driver centre at t_{n+1}, in box coordinates
+    const int64_t w1 = window_planes_at(p, in.steps + 1);
+    a.zc = (float)(p.z0 + (double)(in.steps + 1) * p.dt - (double)w1 * p.dx);
+    a.src_shift = w1 > window_planes_at(p, in.steps) ? (uint32_t)(in.g.nx * in.g.ny) : 0u;
     a.dx = (float)p.dx;
     a.bx = in.bx;
     a.by = in.by;
@@ -219,7 +235,8 @@ int alloc_instance(Instance& in, cudaStream_t s) {
     const size_t pad = align_up((size_t)in.g.nx * in.g.ny * sizeof(float));
     const size_t vbytes = pad + align_up((size_t)N * sizeof(float));
     const size_t pbytes = align_up(sizeof(double) * (in.profile.empty() ? 1 : in.profile.size()));
-    const size_t total = 2 * fbytes + 12 * vbytes + pbytes;  // f x2, E 3, B 2x3, J 3
+    const int nvec = 12 + (in.p.moving_window ? 3 : 0);  // E 3, B 2x3, J 3 (+ E for the window move)
+    const size_t total = 2 * fbytes + nvec * vbytes + pbytes;
     if (cudaMalloc(&in.arena, total) != cudaSuccess) {
         cudaGetLastError();
         in.arena = nullptr;
@@ -235,18 +252,23 @@ int alloc_instance(Instance& in, cudaStream_t s) {
     for (int t = 0; t < 2; ++t)
         for (int c = 0; c < 3; ++c) { in.B[t][c] = (float*)(base + pad); base += vbytes; }
     for (int c = 0; c < 3; ++c) { in.J[c] = (float*)(base + pad); base += vbytes; }
+    if (in.p.moving_window)
+        for (int c = 0; c < 3; ++c) { in.Ealt[c] = (float*)(base + pad); base += vbytes; }
     in.d_profile = (double*)base;
     // Fields, currents, their guard planes and the second population buffer
     // start at zero.
     PWFA_CUDA(cudaMemsetAsync(in.f[1], 0, fbytes, s), "cudaMemsetAsync");
-    PWFA_CUDA(cudaMemsetAsync(fields, 0, 12 * vbytes, s), "cudaMemsetAsync");
+    PWFA_CUDA(cudaMemsetAsync(fields, 0, nvec * vbytes, s), "cudaMemsetAsync");
     if (!in.profile.empty())
         PWFA_CUDA(cudaMemcpyAsync(in.d_profile, in.profile.data(), sizeof(double) * in.profile.size(),
                                   cudaMemcpyHostToDevice, s),
                   "cudaMemcpyAsync profile");
-    PWFA_CUDA(launch_init(in.g, in.f[0], in.p.storage, (float)in.p.n0, in.d_profile, (int)in.profile.size(),
-                          in.p.profile_rmax, in.p.dx, s),
-              "init kernel");
+    // both ping-pong buffers carry the fresh-plasma plane above the box that
+    // a moving window pulls from
+    for (int b = 0; b < (in.p.moving_window ? 2 : 1); ++b)
+        PWFA_CUDA(launch_init(in.g, in.f[b], in.p.storage, (float)in.p.n0, in.d_profile, (int)in.profile.size(),
+                              in.p.profile_rmax, in.p.dx, s),
+                  "init kernel");
     return PWFA_OK;
 }
 
@@ -309,7 +331,7 @@ bool batch_eligible(const pwfa_lbm* h) {
     const auto& p0 = h->inst[0].p;
     for (const auto& in : h->inst)
         if (in.p.storage != p0.storage || in.p.collision != p0.collision || in.p.boundary != p0.boundary ||
-            in.p.couple != p0.couple)
+            in.p.couple != p0.couple || in.p.moving_window)
             return false;
     return true;
 }
@@ -448,6 +470,22 @@ int batch_steps(pwfa_lbm* h, int32_t nsteps) {
 
 int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
     cudaStream_t s = h->stream;
+    if (window_planes_at(in.p, in.steps + 1) > window_planes_at(in.p, in.steps)) {
+        // move the box one plane: E and the current B level here, the
+        // populations inside the fluid kernel (src_shift)
+        WindowMove w{};
+        w.g = in.g;
+        for (int c = 0; c < 3; ++c) {
+            w.E[c] = in.E[c];
+            w.B[c] = in.B[in.bcur][c];
+            w.Eo[c] = in.Ealt[c];
+            w.Bo[c] = in.B[1 - in.bcur][c];
+        }
+        int rc = timed_launch(h, PWFA_KERNEL_AUX, "window move kernel", [&] { return launch_window_move(w, s); });
+        if (rc) return rc;
+        for (int c = 0; c < 3; ++c) std::swap(in.E[c], in.Ealt[c]);
+        in.bcur = 1 - in.bcur;
+    }
     StepArgs a = make_args(in);
     int rc;
     if (in.p.couple) {
@@ -510,6 +548,7 @@ int copy_state(const Instance& in, const StateRef& dst, bool to_rec, cudaStream_
 
 int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_every) {
     cudaStream_t s = h->stream;
+    if (in.p.moving_window) return fail(PWFA_ERR_PARAM, "the adjoint does not support the moving window");
     free_recording(in);
     auto& r = in.rec;
     r.T = nsteps;
@@ -767,7 +806,8 @@ int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances, void* cu
         in.p.profile = nullptr;
         in.g.nx = in.p.nx; in.g.ny = in.p.ny; in.g.nz = in.p.nz;
         in.g.N = (int64_t)in.p.nx * in.p.ny * in.p.nz;
-        in.g.Np = (in.g.N + 31) / 32 * 32;
+        // with a moving window one more plane (fresh plasma above the box)
+        in.g.Np = (in.g.N + (in.p.moving_window ? (int64_t)in.p.nx * in.p.ny : 0) + 31) / 32 * 32;
         in.g.periodic = in.p.boundary == PWFA_PERIODIC;
         rc = alloc_instance(in, h->stream);
     }
@@ -942,6 +982,13 @@ int64_t pwfa_lbm_steps_done(pwfa_lbm_t* h, int32_t instance) {
     return h->inst[instance].steps;
 }
 
+int64_t pwfa_lbm_window_planes(pwfa_lbm_t* h, int32_t instance) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    const Instance& in = h->inst[instance];
+    return window_planes_at(in.p, in.steps);
+}
+
 int pwfa_lbm_profile(pwfa_lbm_t* h, int32_t enable) {
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
     if (enable && h->events.empty()) {
@@ -1033,6 +1080,7 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
             in.by = c[1];
             in.variant = c[2];
             StepArgs a = make_args(in);
+            a.src_shift = 0;  // time a plain step even if the next one moves the window
             cudaError_t e = launch_fluid(a, in.p.storage, in.p.collision, h->stream);  // warm
             if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
             for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_fluid(a, in.p.storage, in.p.collision, h->stream);

@@ -32,12 +32,14 @@ __device__ double profile_at(const double* prof, int np, double rmax, double r) 
 // Stored array S with S_i(y) = f^0_i(y + xi_i): pulling it yields the plasma
 // at rest f^0 = w_i n0 prof(r) (lattice 0) and 0 (momentum lattices). Open
 // grids clamp y + xi_i to the interior (such entries are only pulled by
-// interior nodes, for which the clamp is the identity).
+// interior nodes, for which the clamp is the identity). Every population
+// node up to Np is written: the plane above the box (present with a moving
+// window) keeps this fresh plasma for good.
 template <int ST>
 __global__ void init_kernel(Grid g, typename Codec<ST>::T* f, float n0, const double* prof, int np,
                             double rmax, double dx) {
     const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= g.N) return;
+    if (node >= g.Np) return;
     int x, y, z;
     node_xyz(g, node, x, y, z);
     const double xc = 0.5 * (g.nx - 1) * dx, yc = 0.5 * (g.ny - 1) * dx;
@@ -263,7 +265,7 @@ cudaError_t launch_diag_finish(const double* partials, int64_t nparts, double* o
 cudaError_t launch_init(const Grid& g, void* f, int storage, float n0, const double* d_profile, int n_profile,
                         double profile_rmax, double dx, cudaStream_t s) {
     const int threads = 256;
-    const unsigned blocks = (unsigned)((g.N + threads - 1) / threads);
+    const unsigned blocks = (unsigned)((g.Np + threads - 1) / threads);
     switch (storage) {
         case 0: init_kernel<0><<<blocks, threads, 0, s>>>(g, (float*)f, n0, d_profile, n_profile, profile_rmax, dx); break;
         case 1: init_kernel<1><<<blocks, threads, 0, s>>>(g, (__nv_bfloat16*)f, n0, d_profile, n_profile, profile_rmax, dx); break;

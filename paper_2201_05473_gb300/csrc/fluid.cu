@@ -202,7 +202,8 @@ cudaError_t launch_staged_t(const StepArgs& a, cudaStream_t s) {
 
 template <int ST, int COLL>
 cudaError_t launch_fluid_t(const StepArgs& a, cudaStream_t s, const DiagOut* d) {
-    if (ST == 0 && a.staged && !d) return launch_staged_t<COLL>(a, s);
+    // (a window-moving step pulls one plane up: direct kernel)
+    if (ST == 0 && a.staged && !d && a.src_shift == 0) return launch_staged_t<COLL>(a, s);
     const int bx = a.bx, by = a.by;
     if (bx * by > PWFA_FLUID_MAX_THREADS || bx <= 0 || by <= 0 || (bx * by) % 32) return cudaErrorInvalidConfiguration;
     dim3 block(bx, by, 1);

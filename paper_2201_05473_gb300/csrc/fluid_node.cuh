@@ -129,7 +129,7 @@ __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int 
     using T = typename Codec<ST>::T;
     float f[kL][kQ];
     bool bnd;
-    gather<ST, PER>(a.g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+    gather<ST, PER>(a.g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, a.src_shift);
     fluid_compute<ST, COLL, PER, DIAG>(a, x, y, z, f, bnd, nd);
 }
 

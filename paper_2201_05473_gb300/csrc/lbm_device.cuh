@@ -78,7 +78,8 @@ template <> struct Codec<2> {
 struct Grid {
     int nx, ny, nz;
     int64_t N;        // nx * ny * nz
-    int64_t Np;       // N rounded up to a multiple of 32 (population chunks)
+    int64_t Np;       // population nodes: N (plus, with a moving window, one
+                      // trailing plane of fresh plasma) rounded up to 32
     int periodic;     // 1: every axis wraps; 0: open (Eq. 14) + conducting walls
 };
 
@@ -111,6 +112,9 @@ struct StepArgs {
     int couple;
     // driver: J_b,z = -alpha exp(-r^2/(2 sr^2) - (z - zc)^2/(2 sz^2)) at t_{n+1}
     float alpha, inv2sr2, inv2sz2, zc, dx;
+    uint32_t src_shift;   // added to every pulled source node: nx*ny on a step
+                          // that moves the window (the streaming source is
+                          // read one plane up), else 0
     int bx, by;           // fluid kernel block shape (autotuned per instance)
     int staged;           // 1: software-pipelined fluid kernel (FP32 storage), 128-thread tiles
 };

@@ -36,6 +36,17 @@ cudaError_t launch_ampere(const StepArgs& a, cudaStream_t s);
 // the conducting walls (tangential E, normal B, components past the grid).
 cudaError_t launch_zero_walls(const StepArgs& a, cudaStream_t s);
 
+// Moving window (open grids): Eo, Bo := E, B moved down one plane (box node
+// k takes node k + 1), zero on the top plane and on the conducting walls.
+struct WindowMove {
+    Grid g;
+    const float* E[3];
+    const float* B[3];
+    float* Eo[3];
+    float* Bo[3];
+};
+cudaError_t launch_window_move(const WindowMove& w, cudaStream_t s);
+
 // Initial condition: stored populations whose pull gives the plasma at rest,
 // f = w_i n0 prof(r) (lattice 0), 0 (momentum lattices).
 cudaError_t launch_init(const Grid& g, void* f, int storage, float n0, const double* d_profile,

@@ -18,10 +18,14 @@ __device__ __forceinline__ int64_t src_index(const Grid& g, int x, int y, int z,
 // gather at the clamped interior node instead and flag the node as a boundary
 // node: its state is then f^eq of those moments (Eq. 14). Each lattice's
 // block of 19 Np elements is addressed with 32-bit offsets (the host limits
-// the grid so that 19 Np < 2^32).
+// the grid so that 19 Np < 2^32). src_shift (open grids) moves every source
+// node by that many nodes: nx*ny pulls from one plane up, which is how a
+// moving-window step reads the moved streaming source (the plane above the
+// box holds fresh plasma).
 template <int ST, bool PER>
 __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::T* __restrict__ fin,
-                                       float n0, int x, int y, int z, float f[kL][kQ], bool& bnd) {
+                                       float n0, int x, int y, int z, float f[kL][kQ], bool& bnd,
+                                       uint32_t src_shift = 0) {
     using T = typename Codec<ST>::T;
     int xs = x, ys = y, zs = z;
     bnd = false;
@@ -34,7 +38,8 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
     const int64_t LS = lattice_stride(g);
     const T* __restrict__ fl[kL] = {fin, fin + LS, fin + 2 * LS, fin + 3 * LS};
     const uint32_t sxy = (uint32_t)g.nx * (uint32_t)g.ny;
-    const uint32_t nodec = ((uint32_t)zs * (uint32_t)g.ny + (uint32_t)ys) * (uint32_t)g.nx + (uint32_t)xs;
+    const uint32_t nodec =
+        ((uint32_t)zs * (uint32_t)g.ny + (uint32_t)ys) * (uint32_t)g.nx + (uint32_t)xs + (PER ? 0u : src_shift);
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
         uint32_t src;

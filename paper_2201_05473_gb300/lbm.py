@@ -43,6 +43,7 @@ class Params(ctypes.Structure):
         ("profile_rmax", ctypes.c_double),
         ("alpha", ctypes.c_double), ("sigma_r", ctypes.c_double), ("sigma_z", ctypes.c_double),
         ("z0", ctypes.c_double), ("n_floor", ctypes.c_double),
+        ("moving_window", ctypes.c_int32), ("window_z", ctypes.c_double),
     ]
 
 
@@ -60,7 +61,8 @@ EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_
            "pwfa_lbm_destroy", "pwfa_lbm_last_error", "pwfa_lbm_profile", "pwfa_lbm_kernel_times",
            "pwfa_lbm_set_launch", "pwfa_lbm_get_launch", "pwfa_lbm_autotune",
            "pwfa_lbm_diag_noalloc", "pwfa_lbm_record", "pwfa_lbm_adjoint_step", "pwfa_lbm_set_batching",
-           "pwfa_lbm_step_diag", "pwfa_lbm_linecut", "pwfa_lbm_set_fluid_variant", "pwfa_lbm_get_fluid_variant")
+           "pwfa_lbm_step_diag", "pwfa_lbm_linecut", "pwfa_lbm_set_fluid_variant", "pwfa_lbm_get_fluid_variant",
+           "pwfa_lbm_window_planes")
 
 
 def load(build: bool = True):
@@ -84,6 +86,8 @@ def load(build: bool = True):
         lib.pwfa_lbm_set_state.argtypes = [vp, i32, vp, vp, vp]
         lib.pwfa_lbm_steps_done.argtypes = [vp, i32]
         lib.pwfa_lbm_steps_done.restype = i64
+        lib.pwfa_lbm_window_planes.argtypes = [vp, i32]
+        lib.pwfa_lbm_window_planes.restype = i64
         lib.pwfa_lbm_set_stream.argtypes = [vp, vp]
         lib.pwfa_lbm_destroy.argtypes = [vp]
         lib.pwfa_lbm_profile.argtypes = [vp, i32]
@@ -139,6 +143,7 @@ def params_of(w: W.Workload):
         p.profile_rmax = w.profile_rmax
     p.alpha, p.sigma_r, p.sigma_z, p.z0 = w.alpha, w.sigma_r, w.sigma_z, w.z0
     p.n_floor = w.n_floor
+    p.moving_window, p.window_z = int(w.moving_window), w.window_z
     return p, keep
 
 
@@ -210,6 +215,14 @@ class Simulation:
 
     def steps_done(self, instance: int = 0) -> int:
         r = self._lib.pwfa_lbm_steps_done(self._h, instance)
+        if r < 0:
+            _check(int(r))
+        return int(r)
+
+    def window_planes(self, instance: int = 0) -> int:
+        """Planes the moving window has advanced (box node k sits at lab
+        z = (k + W) dx)."""
+        r = self._lib.pwfa_lbm_window_planes(self._h, instance)
         if r < 0:
             _check(int(r))
         return int(r)

@@ -46,6 +46,8 @@ class Workload:
     n_floor: float = 1e-6
     profile: np.ndarray | None = None
     profile_rmax: float = 0.0
+    moving_window: int = 0   # 1: the box follows the driver once it passes window_z
+    window_z: float = 0.0
     name: str = ""
 
     @property

@@ -77,6 +77,9 @@ def _create(lib, **changes):
     (dict(sigma_r=0.0), "sigma"),
     (dict(alpha=-1.0), "alpha"),
     (dict(n0=float("nan")), "n0"),
+    (dict(moving_window=2), "moving_window"),
+    (dict(moving_window=1, boundary=1), "moving window"),
+    (dict(moving_window=1, window_z=float("inf")), "window_z"),
 ])
 def test_invalid_params_rejected(lib, change, needle):
     rc, h, msg = _create(lib, **change)
