@@ -24,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pwfa_oracle.cpp")
+_SRCS = [_SRC, os.path.join(_HERE, "axi_oracle.cpp")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -35,11 +36,11 @@ BND_OPEN, BND_PERIODIC = 0, 1
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` (g++, OpenMP)."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-Wall",
-           "-o", tmp, _SRC]
+           "-o", tmp] + _SRCS
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -57,6 +58,18 @@ class _Params(ctypes.Structure):
         ("z0", ctypes.c_double),
         ("n_floor", ctypes.c_double),
         ("moving_window", ctypes.c_int32), ("window_z", ctypes.c_double),
+    ]
+
+
+class _AxiParams(ctypes.Structure):
+    _fields_ = [
+        ("nz", ctypes.c_int32), ("nr", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
+        ("collision", ctypes.c_int32), ("couple", ctypes.c_int32),
+        ("n0", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("sigma_r", ctypes.c_double), ("sigma_z", ctypes.c_double),
+        ("z0", ctypes.c_double),
+        ("n_floor", ctypes.c_double),
     ]
 
 
@@ -85,6 +98,17 @@ def _load():
             lib.oracle_tangent_run.argtypes = [ctypes.POINTER(_Params), ctypes.c_int32, ctypes.c_int32,
                                                dp, dp, dp]
             lib.oracle_tangent_run.restype = ctypes.c_int
+            lib.axi_create.restype = ctypes.c_void_p
+            lib.axi_create.argtypes = [ctypes.POINTER(_AxiParams)]
+            lib.axi_destroy.argtypes = [ctypes.c_void_p]
+            lib.axi_step.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+            lib.axi_steps_done.restype = ctypes.c_int64
+            lib.axi_steps_done.argtypes = [ctypes.c_void_p]
+            for name in ("axi_get_f", "axi_set_f", "axi_set_equilibrium", "axi_moments"):
+                getattr(lib, name).argtypes = [ctypes.c_void_p, dp]
+            lib.axi_get_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
+            lib.axi_set_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
+            lib.axi_last_current.argtypes = [ctypes.c_void_p, dp, dp]
             lib.oracle_qtilde.restype = ctypes.c_double
             lib.oracle_qtilde.argtypes = [ctypes.c_double] * 5 + [dp]
             _lib = lib
@@ -191,6 +215,78 @@ class Oracle:
         out = np.empty(8, dtype=np.float64)
         self._lib.oracle_diag(self._h, _ptr(out))
         return out
+
+
+class AxiOracle:
+    """2D-axisymmetric (z, r) FP64 simulation (see ``axi_oracle.cpp``).
+
+    Nodes (z_k, r_j), z_k = k dx, r_j = (j - 1/2) dx; row 0 mirrors the axis,
+    row nr - 1 is the outer boundary row. Arrays are ``[..][z][r]``."""
+
+    def __init__(self, nz, nr, dx, dt, tau, collision=COLL_BGK, couple=1, n0=1.0, alpha=0.0,
+                 sigma_r=0.5, sigma_z=0.5, z0=0.0, n_floor=1e-6):
+        self._lib = _load()
+        self.shape = (nz, nr)
+        self.N = nz * nr
+        p = _AxiParams(nz, nr, dx, dt, tau, collision, couple, n0, alpha, sigma_r, sigma_z, z0, n_floor)
+        self._h = self._lib.axi_create(ctypes.byref(p))
+        if not self._h:
+            raise ValueError("axi_create rejected the parameters")
+        self.params = dict(nz=nz, nr=nr, dx=dx, dt=dt, tau=tau, collision=collision, couple=couple, n0=n0,
+                           alpha=alpha, sigma_r=sigma_r, sigma_z=sigma_z, z0=z0, n_floor=n_floor)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.axi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        self._lib.axi_step(self._h, int(n))
+
+    @property
+    def steps_done(self) -> int:
+        return int(self._lib.axi_steps_done(self._h))
+
+    def radii(self) -> np.ndarray:
+        return (np.arange(self.shape[1]) - 0.5) * self.params["dx"]
+
+    def get_f(self) -> np.ndarray:
+        out = np.empty((3, 9) + self.shape)
+        self._lib.axi_get_f(self._h, _ptr(out))
+        return out
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape((3, 9) + self.shape)
+        self._lib.axi_set_f(self._h, _ptr(f))
+
+    def set_equilibrium(self, A):
+        A = np.ascontiguousarray(A, dtype=np.float64).reshape((3,) + self.shape)
+        self._lib.axi_set_equilibrium(self._h, _ptr(A))
+
+    def get_fields(self):
+        Ez, Er, Bt = (np.empty(self.shape) for _ in range(3))
+        self._lib.axi_get_fields(self._h, _ptr(Ez), _ptr(Er), _ptr(Bt))
+        return Ez, Er, Bt
+
+    def set_fields(self, Ez, Er, Bt):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape) for a in (Ez, Er, Bt)]
+        self._lib.axi_set_fields(self._h, *(_ptr(a) for a in arrs))
+
+    def moments(self) -> dict:
+        out = np.empty((6,) + self.shape)
+        self._lib.axi_moments(self._h, _ptr(out))
+        return {"n": out[0], "beta_z": out[1], "beta_r": out[2], "A": out[3:5], "beta_abs": out[5]}
+
+    def last_current(self):
+        Jz, Jr = np.empty(self.shape), np.empty(self.shape)
+        self._lib.axi_last_current(self._h, _ptr(Jz), _ptr(Jr))
+        return Jz, Jr
 
 
 def tangent_run(nsteps, dirs, nx, ny, nz, dx, dt, tau, collision=COLL_BGK, boundary=BND_OPEN,
