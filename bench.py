@@ -342,6 +342,35 @@ def run_ours(args):
                            "note": "box follows the driver; each move: E and B moved by a kernel "
                                    "(24 B/node), populations read one plane up inside the fluid kernel",
                            "finite": bool(dw[7] == 0)}
+        # ---- the paper's own geometry: 2D-axisymmetric (z, r), 2400 x 400
+        # cells at 0.25 um, Q = 0.1 (context: the paper's LBM routine ran
+        # 2.0 M cell-steps/s on a Xeon E5-2695, Table I)
+        axi_line = None
+        if not args.no_extra and args.only in ("", "axisymmetric"):
+            torch.cuda.empty_cache()
+            wa_ = W.axisymmetric_paper(0.1)
+            sa = lbm.AxiSimulation(wa_, stream=stream)
+            sa.step(args.warmup)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sa.step(args.steps)
+            e1.record(stream)
+            stream.synchronize()
+            msa = e0.elapsed_time(e1)
+            sa.kernel_times()
+            sa.profile(True)
+            sa.step(args.steps)
+            ka, la = sa.kernel_times()
+            sa.profile(False)
+            ga = sa.fields()
+            finite = bool(torch.isfinite(ga).all().item())
+            sa.close()
+            rate = wa_.nodes * args.steps / (msa * 1e-3)
+            axi_line = {"value": rate / 1e9, "unit": "GLUPS", "grid_zr": [wa_.nz, wa_.nr], "steps": args.steps,
+                        "note": "three D2Q9 lattices + cylindrical Yee per node-step",
+                        "kernel_ms_per_step": {k: ka[k] / max(la[k], 1) for k in ka if la[k]},
+                        "vs_paper_cpu_lbm_routine": rate / 2.0e6, "finite": finite}
         # ---- adjoint: the differentiable form (256x128x128, 500 steps,
         # checkpoints every 23 steps, witness loss)
         adjoint_line = None
@@ -443,6 +472,7 @@ def run_ours(args):
         "adjoint": adjoint_line,
         "batched": batch_line,
         "moving_window": window_line,
+        "axisymmetric": axi_line,
         "clocks": clk.summary(),
         "diag_after": {"sum_n": diag[0], "min_n": diag[5], "max_beta": diag[6], "nonfinite": diag[7]},
     }
@@ -502,7 +532,7 @@ def main():
     ap.add_argument("--grid", default="", help="override the grid as ZxYxX (profiling captures)")
     ap.add_argument("--no-extra", action="store_true", help="skip the BF16/FP16 and adjoint lines")
     ap.add_argument("--adjoint-steps", type=int, default=500)
-    ap.add_argument("--only", default="", choices=["", "storage", "adjoint", "batched", "window"],
+    ap.add_argument("--only", default="", choices=["", "storage", "adjoint", "batched", "window", "axisymmetric"],
                     help="with a small --steps: run the main pass and one extra section (profiling captures)")
     ap.add_argument("--report", default="", choices=["", "precision"],
                     help="precision: error table of BF16/FP16/FP32 storage against the oracle")

@@ -306,6 +306,74 @@ int pwfa_lbm_destroy(pwfa_lbm_t* h);
  * pointer stays valid until the next call on this thread. */
 const char* pwfa_lbm_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * 2D-axisymmetric (z, r) form: the paper's own geometry (Sec. III).
+ *
+ * Three D2Q9 advection-diffusion lattices on the (z, r) plane for
+ * A = (n, n p_z, n p_r) (Eq. 4), BGK collision (Eq. 7) to the equilibrium of
+ * Eq. 9 (lattice units, c_s^2 = 1/3), u = beta(p) dt/dx (Eq. 2), pull
+ * streaming (Eq. 6), and the cylindrical terms of Eq. 13 added to every
+ * lattice's source: S_i = w_i dt (F + D (1/r) dA/dr - A u_r / r), with
+ * D = (tau - 1/2)/3 dx^2/dt (Eq. 12) and dA/dr the central difference of the
+ * node moments. Fields: cylindrical Yee TM (E_z, E_r, B_theta),
+ * dB_theta/dt = dE_z/dr - dE_r/dz, dE_r/dt = -dB_theta/dz - J_r,
+ * dE_z/dt = (1/r) d(r B_theta)/dr - J_z - J_b, with J = -n beta and the rigid
+ * driver J_b = -n_b z_hat; conducting z walls and outer wall.
+ *
+ * Grid: nodes (z_k = k dx, r_j = (j - 1/2) dx), k = 0..nz-1, j = 0..nr-1;
+ * row 0 is the mirror image of row 1 (cylindrical symmetry: the axis lies
+ * between them), rows 1..nr-2 hold the plasma, row nr-1 and the planes
+ * k = 0, nz-1 are Eq. 14 boundary nodes (equilibrium of the clamped interior
+ * node). E_z sits at (z_{k+1/2}, r_j), E_r at (z_k, j dx), B_theta at
+ * (z_{k+1/2}, j dx). Arrays are [..][z][r], r fastest. Initial state: plasma
+ * at rest of density n0, zero fields. */
+typedef struct {
+    int32_t nz, nr;        /* nodes along z; rows along r including the mirror
+                              and outer rows; each >= 3 */
+    double dx;             /* dz = dr in c/omega_p, > 0 */
+    double dt;             /* 0 selects 0.17628 dx; must be < dx / sqrt(2) */
+    double tau;            /* > 0.5 */
+    int32_t collision;     /* PWFA_BGK or PWFA_STREAM_ONLY */
+    int32_t couple;        /* 1: Lorentz source + Maxwell update; 0: fluid only */
+    double n0;             /* plasma density (normalised, >= 0) */
+    double alpha, sigma_r, sigma_z, z0;  /* driver: peak n_b/n0, rms sizes, centre at t = 0 */
+    double n_floor;        /* 0 selects 1e-6 */
+} pwfa_axi_params;
+
+typedef struct pwfa_axi pwfa_axi_t;
+
+/* Allocate the device state and set the initial condition. cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream). */
+int pwfa_axi_create(const pwfa_axi_params* params, void* cuda_stream, pwfa_axi_t** out);
+
+/* Advance nsteps (>= 0): Faraday, node moments, fused fluid step, Ampere
+ * with the driver at t_{n+1}. Asynchronous on the stream. */
+int pwfa_axi_step(pwfa_axi_t* h, int32_t nsteps);
+
+/* out[6][nz][nr] (host or device FP32): n, beta_z, beta_r of the current
+ * state, then the raw Yee E_z, E_r (t_{n+1/2}) and B_theta (t_n).
+ * Synchronises the stream. */
+int pwfa_axi_fields(pwfa_axi_t* h, float* out);
+
+/* The stored streaming source (post-collision populations of the last
+ * step, [3][9][nz][nr], D2Q9 order rest, +z, -z, +r, -r, (+z,+r), (-z,-r),
+ * (+z,-r), (-z,+r)); the pre-collision state of every interior node is its
+ * pull f_i(x) = S_i(x - xi_i). Host or device FP32; synchronises. */
+int pwfa_axi_get_source(pwfa_axi_t* h, float* fs);
+int pwfa_axi_set_source(pwfa_axi_t* h, const float* fs);
+
+/* Steps taken so far (>= 0), or a negative error code. */
+int64_t pwfa_axi_steps_done(pwfa_axi_t* h);
+
+/* Accumulated device time (ms) of the step's kernels since the last call:
+ * ms[0] Faraday, ms[1] moments, ms[2] fluid, ms[3] Ampere, from CUDA event
+ * pairs recorded while enabled (pwfa_axi_profile). Synchronises. */
+int pwfa_axi_profile(pwfa_axi_t* h, int32_t enable);
+int pwfa_axi_kernel_times(pwfa_axi_t* h, double* ms, int64_t* launches);
+
+/* Release the device state. Accepts NULL. */
+int pwfa_axi_destroy(pwfa_axi_t* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,7 +104,8 @@ def _load():
             lib.axi_step.argtypes = [ctypes.c_void_p, ctypes.c_int32]
             lib.axi_steps_done.restype = ctypes.c_int64
             lib.axi_steps_done.argtypes = [ctypes.c_void_p]
-            for name in ("axi_get_f", "axi_set_f", "axi_set_equilibrium", "axi_moments"):
+            for name in ("axi_get_f", "axi_set_f", "axi_set_equilibrium", "axi_moments", "axi_get_source",
+                         "axi_set_source"):
                 getattr(lib, name).argtypes = [ctypes.c_void_p, dp]
             lib.axi_get_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
             lib.axi_set_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
@@ -268,6 +269,15 @@ class AxiOracle:
     def set_equilibrium(self, A):
         A = np.ascontiguousarray(A, dtype=np.float64).reshape((3,) + self.shape)
         self._lib.axi_set_equilibrium(self._h, _ptr(A))
+
+    def get_source(self) -> np.ndarray:
+        out = np.empty((3, 9) + self.shape)
+        self._lib.axi_get_source(self._h, _ptr(out))
+        return out
+
+    def set_source(self, fs):
+        fs = np.ascontiguousarray(fs, dtype=np.float64).reshape((3, 9) + self.shape)
+        self._lib.axi_set_source(self._h, _ptr(fs))
 
     def get_fields(self):
         Ez, Er, Bt = (np.empty(self.shape) for _ in range(3))

@@ -377,6 +377,26 @@ void axi_moments(void* h, double* out) {
     }
 }
 
+/* The streaming source (post-collision populations of the last step,
+ * [lattice][q][z][r]). */
+void axi_get_source(void* h, double* out) {
+    Axi* s = static_cast<Axi*>(h);
+    for (int l = 0; l < AL; ++l)
+        for (int q = 0; q < AQ; ++q)
+            for (int64_t o = 0; o < s->N; ++o) out[(int64_t)(l * AQ + q) * s->N + o] = s->fs[o * AL * AQ + l * AQ + q];
+}
+
+/* Set the streaming source and pull the pre-collision state from it (Eq. 6,
+ * Eq. 14 boundary rows, mirror row). */
+void axi_set_source(void* h, const double* in) {
+    Axi* s = static_cast<Axi*>(h);
+    for (int l = 0; l < AL; ++l)
+        for (int q = 0; q < AQ; ++q)
+            for (int64_t o = 0; o < s->N; ++o) s->fs[o * AL * AQ + l * AQ + q] = in[(int64_t)(l * AQ + q) * s->N + o];
+    s->stream();
+    s->f.swap(s->fn);
+}
+
 /* Node currents of the last step [z][r] (plasma only). */
 void axi_last_current(void* h, double* Jz, double* Jr) {
     Axi* s = static_cast<Axi*>(h);

@@ -47,6 +47,18 @@ class Params(ctypes.Structure):
     ]
 
 
+class AxiParams(ctypes.Structure):
+    """Mirror of ``pwfa_axi_params``."""
+    _fields_ = [
+        ("nz", ctypes.c_int32), ("nr", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
+        ("collision", ctypes.c_int32), ("couple", ctypes.c_int32),
+        ("n0", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("sigma_r", ctypes.c_double), ("sigma_z", ctypes.c_double),
+        ("z0", ctypes.c_double), ("n_floor", ctypes.c_double),
+    ]
+
+
 class LBMError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -62,7 +74,9 @@ EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_
            "pwfa_lbm_set_launch", "pwfa_lbm_get_launch", "pwfa_lbm_autotune",
            "pwfa_lbm_diag_noalloc", "pwfa_lbm_record", "pwfa_lbm_adjoint_step", "pwfa_lbm_set_batching",
            "pwfa_lbm_step_diag", "pwfa_lbm_linecut", "pwfa_lbm_set_fluid_variant", "pwfa_lbm_get_fluid_variant",
-           "pwfa_lbm_window_planes")
+           "pwfa_lbm_window_planes", "pwfa_axi_create", "pwfa_axi_step", "pwfa_axi_fields",
+           "pwfa_axi_get_source", "pwfa_axi_set_source", "pwfa_axi_steps_done", "pwfa_axi_profile",
+           "pwfa_axi_kernel_times", "pwfa_axi_destroy")
 
 
 def load(build: bool = True):
@@ -88,6 +102,19 @@ def load(build: bool = True):
         lib.pwfa_lbm_steps_done.restype = i64
         lib.pwfa_lbm_window_planes.argtypes = [vp, i32]
         lib.pwfa_lbm_window_planes.restype = i64
+        lib.pwfa_axi_create.argtypes = [ctypes.POINTER(AxiParams), vp, ctypes.POINTER(vp)]
+        lib.pwfa_axi_step.argtypes = [vp, i32]
+        lib.pwfa_axi_fields.argtypes = [vp, vp]
+        lib.pwfa_axi_get_source.argtypes = [vp, vp]
+        lib.pwfa_axi_set_source.argtypes = [vp, vp]
+        lib.pwfa_axi_steps_done.argtypes = [vp]
+        lib.pwfa_axi_steps_done.restype = i64
+        lib.pwfa_axi_profile.argtypes = [vp, i32]
+        lib.pwfa_axi_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        lib.pwfa_axi_destroy.argtypes = [vp]
+        for name in ("pwfa_axi_create", "pwfa_axi_step", "pwfa_axi_fields", "pwfa_axi_get_source",
+                     "pwfa_axi_set_source", "pwfa_axi_profile", "pwfa_axi_kernel_times", "pwfa_axi_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
         lib.pwfa_lbm_set_stream.argtypes = [vp, vp]
         lib.pwfa_lbm_destroy.argtypes = [vp]
         lib.pwfa_lbm_profile.argtypes = [vp, i32]
@@ -345,3 +372,80 @@ class Simulation:
             else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)))
         f, E, B = conv(f), conv(E), conv(B)
         _check(self._lib.pwfa_lbm_set_state(self._h, instance, _ptr(f), _ptr(E), _ptr(B)))
+
+
+class AxiSimulation:
+    """The 2D-axisymmetric (z, r) form through the ``pwfa_axi_*`` C ABI.
+
+    Nodes (z_k = k dx, r_j = (j - 1/2) dx); row 0 mirrors the axis, row nr - 1
+    and the z planes 0, nz - 1 are boundary nodes. Arrays are [..][z][r]."""
+
+    KERNELS = ("faraday", "moments", "fluid", "ampere")
+
+    def __init__(self, w: "W.AxiWorkload", stream=None):
+        import torch
+        self._torch = torch
+        self._lib = load()
+        self.work = w
+        p = AxiParams(w.nz, w.nr, w.dx, w.dt, w.tau, w.collision, w.couple, w.n0, w.alpha, w.sigma_r,
+                      w.sigma_z, w.z0, w.n_floor)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(self._lib.pwfa_axi_create(ctypes.byref(p), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pwfa_axi_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, n: int = 1):
+        _check(self._lib.pwfa_axi_step(self._h, int(n)))
+
+    def steps_done(self) -> int:
+        r = self._lib.pwfa_axi_steps_done(self._h)
+        if r < 0:
+            _check(int(r))
+        return int(r)
+
+    def fields(self):
+        """[6][nz][nr] device tensor: n, beta_z, beta_r, E_z, E_r, B_theta (raw Yee)."""
+        out = self._torch.empty((6, self.work.nz, self.work.nr), dtype=self._torch.float32, device="cuda")
+        _check(self._lib.pwfa_axi_fields(self._h, _ptr(out)))
+        return out
+
+    def get_source(self):
+        out = self._torch.empty((3, 9, self.work.nz, self.work.nr), dtype=self._torch.float32, device="cuda")
+        _check(self._lib.pwfa_axi_get_source(self._h, _ptr(out)))
+        return out
+
+    def set_source(self, fs):
+        t = self._torch
+        a = fs.contiguous().to(t.float32) if isinstance(fs, t.Tensor) else \
+            t.from_numpy(np.ascontiguousarray(fs, dtype=np.float32))
+        _check(self._lib.pwfa_axi_set_source(self._h, _ptr(a)))
+
+    def profile(self, enable: bool = True):
+        _check(self._lib.pwfa_axi_profile(self._h, 1 if enable else 0))
+
+    def kernel_times(self):
+        ms = np.zeros(4, dtype=np.float64)
+        n = np.zeros(4, dtype=np.int64)
+        _check(self._lib.pwfa_axi_kernel_times(
+            self._h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return dict(zip(self.KERNELS, ms)), dict(zip(self.KERNELS, n.tolist()))

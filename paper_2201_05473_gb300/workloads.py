@@ -151,3 +151,58 @@ def witness_slab(w: Workload, steps: int, behind: float = 1.5 * 2 * math.pi, rad
     mask[0, :] = mask[-1, :] = False
     mask[:, 0] = mask[:, -1] = False
     return k, mask
+
+
+@dataclasses.dataclass
+class AxiWorkload:
+    """One 2D-axisymmetric (z, r) simulation: nz nodes along z, nr rows along
+    r (row 0 mirrors the axis, row nr - 1 is the outer boundary row)."""
+    nz: int
+    nr: int
+    dx: float
+    tau: float
+    alpha: float
+    sigma_r: float
+    sigma_z: float
+    z0: float
+    steps: int
+    collision: int = BGK
+    couple: int = 1
+    n0: float = 1.0
+    n_floor: float = 1e-6
+    name: str = ""
+
+    @property
+    def dt(self) -> float:
+        return DT_OVER_DX * self.dx
+
+    @property
+    def nodes(self) -> int:
+        return self.nz * self.nr
+
+    def replace(self, **kw) -> "AxiWorkload":
+        return dataclasses.replace(self, **kw)
+
+
+# c / omega_p at n0 = 1e16 cm^-3, in micrometres
+KP_INV_UM = 53.14
+
+
+def axisymmetric_parity() -> AxiWorkload:
+    """The parity workload's physics in the paper's geometry: 64 x 34 (z, r
+    rows incl. the mirror and outer rows) at dx = 0.2, n_b/n0 = 0.1,
+    sigma = 0.5, BGK, 200 steps."""
+    return AxiWorkload(nz=64, nr=34, dx=0.2, tau=0.51, alpha=0.1, sigma_r=0.5, sigma_z=0.5, z0=-2.0,
+                       steps=200, name="lbm-pwfa axisymmetric 64x34 dx0.2")
+
+
+def axisymmetric_paper(qtilde: float = 0.1) -> AxiWorkload:
+    """The paper's grid (Sec. IV): 600 um x 100 um at dz = dr = 0.25 um, i.e.
+    2400 x 400 cells (+ the mirror and outer rows), dt = 0.147 fs
+    (dt = 0.17628 dx), n0 = 1e16 cm^-3; bi-Gaussian driver sigma_r = 8.9 um,
+    sigma_z = 17.7 um with the peak density of Q = 0.1 / 0.5 / 1 (Eq. 15,
+    alpha = 0.68 Q / 0.1)."""
+    dx = 0.25 / KP_INV_UM
+    return AxiWorkload(nz=2400, nr=402, dx=dx, tau=0.51, alpha=0.68 * qtilde / 0.1,
+                       sigma_r=8.9 / KP_INV_UM, sigma_z=17.7 / KP_INV_UM, z0=-4.0 * 17.7 / KP_INV_UM,
+                       steps=2000, name=f"lbm-pwfa axisymmetric 2400x400 dz0.25um Q{qtilde:g}")

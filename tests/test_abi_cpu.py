@@ -42,21 +42,23 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n)
 
 
-def test_params_layout_matches_header(tmp_path):
+@pytest.mark.parametrize("cname,pytype", [("pwfa_lbm_params", lbm.Params), ("pwfa_axi_params", lbm.AxiParams)])
+def test_params_layout_matches_header(tmp_path, cname, pytype):
     """Compile a probe against the header and compare offsets with ctypes."""
-    fields = [f[0] for f in lbm.Params._fields_]
+    fields = [f[0] for f in pytype._fields_]
     prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "pwfa_lbm.h"', "int main(void){",
-            'printf("%zu\\n", sizeof(pwfa_lbm_params));']
-    prog += [f'printf("%zu\\n", offsetof(pwfa_lbm_params, {f}));' for f in fields]
+            f'printf("%zu\\n", sizeof({cname}));']
+    prog += [f'printf("%zu\\n", offsetof({cname}, {f}));' for f in fields]
     prog += ["return 0;}"]
     c = tmp_path / "probe.c"
     c.write_text("\n".join(prog))
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    assert vals[0] == ctypes.sizeof(lbm.Params)
+    assert vals[0] == ctypes.sizeof(pytype)
+    assert len(vals) == len(fields) + 1
     for f, off in zip(fields, vals[1:]):
-        assert getattr(lbm.Params, f).offset == off, f
+        assert getattr(pytype, f).offset == off, f
 
 
 def _create(lib, **changes):
