@@ -346,8 +346,8 @@ typedef struct pwfa_axi pwfa_axi_t;
  * cudaStream_t (NULL = legacy default stream). */
 int pwfa_axi_create(const pwfa_axi_params* params, void* cuda_stream, pwfa_axi_t** out);
 
-/* Advance nsteps (>= 0): Faraday, node moments, fused fluid step, Ampere
- * with the driver at t_{n+1}. Asynchronous on the stream. */
+/* Advance nsteps (>= 0): the fused Faraday + fluid step, then Ampere with
+ * the driver at t_{n+1}. Asynchronous on the stream. */
 int pwfa_axi_step(pwfa_axi_t* h, int32_t nsteps);
 
 /* out[6][nz][nr] (host or device FP32): n, beta_z, beta_r of the current
@@ -366,8 +366,10 @@ int pwfa_axi_set_source(pwfa_axi_t* h, const float* fs);
 int64_t pwfa_axi_steps_done(pwfa_axi_t* h);
 
 /* Accumulated device time (ms) of the step's kernels since the last call:
- * ms[0] Faraday, ms[1] moments, ms[2] fluid, ms[3] Ampere, from CUDA event
- * pairs recorded while enabled (pwfa_axi_profile). Synchronises. */
+ * ms[2] the fused Faraday + fluid kernel, ms[3] Ampere (ms[0], ms[1] stay
+ * zero: Faraday's law and the node moments run inside the fluid kernel),
+ * from CUDA event pairs recorded while enabled (pwfa_axi_profile).
+ * Synchronises. */
 int pwfa_axi_profile(pwfa_axi_t* h, int32_t enable);
 int pwfa_axi_kernel_times(pwfa_axi_t* h, double* ms, int64_t* launches);
 

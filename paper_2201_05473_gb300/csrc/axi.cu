@@ -1,6 +1,7 @@
-// Kernels of the 2D-axisymmetric (z, r) form: Faraday, node moments, the
-// fused fluid step with the cylindrical terms of Eq. 13, Ampere with the
-// driver. One thread per node, warps along r (coalesced rows).
+// Kernels of the 2D-axisymmetric (z, r) form: the fused step (Faraday's law,
+// pull, node moments, the cylindrical terms of Eq. 13, collision), Ampere
+// with the driver, and the node moments for exports. One thread per node,
+// warps along r (coalesced rows).
 #include "axi.h"
 
 namespace pwfa {
@@ -37,17 +38,14 @@ __device__ __forceinline__ float yee(const float* a, const Args& g, int k, int j
     return a[(int64_t)k * g.nr + j];
 }
 
-// Faraday: dB_theta/dt = dE_z/dr - dE_r/dz on the active faces
-__global__ void __launch_bounds__(kBR * kBZ) faraday_kernel(const Args a) {
-    const int j = blockIdx.x * kBR + threadIdx.x;
-    const int k = blockIdx.y * kBZ + threadIdx.y;
-    if (j >= a.nr || k >= a.nz) return;
+// Faraday on one face: B_theta(t_{n+1}) = B_theta(t_n) + dt (dE_z/dr - dE_r/dz)
+// on the active faces, zero elsewhere (axis, outer wall, outside the grid)
+__device__ __forceinline__ float faraday_bt(const Args& a, int k, int j) {
+    if (k < 0 || k > a.nz - 2 || j < 1 || j > a.nr - 2) return 0.0f;
     const int64_t o = (int64_t)k * a.nr + j;
-    float b = 0.0f;
-    if (k <= a.nz - 2 && j >= 1 && j <= a.nr - 2)
-        b = a.Bt[o] - a.cdt * ((a.Er[o + a.nr] - a.Er[o]) - (a.Ez[o + 1] - a.Ez[o]));
-    a.Btn[o] = b;
+    return a.Bt[o] - a.cdt * ((a.Er[o + a.nr] - a.Er[o]) - (a.Ez[o + 1] - a.Ez[o]));
 }
+
 
 // Pre-collision moments of every node: interior nodes sum their pulled
 // populations; the z walls and the outer row take their clamped interior
@@ -75,49 +73,73 @@ __global__ void __launch_bounds__(kBR * kBZ) moments_kernel(const Args a) {
     for (int l = 0; l < kL; ++l) a.Am[(int64_t)l * a.N + o] = A[l];
 }
 
-// One fused step of every node of rows 1..nr-1: pull (interior) or the
-// equilibrium of the clamped node (z walls, outer row), Lorentz source with
-// the node fields, the cylindrical terms D (1/r) dA/dr - A u_r / r of Eq. 13
-// on interior nodes (dA/dr the central difference of the node moments), BGK
-// collision (Eq. 7) with S_i = w_i S dt, store; row 1 also writes the axis
-// row as its mirror image. Node current J = -n* beta(p*) of the
-// post-collision moments.
+// One fused step of every node of rows 1..nr-1. A warp takes 30 consecutive
+// nodes of one z row plus a halo node on each side (lanes 0 and 31); every
+// lane gathers the pulled populations of its clamped node (its own node when
+// interior; the clamped interior node for the z walls, the outer row and the
+// mirror row, which negates n p_r), so the radial neighbours' moments of
+// dA/dr come from the neighbouring lanes (warp shuffles) without a separate
+// moments pass. Faraday's law runs here too: each node evaluates B_theta at
+// t_{n+1} on the four faces around it and stores the one it owns (rows
+// 1..nr-1; the axis row's B_theta stays zero). Then: the equilibrium of the
+// clamped node on boundary nodes (Eq. 14), Lorentz source with the node
+// fields, the cylindrical terms
+// D (1/r) dA/dr - A u_r / r of Eq. 13 on interior nodes, BGK collision
+// (Eq. 7) with S_i = w_i S dt, store; row 1 also writes the axis row as its
+// mirror image. Node current J = -n* beta(p*) of the post-collision moments.
+constexpr int kOut = 30;  // output nodes per warp
+
 __global__ void __launch_bounds__(kBR * kBZ) fluid_kernel(const Args a) {
-    const int j = blockIdx.x * kBR + threadIdx.x;
-    const int k = blockIdx.y * kBZ + threadIdx.y;
-    if (j < 1 || j >= a.nr || k >= a.nz) return;
-    const int64_t o = (int64_t)k * a.nr + j;
+    const int lane = (int)threadIdx.x;
+    const int j = (int)blockIdx.x * kOut + lane - 1;
+    const int k = (int)(blockIdx.y * kBZ + threadIdx.y);
+    const bool row_ok = k < a.nz;
+    const bool valid = row_ok && j >= 0 && j < a.nr;
+    const bool out = valid && lane >= 1 && lane <= kOut && j >= 1;
+    const int kc = clampi(k, 1, a.nz - 2);
+    const int jc = clampi(j, 1, a.nr - 2);
     const bool bnd = k == 0 || k == a.nz - 1 || j == a.nr - 1;
     float f[kL][kQ];
-    float A[kL];
-    if (!bnd) {
+    float A[kL] = {0.0f, 0.0f, 0.0f};
+    if (valid) {
+        const int64_t c = (int64_t)kc * a.nr + jc;
 #pragma unroll
         for (int l = 0; l < kL; ++l) {
             const float* fl = a.fin + (int64_t)l * kQ * a.Np;
             float s = 0.0f;
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
-                f[l][q] = __ldg(fl + (int64_t)q * a.Np + o - (int64_t)xz(q) * a.nr - xr(q));
+                f[l][q] = __ldg(fl + (int64_t)q * a.Np + c - (int64_t)xz(q) * a.nr - xr(q));
                 s += f[l][q];
             }
             A[l] = s;
         }
-    } else {
-        const int64_t src = (int64_t)clampi(k, 1, a.nz - 2) * a.nr + clampi(j, 1, a.nr - 2);
-#pragma unroll
-        for (int l = 0; l < kL; ++l) A[l] = a.Am[(int64_t)l * a.N + src];
+        if (j == 0) A[2] = -A[2];
     }
+    // radial neighbours' moments (pre-collision, every node's own rule)
+    float Am1[kL], Ap1[kL];
+#pragma unroll
+    for (int l = 0; l < kL; ++l) {
+        Am1[l] = __shfl_up_sync(0xffffffffu, A[l], 1);
+        Ap1[l] = __shfl_down_sync(0xffffffffu, A[l], 1);
+    }
+    if (!out) return;
+    const int64_t o = (int64_t)k * a.nr + j;
     const float nn = A[0] > a.n_floor ? A[0] : a.n_floor;
     const float pz = A[1] / nn, pr = A[2] / nn;
     const float gam = sqrtf(1.0f + pz * pz + pr * pr);
     const float bz = pz / gam, br = pr / gam;
     const float uz = bz * a.lat, ur = br * a.lat;
+    // equilibrium factors shared by the three lattices: f^eq_l,i = A_l phi_i
+    float phi[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) phi[q] = feq(q, 1.0f, uz, ur);
     if (bnd) {
         // Eq. 14: the equilibrium of the clamped node
 #pragma unroll
         for (int l = 0; l < kL; ++l)
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) f[l][q] = feq(q, A[l], uz, ur);
+            for (int q = 0; q < kQ; ++q) f[l][q] = A[l] * phi[q];
 #pragma unroll
         for (int l = 0; l < kL; ++l) {
             float s = 0.0f;
@@ -138,19 +160,18 @@ __global__ void __launch_bounds__(kBR * kBZ) fluid_kernel(const Args a) {
 #pragma unroll
             for (int dk = -1; dk <= 0; ++dk)
 #pragma unroll
-                for (int dj = -1; dj <= 0; ++dj) bs += yee(a.Bt, a, k + dk, j + dj) + yee(a.Btn, a, k + dk, j + dj);
+                for (int dj = -1; dj <= 0; ++dj) bs += yee(a.Bt, a, k + dk, j + dj) + faraday_bt(a, k + dk, j + dj);
             const float bt = bs / 8.0f;
             // F_z = -n (E_z + beta_r B_theta), F_r = -n (E_r - beta_z B_theta)
             S[1] = -A[0] * (ez + br * bt);
             S[2] = -A[0] * (er - bz * bt);
         }
         if (!bnd) {
-            const float r = ((float)j - 0.5f) * a.dx;
+            // D (1/r) dA/dr - A u_r / r, dA/dr = (A(r + dx) - A(r - dx)) / 2 dx
+            const float inv_r = 1.0f / (((float)j - 0.5f) * a.dx);
+            const float c = 0.5f * a.D / a.dx;
 #pragma unroll
-            for (int l = 0; l < kL; ++l) {
-                const float dAdr = (a.Am[(int64_t)l * a.N + o + 1] - a.Am[(int64_t)l * a.N + o - 1]) / (2.0f * a.dx);
-                S[l] += a.D * dAdr / r - A[l] * br / r;
-            }
+            for (int l = 0; l < kL; ++l) S[l] += (c * (Ap1[l] - Am1[l]) - A[l] * br) * inv_r;
         }
         nst = A[0] + S[0] * a.dt;
         pzs = A[1] + S[1] * a.dt;
@@ -165,7 +186,7 @@ __global__ void __launch_bounds__(kBR * kBZ) fluid_kernel(const Args a) {
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             float fs = f[l][q];
-            if (a.collision != 2) fs = fs - a.omega * (fs - feq(q, A[l], uz, ur)) + w9(q) * S[l] * a.dt;
+            if (a.collision != 2) fs = fs - a.omega * (fs - A[l] * phi[q]) + w9(q) * S[l] * a.dt;
             fo[(int64_t)q * a.Np + o] = fs;
             if (j == 1) fo[(int64_t)rrefl(q) * a.Np + om] = sg * fs;
         }
@@ -174,6 +195,7 @@ __global__ void __launch_bounds__(kBR * kBZ) fluid_kernel(const Args a) {
     const float qz = pzs / nsn, qr = prs / nsn;
     const float gs = sqrtf(1.0f + qz * qz + qr * qr);
     const float jz = -nst * qz / gs, jr = -nst * qr / gs;
+    if (a.couple) a.Btn[o] = faraday_bt(a, k, j);
     a.Jz[o] = jz;
     a.Jr[o] = jr;
     if (j == 1) {
@@ -229,16 +251,13 @@ dim3 grid_of(const Args& a) { return dim3((a.nr + kBR - 1) / kBR, (a.nz + kBZ - 
 
 }  // namespace
 
-cudaError_t launch_faraday(const Args& a, cudaStream_t s) {
-    faraday_kernel<<<grid_of(a), dim3(kBR, kBZ), 0, s>>>(a);
-    return cudaGetLastError();
-}
 cudaError_t launch_moments(const Args& a, cudaStream_t s) {
     moments_kernel<<<grid_of(a), dim3(kBR, kBZ), 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_fluid(const Args& a, cudaStream_t s) {
-    fluid_kernel<<<grid_of(a), dim3(kBR, kBZ), 0, s>>>(a);
+    const dim3 grid((unsigned)((a.nr + kOut - 1) / kOut), (unsigned)((a.nz + kBZ - 1) / kBZ), 1);
+    fluid_kernel<<<grid, dim3(kBR, kBZ), 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_ampere(const Args& a, cudaStream_t s) {

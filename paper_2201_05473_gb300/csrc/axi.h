@@ -25,7 +25,7 @@ struct Args {
     int64_t N, Np;
     const float* fin;    // streaming source of this step
     float* fout;         // post-collision populations written by this step
-    float* Am;           // [3][N] pre-collision moments of every node
+    float* Am;           // [3][N] node moments (exports)
     const float* Ez;     // E_z, E_r at t_{n+1/2} (updated in place by Ampere)
     const float* Er;
     const float* Bt;     // B_theta at t_n
@@ -43,7 +43,8 @@ struct Args {
     float alpha, inv2sr2, inv2sz2, zc;  // driver at t_{n+1}
 };
 
-cudaError_t launch_faraday(const Args& a, cudaStream_t s);
+// a.Am := pre-collision node moments (for exports; the step's fluid kernel
+// takes its neighbours' moments from adjacent lanes)
 cudaError_t launch_moments(const Args& a, cudaStream_t s);
 cudaError_t launch_fluid(const Args& a, cudaStream_t s);
 cudaError_t launch_ampere(const Args& a, cudaStream_t s);

@@ -1,7 +1,7 @@
 // Host runtime of the 2D-axisymmetric form (pwfa_axi_* in
 // include/pwfa_lbm.h): validation, one device arena, the per-step launch
-// sequence (Faraday -> moments -> fused fluid -> Ampere), state exchange and
-// per-kernel timing.
+// sequence (fused Faraday + fluid -> Ampere), state exchange and per-kernel
+// timing.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -212,9 +212,8 @@ int pwfa_axi_step(pwfa_axi_t* h, int32_t nsteps) {
     for (int32_t n = 0; n < nsteps; ++n) {
         pwfa::axi::Args a = make_args(h);
         int rc = PWFA_OK;
-        if (h->p.couple) rc = timed(h, 0, "axi faraday", [&] { return pwfa::axi::launch_faraday(a, h->stream); });
-        if (rc == PWFA_OK) rc = timed(h, 1, "axi moments", [&] { return pwfa::axi::launch_moments(a, h->stream); });
-        if (rc == PWFA_OK) rc = timed(h, 2, "axi fluid", [&] { return pwfa::axi::launch_fluid(a, h->stream); });
+        // (Faraday's law runs inside the fluid kernel)
+        rc = timed(h, 2, "axi fluid", [&] { return pwfa::axi::launch_fluid(a, h->stream); });
         if (rc == PWFA_OK && h->p.couple)
             rc = timed(h, 3, "axi ampere", [&] { return pwfa::axi::launch_ampere(a, h->stream); });
         if (rc) return rc;
