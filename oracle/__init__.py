@@ -58,6 +58,7 @@ class _Params(ctypes.Structure):
         ("z0", ctypes.c_double),
         ("n_floor", ctypes.c_double),
         ("moving_window", ctypes.c_int32), ("window_z", ctypes.c_double),
+        ("driver", ctypes.c_int32),
     ]
 
 
@@ -87,6 +88,9 @@ def _load():
             lib.oracle_window_planes.restype = ctypes.c_int64
             lib.oracle_window_planes.argtypes = [ctypes.c_void_p]
             lib.oracle_set_source.argtypes = [ctypes.c_void_p, dp]
+            lib.oracle_set_particles.argtypes = [ctypes.c_void_p, ctypes.c_int64, dp, ctypes.c_double]
+            lib.oracle_get_particles.argtypes = [ctypes.c_void_p, dp]
+            lib.oracle_driver_current.argtypes = [ctypes.c_void_p, dp]
             lib.oracle_steps_done.restype = ctypes.c_int64
             lib.oracle_steps_done.argtypes = [ctypes.c_void_p]
             for name in ("oracle_get_f", "oracle_set_f", "oracle_set_equilibrium",
@@ -126,7 +130,7 @@ class Oracle:
 
     def __init__(self, nx, ny, nz, dx, dt, tau, collision=COLL_BGK, boundary=BND_OPEN,
                  couple=1, n0=1.0, profile=None, profile_rmax=0.0, alpha=0.0,
-                 sigma_r=0.5, sigma_z=0.5, z0=0.0, n_floor=1e-6, moving_window=0, window_z=0.0):
+                 sigma_r=0.5, sigma_z=0.5, z0=0.0, n_floor=1e-6, moving_window=0, window_z=0.0, driver=0):
         self._lib = _load()
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
@@ -135,8 +139,9 @@ class Oracle:
         p = _Params(nx, ny, nz, dx, dt, tau, collision, boundary, couple, n0,
                     _ptr(prof) if prof is not None else None,
                     0 if prof is None else len(prof), profile_rmax,
-                    alpha, sigma_r, sigma_z, z0, n_floor, int(moving_window), window_z)
+                    alpha, sigma_r, sigma_z, z0, n_floor, int(moving_window), window_z, int(driver))
         self._h = self._lib.oracle_create(ctypes.byref(p))
+        self._np = 0
         if not self._h:
             raise ValueError("oracle_create rejected the parameters")
         self.params = dict(nx=nx, ny=ny, nz=nz, dx=dx, dt=dt, tau=tau, collision=collision,
@@ -164,6 +169,22 @@ class Oracle:
     def window_planes(self) -> int:
         """Planes the moving window has advanced (0 without a window)."""
         return int(self._lib.oracle_window_planes(self._h))
+
+    def set_particles(self, xp: np.ndarray, weight: float):
+        """PIC driver: xp[6][n] = x, y, z at t_{n+1/2}, p_x, p_y, p_z at t_n."""
+        xp = np.ascontiguousarray(xp, dtype=np.float64)
+        self._np = xp.shape[1]
+        self._lib.oracle_set_particles(self._h, self._np, _ptr(xp), float(weight))
+
+    def get_particles(self) -> np.ndarray:
+        out = np.empty((6, self._np))
+        self._lib.oracle_get_particles(self._h, _ptr(out))
+        return out
+
+    def driver_current(self) -> np.ndarray:
+        out = np.empty((3,) + self.shape)
+        self._lib.oracle_driver_current(self._h, _ptr(out))
+        return out
 
     def set_source(self, fs: np.ndarray):
         """Set the streaming source (post-collision populations) and pull the
@@ -310,7 +331,7 @@ def tangent_run(nsteps, dirs, nx, ny, nz, dx, dt, tau, collision=COLL_BGK, bound
     prof = None if profile is None else np.ascontiguousarray(profile, dtype=np.float64)
     p = _Params(nx, ny, nz, dx, dt, tau, collision, boundary, couple, n0,
                 _ptr(prof) if prof is not None else None, 0 if prof is None else len(prof),
-                profile_rmax, alpha, sigma_r, sigma_z, z0, n_floor, 0, 0.0)
+                profile_rmax, alpha, sigma_r, sigma_z, z0, n_floor, 0, 0.0, 0)
     nd = dirs.shape[0]
     assert dirs.shape[1] == 3 + (0 if prof is None else len(prof))
     E = np.empty((3, nz, ny, nx))

@@ -57,6 +57,19 @@
  * pre-collision populations are pulled again from the moved source. The
  * step then runs as usual, the driver evaluated at lab position z + W dx.
  *
+ * PIC driver (Eq. 1, instead of the rigid bunch): macro-electrons of weight
+ * w (electrons in units of n0 (c/omega_p)^3) with positions at t_{n+1/2} (the
+ * time level of E) and momenta at t_n (that of B). In step n, after the
+ * fluid, each is pushed by the Boris scheme (charge/mass -1) with E(t_{n+1/2})
+ * and the mean of B(t_n), B(t_{n+1}), both interpolated trilinearly from each
+ * component's own Yee lattice at x_{n+1/2}, to p_{n+1}; it moves to
+ * x_{n+3/2} = x_{n+1/2} + dt p_{n+1}/gamma_{n+1}, and the current of that
+ * move is deposited on the E edges by the charge-conserving scheme of
+ * Esirkepov (Comput. Phys. Commun. 135, 2001) for the linear (cloud-in-cell)
+ * shape, so that the driver's charge obeys the discrete continuity equation
+ * exactly; Ampere subtracts it as J_b. Particles outside an open grid see no
+ * field and deposit only on in-grid edges.
+ *
  * The scalar type is a template parameter so that the same step can run on
  * forward-mode dual numbers for derivatives.
  */
@@ -144,6 +157,7 @@ typedef struct {
     double n_floor;
     int32_t moving_window; /* 1: the box follows the driver (open mode only) */
     double window_z;       /* box position held by the driver centre once reached */
+    int32_t driver;        /* 0 rigid bi-Gaussian bunch, 1 macro-particles (PIC, Eq. 1) */
 } oracle_params;
 }
 
@@ -165,6 +179,11 @@ struct Sim {
     std::vector<S> EN[3], BN[3];       // node fields used by the last step
     bool fs_valid = true;              // fs is the streaming source of f
     bool shift_failed = false;         // a window move found no valid source
+    // PIC driver: x, y, z (t_{n+1/2}), p_x, p_y, p_z (t_n); weight; the
+    // driver current of the last step on the E edges
+    std::vector<S> P[6];
+    double pw = 0.0;
+    std::vector<S> Jb[3];
 
     int64_t idx(int i, int j, int k) const { return ((int64_t)k * ny + j) * nx + i; }
     bool periodic() const { return p.boundary == BND_PERIODIC; }
@@ -420,8 +439,127 @@ struct Sim {
                 }
     }
 
+    // ---- PIC driver
+    // Component a at grid coordinates (gx, gy, gz) of its own Yee lattice:
+    // trilinear in the eight surrounding values.
+    S interp(const std::vector<S>& a, const S& gx, const S& gy, const S& gz) const {
+        const int i0 = (int)std::floor(val(gx)), j0 = (int)std::floor(val(gy)), k0 = (int)std::floor(val(gz));
+        const S fx = gx - S((double)i0), fy = gy - S((double)j0), fz = gz - S((double)k0);
+        S r(0.0);
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+                for (int a2 = 0; a2 < 2; ++a2) {
+                    const S wx = a2 ? fx : S(1.0) - fx, wy = b ? fy : S(1.0) - fy, wz = c ? fz : S(1.0) - fz;
+                    r += wx * wy * wz * at(a, i0 + a2, j0 + b, k0 + c);
+                }
+        return r;
+    }
+    // linear (cloud-in-cell) shape
+    static S hat(const S& t) {
+        const S at_ = val(t) < 0.0 ? -t : t;
+        return val(at_) < 1.0 ? S(1.0) - at_ : S(0.0);
+    }
+    void add_edge(std::vector<S>& a, int i, int j, int k, const S& v) {
+        if (periodic()) { i = wrap(i, nx); j = wrap(j, ny); k = wrap(k, nz); }
+        else if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) return;
+        a[idx(i, j, k)] += v;
+    }
+    // Esirkepov's charge-conserving current of one move (grid coordinates in
+    // cells, node-centred; |move| < 1 cell per axis), on a 3-node stencil per
+    // axis: W_x = dSx (S0y S0z + dSy S0z / 2 + S0y dSz / 2 + dSy dSz / 3) and
+    // cyclic, J_x(i + 1/2) = w / (dx^2 dt) sum_{i' <= i} W_x(i').
+    void deposit(const S g0[3], const S g1[3]) {
+        int base[3];
+        S s0[3][3], ds[3][3];
+        for (int d = 0; d < 3; ++d) {
+            base[d] = (int)std::floor(std::min(val(g0[d]), val(g1[d])));
+            for (int m = 0; m < 3; ++m) {
+                const S node((double)(base[d] + m));
+                s0[d][m] = hat(g0[d] - node);
+                ds[d][m] = hat(g1[d] - node) - s0[d][m];
+            }
+        }
+        const S coef(pw / (p.dx * p.dx * p.dt));
+        const S half(0.5), third(1.0 / 3.0);
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) {
+                S run(0.0);
+                for (int a2 = 0; a2 < 2; ++a2) {
+                    run += ds[0][a2] * (s0[1][b] * s0[2][c] + half * ds[1][b] * s0[2][c] + half * s0[1][b] * ds[2][c] +
+                                        third * ds[1][b] * ds[2][c]);
+                    add_edge(Jb[0], base[0] + a2, base[1] + b, base[2] + c, coef * run);
+                }
+            }
+        for (int a2 = 0; a2 < 3; ++a2)
+            for (int c = 0; c < 3; ++c) {
+                S run(0.0);
+                for (int b = 0; b < 2; ++b) {
+                    run += ds[1][b] * (s0[0][a2] * s0[2][c] + half * ds[0][a2] * s0[2][c] + half * s0[0][a2] * ds[2][c] +
+                                       third * ds[0][a2] * ds[2][c]);
+                    add_edge(Jb[1], base[0] + a2, base[1] + b, base[2] + c, coef * run);
+                }
+            }
+        for (int a2 = 0; a2 < 3; ++a2)
+            for (int b = 0; b < 3; ++b) {
+                S run(0.0);
+                for (int c = 0; c < 2; ++c) {
+                    run += ds[2][c] * (s0[0][a2] * s0[1][b] + half * ds[0][a2] * s0[1][b] + half * s0[0][a2] * ds[1][b] +
+                                       third * ds[0][a2] * ds[1][b]);
+                    add_edge(Jb[2], base[0] + a2, base[1] + b, base[2] + c, coef * run);
+                }
+            }
+    }
+    // Boris push of every macro-electron and the deposit of its move
+    void push_deposit() {
+        for (int c = 0; c < 3; ++c) Jb[c].assign(N, S(0.0));
+        const S dt(p.dt), hdt(0.5 * p.dt), inv_dx(1.0 / p.dx);
+        const double L[3] = {nx * p.dx, ny * p.dx, nz * p.dx};
+        const size_t np = P[0].size();
+        for (size_t m = 0; m < np; ++m) {
+            const S g[3] = {P[0][m] * inv_dx, P[1][m] * inv_dx, P[2][m] * inv_dx};
+            const S h(0.5);
+            const S e[3] = {interp(E[0], g[0] - h, g[1], g[2]), interp(E[1], g[0], g[1] - h, g[2]),
+                            interp(E[2], g[0], g[1], g[2] - h)};
+            const S b[3] = {h * (interp(B[0], g[0], g[1] - h, g[2] - h) + interp(Bn[0], g[0], g[1] - h, g[2] - h)),
+                            h * (interp(B[1], g[0] - h, g[1], g[2] - h) + interp(Bn[1], g[0] - h, g[1], g[2] - h)),
+                            h * (interp(B[2], g[0] - h, g[1] - h, g[2]) + interp(Bn[2], g[0] - h, g[1] - h, g[2]))};
+            // Boris, q/m = -1: half kick, rotation, half kick
+            S um[3], up[3], pn[3];
+            for (int c = 0; c < 3; ++c) um[c] = P[3 + c][m] - hdt * e[c];
+            const S gm = sqrt(S(1.0) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+            S tv[3];
+            for (int c = 0; c < 3; ++c) tv[c] = -hdt * b[c] / gm;
+            const S t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+            S sv[3];
+            for (int c = 0; c < 3; ++c) sv[c] = S(2.0) * tv[c] / (S(1.0) + t2);
+            const S w1[3] = {um[0] + (um[1] * tv[2] - um[2] * tv[1]), um[1] + (um[2] * tv[0] - um[0] * tv[2]),
+                             um[2] + (um[0] * tv[1] - um[1] * tv[0])};
+            up[0] = um[0] + (w1[1] * sv[2] - w1[2] * sv[1]);
+            up[1] = um[1] + (w1[2] * sv[0] - w1[0] * sv[2]);
+            up[2] = um[2] + (w1[0] * sv[1] - w1[1] * sv[0]);
+            for (int c = 0; c < 3; ++c) pn[c] = up[c] - hdt * e[c];
+            const S gn = sqrt(S(1.0) + pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2]);
+            S xn[3], g1[3];
+            for (int c = 0; c < 3; ++c) {
+                xn[c] = P[c][m] + dt * pn[c] / gn;
+                g1[c] = xn[c] * inv_dx;
+            }
+            deposit(g, g1);
+            for (int c = 0; c < 3; ++c) {
+                if (periodic()) {
+                    const double v = val(xn[c]);
+                    if (v < 0.0) xn[c] += S(L[c]);
+                    else if (v >= L[c]) xn[c] -= S(L[c]);
+                }
+                P[c][m] = xn[c];
+                P[3 + c][m] = pn[c];
+            }
+        }
+    }
+
     // 5. Ampere: E += dt (curl B(t_{n+1}) - J_e - J_b), J_e averaged from the
-    //    two nodes of each edge, J_b,z = -n_b at t_{n+1}.
+    //    two nodes of each edge, J_b,z = -n_b at t_{n+1} (rigid bunch) or the
+    //    deposited current of the PIC driver.
     void ampere() {
         const S c(p.dt / p.dx);
         const S dt(p.dt);
@@ -432,21 +570,24 @@ struct Sim {
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
                     int64_t o = idx(i, j, k);
+                    const bool pic = p.driver == 1;
                     if (act_ex(i, j, k)) {
                         S curl = (at(Bn[2], i, j, k) - at(Bn[2], i, j - 1, k)) - (at(Bn[1], i, j, k) - at(Bn[1], i, j, k - 1));
                         S Je = S(0.5) * (at(Jn[0], i, j, k) + at(Jn[0], i + 1, j, k));
+                        if (pic) Je += Jb[0][o];
                         E[0][o] = E[0][o] + c * curl - dt * Je;
                     }
                     if (act_ey(i, j, k)) {
                         S curl = (at(Bn[0], i, j, k) - at(Bn[0], i, j, k - 1)) - (at(Bn[2], i, j, k) - at(Bn[2], i - 1, j, k));
                         S Je = S(0.5) * (at(Jn[1], i, j, k) + at(Jn[1], i, j + 1, k));
+                        if (pic) Je += Jb[1][o];
                         E[1][o] = E[1][o] + c * curl - dt * Je;
                     }
                     if (act_ez(i, j, k)) {
                         S curl = (at(Bn[1], i, j, k) - at(Bn[1], i - 1, j, k)) - (at(Bn[0], i, j, k) - at(Bn[0], i, j - 1, k));
                         S Je = S(0.5) * (at(Jn[2], i, j, k) + at(Jn[2], i, j, k + 1));
-                        S Jb = -driver(i * p.dx, j * p.dx, (k + 0.5 + (double)zshift) * p.dx, t1);
-                        E[2][o] = E[2][o] + c * curl - dt * (Je + Jb);
+                        S Jd = pic ? Jb[2][o] : -driver(i * p.dx, j * p.dx, (k + 0.5 + (double)zshift) * p.dx, t1);
+                        E[2][o] = E[2][o] + c * curl - dt * (Je + Jd);
                     }
                 }
     }
@@ -492,6 +633,7 @@ struct Sim {
         else for (int c = 0; c < 3; ++c) Bn[c] = B[c];
         collide();
         stream();
+        if (p.driver == 1) push_deposit();
         if (p.couple) ampere();
         for (int c = 0; c < 3; ++c) B[c].swap(Bn[c]);
         f.swap(fn);
@@ -514,6 +656,7 @@ extern "C" {
 
 void* oracle_create(const oracle_params* prm) {
     if (!prm || prm->nx < 3 || prm->ny < 3 || prm->nz < 3) return nullptr;
+    if (prm->driver == 1 && prm->moving_window) return nullptr;
     Sim<double>* s = new (std::nothrow) Sim<double>();
     if (!s) return nullptr;
     s->p = *prm;
@@ -533,6 +676,28 @@ int oracle_step(void* h, int32_t nsteps) {
         if (s->shift_failed) return -1;
     }
     return 0;
+}
+
+/* PIC driver macro-electrons: xp[6][n] = x, y, z at t_{n+1/2} and p_x, p_y,
+ * p_z at t_n; weight in electrons per n0 (c/omega_p)^3. */
+void oracle_set_particles(void* h, int64_t n, const double* xp, double weight) {
+    Sim<double>* s = static_cast<Sim<double>*>(h);
+    for (int c = 0; c < 6; ++c) s->P[c].assign(xp + c * n, xp + (c + 1) * n);
+    s->pw = weight;
+}
+
+void oracle_get_particles(void* h, double* out) {
+    Sim<double>* s = static_cast<Sim<double>*>(h);
+    const size_t n = s->P[0].size();
+    for (int c = 0; c < 6; ++c)
+        for (size_t m = 0; m < n; ++m) out[c * n + m] = s->P[c][m];
+}
+
+/* Driver current of the last step on the E edges, [3][z][y][x] (PIC only). */
+void oracle_driver_current(void* h, double* out) {
+    Sim<double>* s = static_cast<Sim<double>*>(h);
+    for (int c = 0; c < 3; ++c)
+        for (int64_t o = 0; o < s->N; ++o) out[c * s->N + o] = s->Jb[c].empty() ? 0.0 : s->Jb[c][o];
 }
 
 /* Planes the moving window has advanced so far (0 without a window). */
@@ -653,7 +818,7 @@ void oracle_diag(void* h, double* out) {
  * scalar type. */
 int oracle_tangent_run(const oracle_params* prm, int32_t nsteps, int32_t ndir, const double* dirs,
                        double* E, double* dE) {
-    if (!prm || ndir < 1 || ndir > 4 || nsteps < 0) return -1;
+    if (!prm || ndir < 1 || ndir > 4 || nsteps < 0 || prm->driver != 0) return -1;
     using D = Dual<4>;
     Sim<D>* s = new (std::nothrow) Sim<D>();
     if (!s) return -1;

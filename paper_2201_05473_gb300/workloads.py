@@ -206,3 +206,23 @@ def axisymmetric_paper(qtilde: float = 0.1) -> AxiWorkload:
     return AxiWorkload(nz=2400, nr=402, dx=dx, tau=0.51, alpha=0.68 * qtilde / 0.1,
                        sigma_r=8.9 / KP_INV_UM, sigma_z=17.7 / KP_INV_UM, z0=-4.0 * 17.7 / KP_INV_UM,
                        steps=2000, name=f"lbm-pwfa axisymmetric 2400x400 dz0.25um Q{qtilde:g}")
+
+
+def bunch_particles(n: int, alpha: float, sigma_r: float, sigma_z: float, z0: float, dt: float,
+                    nx: int, ny: int, dx: float, gamma: float = 5000.0, seed: int = 2):
+    """Macro-electrons of a bi-Gaussian driver for the PIC form: n positions
+    drawn from N(centre, sigma) per axis (PCG64, seed), momenta p_z =
+    sqrt(gamma^2 - 1) along z, positions advanced by half a step at that
+    velocity (positions live at t_{n+1/2}, momenta at t_n). Returns
+    (xp[6][n], weight) with the weight (electrons per n0 (c/omega_p)^3) that
+    gives the rigid bunch's charge alpha (2 pi)^{3/2} sigma_r^2 sigma_z."""
+    rng = np.random.default_rng(seed)
+    xc, yc = 0.5 * (nx - 1) * dx, 0.5 * (ny - 1) * dx
+    xp = np.zeros((6, n))
+    xp[0] = xc + sigma_r * rng.standard_normal(n)
+    xp[1] = yc + sigma_r * rng.standard_normal(n)
+    pz = np.sqrt(gamma * gamma - 1.0)
+    xp[2] = z0 + sigma_z * rng.standard_normal(n) + 0.5 * dt * pz / gamma
+    xp[5] = pz
+    weight = alpha * (2.0 * np.pi) ** 1.5 * sigma_r * sigma_r * sigma_z / n
+    return xp, weight
