@@ -342,6 +342,36 @@ def run_ours(args):
                            "note": "box follows the driver; each move: E and B moved by a kernel "
                                    "(24 B/node), populations read one plane up inside the fluid kernel",
                            "finite": bool(dw[7] == 0)}
+        # ---- PIC driver (Eq. 1): the production step with the bunch as
+        # 2e5 macro-electrons (the paper's particle count, gamma = 5000)
+        pic_line = None
+        if not args.no_extra and args.only in ("", "pic"):
+            torch.cuda.empty_cache()
+            wp = w.replace(driver=1)
+            npart = 200000
+            xp, pwt = W.bunch_particles(npart, wp.alpha, wp.sigma_r, wp.sigma_z, wp.z0, wp.dt, wp.nx, wp.ny, wp.dx)
+            sp = lbm.Simulation(wp, stream=stream)
+            sp.set_particles(xp, pwt)
+            sp.set_launch(*launch_shape)
+            sp.step(args.warmup)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sp.step(args.steps)
+            e1.record(stream)
+            stream.synchronize()
+            msp = e0.elapsed_time(e1)
+            sp.kernel_times()
+            sp.profile(True)
+            sp.step(args.steps)
+            kp, lp = sp.kernel_times()
+            sp.profile(False)
+            dp_ = sp.diag(check=False)
+            sp.close()
+            pic_line = {"value": N * args.steps / (msp * 1e-3) / 1e9, "unit": "GLUPS", "particles": npart,
+                        "vs_rigid_driver": ms / msp, "particle_kernel_ms": kp["aux"] / max(lp["aux"], 1),
+                        "note": "Boris push + Esirkepov deposit (FP32 atomics) after the fluid kernel",
+                        "finite": bool(dp_[7] == 0)}
         # ---- the paper's own geometry: 2D-axisymmetric (z, r), 2400 x 400
         # cells at 0.25 um, Q = 0.1 (context: the paper's LBM routine ran
         # 2.0 M cell-steps/s on a Xeon E5-2695, Table I)
@@ -473,6 +503,7 @@ def run_ours(args):
         "batched": batch_line,
         "moving_window": window_line,
         "axisymmetric": axi_line,
+        "pic_driver": pic_line,
         "clocks": clk.summary(),
         "diag_after": {"sum_n": diag[0], "min_n": diag[5], "max_beta": diag[6], "nonfinite": diag[7]},
     }
@@ -532,7 +563,7 @@ def main():
     ap.add_argument("--grid", default="", help="override the grid as ZxYxX (profiling captures)")
     ap.add_argument("--no-extra", action="store_true", help="skip the BF16/FP16 and adjoint lines")
     ap.add_argument("--adjoint-steps", type=int, default=500)
-    ap.add_argument("--only", default="", choices=["", "storage", "adjoint", "batched", "window", "axisymmetric"],
+    ap.add_argument("--only", default="", choices=["", "storage", "adjoint", "batched", "window", "axisymmetric", "pic"],
                     help="with a small --steps: run the main pass and one extra section (profiling captures)")
     ap.add_argument("--report", default="", choices=["", "precision"],
                     help="precision: error table of BF16/FP16/FP32 storage against the oracle")

@@ -110,7 +110,15 @@ typedef struct {
                               the driver at its lab position. 0: fixed box. */
     double window_z;       /* box coordinate at which the driver centre is held
                               once the window moves (c/omega_p) */
+    int32_t driver;        /* PWFA_DRIVER_RIGID: the rigid bi-Gaussian bunch
+                              (alpha, sigma_r, sigma_z, z0); PWFA_DRIVER_PIC:
+                              macro-electrons set by pwfa_lbm_set_particles
+                              (Eq. 1; single-instance stepping, no moving
+                              window, no adjoint) */
 } pwfa_lbm_params;
+
+#define PWFA_DRIVER_RIGID 0
+#define PWFA_DRIVER_PIC 1
 
 typedef struct pwfa_lbm pwfa_lbm_t;
 
@@ -219,6 +227,23 @@ int64_t pwfa_lbm_steps_done(pwfa_lbm_t* h, int32_t instance);
 /* Planes the moving window of an instance has advanced so far (0 for a fixed
  * box), or a negative error code: box node k sits at lab z = (k + W) dx. */
 int64_t pwfa_lbm_window_planes(pwfa_lbm_t* h, int32_t instance);
+
+/* PIC driver (Eq. 1): n macro-electrons, xp[6][n] FP32 (host or device) =
+ * x, y, z (box coordinates, c/omega_p) at t_{n+1/2} and p_x, p_y, p_z (m_e c)
+ * at t_n, each of weight electrons in units of n0 (c/omega_p)^3. Each step,
+ * after the fluid, they are pushed by the Boris scheme with E(t_{n+1/2}) and
+ * the mean of B(t_n), B(t_{n+1}) interpolated trilinearly from each Yee
+ * component, moved by dt p/gamma, and the current of the move is deposited
+ * on the E edges by Esirkepov's charge-conserving scheme (linear shape);
+ * Ampere subtracts it in place of the rigid J_b. Particles outside an open
+ * grid see no field and deposit only on in-grid edges; periodic grids wrap
+ * them. PWFA_ERR_PARAM unless the instance was created with
+ * PWFA_DRIVER_PIC. Replaces any previous particle set. */
+int pwfa_lbm_set_particles(pwfa_lbm_t* h, int32_t instance, int64_t n, const float* xp, double weight);
+
+/* Current particles, out[6][n] as above (host or device); n from the last
+ * pwfa_lbm_set_particles. Synchronises. */
+int pwfa_lbm_get_particles(pwfa_lbm_t* h, int32_t instance, float* out);
 
 /* Kernel kinds reported by pwfa_lbm_kernel_times. */
 #define PWFA_KERNEL_FARADAY 0 /* Yee B update */

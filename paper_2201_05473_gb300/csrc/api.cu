@@ -48,6 +48,10 @@ struct Instance {
     int fcur = 0;
     float* E[3] = {nullptr, nullptr, nullptr};
     float* Ealt[3] = {nullptr, nullptr, nullptr};  // moving window: E is moved into it
+    float* Jb[3] = {nullptr, nullptr, nullptr};    // PIC driver: deposited current
+    float* particles = nullptr;                    // PIC driver: [6][np]
+    int64_t np = 0;
+    double pweight = 0.0;
     float* B[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int bcur = 0;
     float* J[3] = {nullptr, nullptr, nullptr};
@@ -148,6 +152,8 @@ int validate(const pwfa_lbm_params& p, int idx) {
     if (p.moving_window < 0 || p.moving_window > 1) return bad("moving_window must be 0 or 1");
     if (p.moving_window && p.boundary != PWFA_OPEN) return bad("the moving window needs the open boundary");
     if (p.moving_window && !std::isfinite(p.window_z)) return bad("window_z must be finite");
+    if (p.driver != PWFA_DRIVER_RIGID && p.driver != PWFA_DRIVER_PIC) return bad("unknown driver");
+    if (p.driver == PWFA_DRIVER_PIC && p.moving_window) return bad("the PIC driver does not support the moving window");
     return PWFA_OK;
 }
 
@@ -189,6 +195,7 @@ StepArgs make_args(const Instance& in) {
     a.bx = in.bx;
     a.by = in.by;
     a.staged = in.variant == PWFA_FLUID_STAGED && in.p.storage == PWFA_F32 && in.bx * in.by == 128;
+    for (int c = 0; c < 3; ++c) a.Jb[c] = in.Jb[c];
     return a;
 }
 
@@ -223,6 +230,8 @@ void free_recording(Instance& in) {
 
 void free_instance(Instance& in) {
     free_recording(in);
+    if (in.particles) cudaFree(in.particles);
+    in.particles = nullptr;
     if (in.arena) cudaFree(in.arena);
     in.arena = nullptr;
 }
@@ -235,7 +244,8 @@ int alloc_instance(Instance& in, cudaStream_t s) {
     const size_t pad = align_up((size_t)in.g.nx * in.g.ny * sizeof(float));
     const size_t vbytes = pad + align_up((size_t)N * sizeof(float));
     const size_t pbytes = align_up(sizeof(double) * (in.profile.empty() ? 1 : in.profile.size()));
-    const int nvec = 12 + (in.p.moving_window ? 3 : 0);  // E 3, B 2x3, J 3 (+ E for the window move)
+    // E 3, B 2x3, J 3 (+ E for the window move, + the PIC driver's current)
+    const int nvec = 12 + (in.p.moving_window ? 3 : 0) + (in.p.driver == PWFA_DRIVER_PIC ? 3 : 0);
     const size_t total = 2 * fbytes + nvec * vbytes + pbytes;
     if (cudaMalloc(&in.arena, total) != cudaSuccess) {
         cudaGetLastError();
@@ -254,6 +264,8 @@ int alloc_instance(Instance& in, cudaStream_t s) {
     for (int c = 0; c < 3; ++c) { in.J[c] = (float*)(base + pad); base += vbytes; }
     if (in.p.moving_window)
         for (int c = 0; c < 3; ++c) { in.Ealt[c] = (float*)(base + pad); base += vbytes; }
+    if (in.p.driver == PWFA_DRIVER_PIC)
+        for (int c = 0; c < 3; ++c) { in.Jb[c] = (float*)(base + pad); base += vbytes; }
     in.d_profile = (double*)base;
     // Fields, currents, their guard planes and the second population buffer
     // start at zero.
@@ -331,7 +343,7 @@ bool batch_eligible(const pwfa_lbm* h) {
     const auto& p0 = h->inst[0].p;
     for (const auto& in : h->inst)
         if (in.p.storage != p0.storage || in.p.collision != p0.collision || in.p.boundary != p0.boundary ||
-            in.p.couple != p0.couple || in.p.moving_window)
+            in.p.couple != p0.couple || in.p.moving_window || in.p.driver != PWFA_DRIVER_RIGID)
             return false;
     return true;
 }
@@ -495,6 +507,13 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
     rc = timed_launch(h, PWFA_KERNEL_FLUID, "fluid kernel",
                       [&] { return launch_fluid(a, in.p.storage, in.p.collision, s, diag); });
     if (rc) return rc;
+    if (in.p.driver == PWFA_DRIVER_PIC) {
+        for (int c = 0; c < 3; ++c)
+            PWFA_CUDA(cudaMemsetAsync(in.Jb[c], 0, sizeof(float) * in.g.N, s), "cudaMemsetAsync");
+        rc = timed_launch(h, PWFA_KERNEL_AUX, "particle kernel",
+                          [&] { return launch_push_deposit(a, in.particles, in.np, in.pweight, in.Jb, s); });
+        if (rc) return rc;
+    }
     if (in.p.couple) {
         rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere kernel", [&] { return launch_ampere(a, s); });
         if (rc) return rc;
@@ -549,6 +568,7 @@ int copy_state(const Instance& in, const StateRef& dst, bool to_rec, cudaStream_
 int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_every) {
     cudaStream_t s = h->stream;
     if (in.p.moving_window) return fail(PWFA_ERR_PARAM, "the adjoint does not support the moving window");
+    if (in.p.driver != PWFA_DRIVER_RIGID) return fail(PWFA_ERR_PARAM, "the adjoint needs the rigid driver");
     free_recording(in);
     auto& r = in.rec;
     r.T = nsteps;
@@ -980,6 +1000,43 @@ int64_t pwfa_lbm_steps_done(pwfa_lbm_t* h, int32_t instance) {
     int rc = check_instance(h, instance);
     if (rc) return rc;
     return h->inst[instance].steps;
+}
+
+int pwfa_lbm_set_particles(pwfa_lbm_t* h, int32_t instance, int64_t n, const float* xp, double weight) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    Instance& in = h->inst[instance];
+    if (in.p.driver != PWFA_DRIVER_PIC) return fail(PWFA_ERR_PARAM, "the instance was not created with the PIC driver");
+    if (n < 0 || (n > 0 && !xp)) return fail(PWFA_ERR_PARAM, "bad particle array");
+    if (!(weight >= 0) || !std::isfinite(weight)) return fail(PWFA_ERR_PARAM, "weight must be finite and >= 0");
+    PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (in.particles) cudaFree(in.particles);
+    in.particles = nullptr;
+    in.np = 0;
+    if (n > 0) {
+        if (cudaMalloc(&in.particles, sizeof(float) * 6 * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the particle array failed");
+        }
+        PWFA_CUDA(cudaMemcpyAsync(in.particles, xp, sizeof(float) * 6 * (size_t)n, cudaMemcpyDefault, h->stream),
+                  "particle copy");
+        PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    }
+    in.np = n;
+    in.pweight = weight;
+    return PWFA_OK;
+}
+
+int pwfa_lbm_get_particles(pwfa_lbm_t* h, int32_t instance, float* out) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    Instance& in = h->inst[instance];
+    if (in.np == 0) return PWFA_OK;
+    if (!out) return fail(PWFA_ERR_PARAM, "out is NULL");
+    PWFA_CUDA(cudaMemcpyAsync(out, in.particles, sizeof(float) * 6 * (size_t)in.np, cudaMemcpyDefault, h->stream),
+              "particle copy");
+    PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return PWFA_OK;
 }
 
 int64_t pwfa_lbm_window_planes(pwfa_lbm_t* h, int32_t instance) {

@@ -17,6 +17,7 @@ constexpr int kThreads = kBatchTile;
 // the same entry (broadcast), so no shared-memory copy and no barrier is
 // needed anywhere in the kernel.
 __constant__ BatchEntry c_entries[kMaxBatch];
+static_assert(sizeof(BatchEntry) * kMaxBatch <= 60 * 1024, "instance table exceeds constant memory");
 
 // Resident blocks per SM: the fluid phase needs up to 128 registers (4 blocks
 // of 128 threads); the light field phases run 8 blocks (64 registers).

@@ -61,13 +61,15 @@ __device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int
     if (PER || (i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2)) {
         const float curl = (yee_ld<PER>(g, Bz, i, j, k) - yee_ld<PER>(g, Bz, i, j - 1, k))
                          - (yee_ld<PER>(g, By, i, j, k) - yee_ld<PER>(g, By, i, j, k - 1));
-        const float je = 0.5f * (yee_ld<PER>(g, a.J[0], i, j, k) + yee_ld<PER>(g, a.J[0], i + 1, j, k));
+        float je = 0.5f * (yee_ld<PER>(g, a.J[0], i, j, k) + yee_ld<PER>(g, a.J[0], i + 1, j, k));
+        if (a.Jb[0]) je += a.Jb[0][o];
         a.Eout[0][o] = a.Eout[0][o] + c * curl - dt * je;
     }
     if (PER || (i >= 1 && i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2)) {
         const float curl = (yee_ld<PER>(g, Bx, i, j, k) - yee_ld<PER>(g, Bx, i, j, k - 1))
                          - (yee_ld<PER>(g, Bz, i, j, k) - yee_ld<PER>(g, Bz, i - 1, j, k));
-        const float je = 0.5f * (yee_ld<PER>(g, a.J[1], i, j, k) + yee_ld<PER>(g, a.J[1], i, j + 1, k));
+        float je = 0.5f * (yee_ld<PER>(g, a.J[1], i, j, k) + yee_ld<PER>(g, a.J[1], i, j + 1, k));
+        if (a.Jb[1]) je += a.Jb[1][o];
         a.Eout[1][o] = a.Eout[1][o] + c * curl - dt * je;
     }
     if (PER || (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2)) {
@@ -75,7 +77,9 @@ __device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int
                          - (yee_ld<PER>(g, Bx, i, j, k) - yee_ld<PER>(g, Bx, i, j - 1, k));
         const float je = 0.5f * (yee_ld<PER>(g, a.J[2], i, j, k) + yee_ld<PER>(g, a.J[2], i, j, k + 1));
         float jb = 0.0f;
-        if (a.alpha != 0.0f) {
+        if (a.Jb[2]) {
+            jb = a.Jb[2][o];
+        } else if (a.alpha != 0.0f) {
             const float xr = ((float)i - 0.5f * (float)(nx - 1)) * a.dx;
             const float yr = ((float)j - 0.5f * (float)(ny - 1)) * a.dx;
             const float zeta = ((float)k + 0.5f) * a.dx - zc;

@@ -112,6 +112,7 @@ struct StepArgs {
     int couple;
     // driver: J_b,z = -alpha exp(-r^2/(2 sr^2) - (z - zc)^2/(2 sz^2)) at t_{n+1}
     float alpha, inv2sr2, inv2sz2, zc, dx;
+    const float* Jb[3];   // PIC driver: deposited current on the E edges (else null)
     uint32_t src_shift;   // added to every pulled source node: nx*ny on a step
                           // that moves the window (the streaming source is
                           // read one plane up), else 0

@@ -47,6 +47,13 @@ struct WindowMove {
 };
 cudaError_t launch_window_move(const WindowMove& w, cudaStream_t s);
 
+// PIC driver: push np macro-electrons (xp[6][np]: x, y, z at t_{n+1/2},
+// p_x, p_y, p_z at t_n) with the step's fields and add the current of their
+// moves to Jb (E-edge arrays, zeroed by the caller). weight: electrons per
+// macro-particle in units of n0 (c/omega_p)^3.
+cudaError_t launch_push_deposit(const StepArgs& a, float* xp, int64_t np, double weight, float* const Jb[3],
+                                cudaStream_t s);
+
 // Initial condition: stored populations whose pull gives the plasma at rest,
 // f = w_i n0 prof(r) (lattice 0), 0 (momentum lattices).
 cudaError_t launch_init(const Grid& g, void* f, int storage, float n0, const double* d_profile,

@@ -44,6 +44,7 @@ class Params(ctypes.Structure):
         ("alpha", ctypes.c_double), ("sigma_r", ctypes.c_double), ("sigma_z", ctypes.c_double),
         ("z0", ctypes.c_double), ("n_floor", ctypes.c_double),
         ("moving_window", ctypes.c_int32), ("window_z", ctypes.c_double),
+        ("driver", ctypes.c_int32),
     ]
 
 
@@ -76,7 +77,7 @@ EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_
            "pwfa_lbm_step_diag", "pwfa_lbm_linecut", "pwfa_lbm_set_fluid_variant", "pwfa_lbm_get_fluid_variant",
            "pwfa_lbm_window_planes", "pwfa_axi_create", "pwfa_axi_step", "pwfa_axi_fields",
            "pwfa_axi_get_source", "pwfa_axi_set_source", "pwfa_axi_steps_done", "pwfa_axi_profile",
-           "pwfa_axi_kernel_times", "pwfa_axi_destroy")
+           "pwfa_axi_kernel_times", "pwfa_axi_destroy", "pwfa_lbm_set_particles", "pwfa_lbm_get_particles")
 
 
 def load(build: bool = True):
@@ -112,6 +113,10 @@ def load(build: bool = True):
         lib.pwfa_axi_profile.argtypes = [vp, i32]
         lib.pwfa_axi_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         lib.pwfa_axi_destroy.argtypes = [vp]
+        lib.pwfa_lbm_set_particles.argtypes = [vp, i32, i64, vp, ctypes.c_double]
+        lib.pwfa_lbm_set_particles.restype = ctypes.c_int
+        lib.pwfa_lbm_get_particles.argtypes = [vp, i32, vp]
+        lib.pwfa_lbm_get_particles.restype = ctypes.c_int
         for name in ("pwfa_axi_create", "pwfa_axi_step", "pwfa_axi_fields", "pwfa_axi_get_source",
                      "pwfa_axi_set_source", "pwfa_axi_profile", "pwfa_axi_kernel_times", "pwfa_axi_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -171,6 +176,7 @@ def params_of(w: W.Workload):
     p.alpha, p.sigma_r, p.sigma_z, p.z0 = w.alpha, w.sigma_r, w.sigma_z, w.z0
     p.n_floor = w.n_floor
     p.moving_window, p.window_z = int(w.moving_window), w.window_z
+    p.driver = int(w.driver)
     return p, keep
 
 
@@ -245,6 +251,21 @@ class Simulation:
         if r < 0:
             _check(int(r))
         return int(r)
+
+    def set_particles(self, xp, weight: float, instance: int = 0):
+        """PIC driver: xp[6][n] = x, y, z at t_{n+1/2}, p_x, p_y, p_z at t_n."""
+        t = self._torch
+        a = xp.contiguous().to(t.float32) if isinstance(xp, t.Tensor) else \
+            t.from_numpy(np.ascontiguousarray(xp, dtype=np.float32))
+        self._np = getattr(self, "_np", {})
+        self._np[instance] = int(a.shape[1])
+        _check(self._lib.pwfa_lbm_set_particles(self._h, instance, int(a.shape[1]), _ptr(a), float(weight)))
+
+    def get_particles(self, instance: int = 0):
+        n = getattr(self, "_np", {}).get(instance, 0)
+        out = self._torch.empty((6, n), dtype=self._torch.float32, device="cuda")
+        _check(self._lib.pwfa_lbm_get_particles(self._h, instance, _ptr(out)))
+        return out
 
     def window_planes(self, instance: int = 0) -> int:
         """Planes the moving window has advanced (box node k sits at lab

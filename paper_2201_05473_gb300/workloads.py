@@ -48,6 +48,7 @@ class Workload:
     profile_rmax: float = 0.0
     moving_window: int = 0   # 1: the box follows the driver once it passes window_z
     window_z: float = 0.0
+    driver: int = 0          # 0 rigid bi-Gaussian bunch, 1 macro-particles (PIC)
     name: str = ""
 
     @property
