@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_ke
     const bool row_in = y >= 1 && y <= g.ny - 2 && z >= 1 && z <= g.nz - 2;
     const bool xwall = !PER && !SHELL && live && row_in && (x == 0 || (x == g.nx - 1 && lane != 0));
     const int64_t LS = lattice_stride(g);
-    const T* __restrict__ fin = static_cast<const T*>(s.fin) + l * LS;
+    const T* __restrict__ fin = static_cast<const T*>(s.fin);
     const float* __restrict__ Sin = a.Sbar_in + l * LS;
     float* __restrict__ Sout = a.Sbar_out + l * LS;
     if (!SHELL && live && bnd) {
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_ke
             uint32_t src;
             if (PER) src = (uint32_t)src_index<true>(g, xs, ys, zs, q);
             else src = nodec - (uint32_t)(xi_x(q) + xi_y(q) * g.nx) - (uint32_t)xi_z(q) * sxy;
-            Al += Codec<ST>::load(fin + pop_off(q, src), l, q, s.n0);
+            Al += Codec<ST>::load(fin + pop_elem<ST>(l, pop_off(q, src), LS), l, q, s.n0);
             S[q] = __ldg(Sin + pop_off(q, node));
         }
         float v[3] = {0.0f, 0.0f, 0.0f};

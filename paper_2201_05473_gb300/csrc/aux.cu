@@ -54,9 +54,10 @@ __global__ void init_kernel(Grid g, typename Codec<ST>::T* f, float n0, const do
             n = (float)((double)n0 * profile_at(prof, np, rmax, sqrt(rx * rx + ry * ry)));
         }
         const uint32_t off = pop_off(q, (uint32_t)node);
-        Codec<ST>::store(f + off, wq(q) * n, 0, q, n0);
+        const int64_t LS = lattice_stride(g);
+        Codec<ST>::store(f + pop_elem<ST>(0, off, LS), wq(q) * n, 0, q, n0);
 #pragma unroll
-        for (int l = 1; l < kL; ++l) Codec<ST>::store(f + l * lattice_stride(g) + off, 0.0f, l, q, n0);
+        for (int l = 1; l < kL; ++l) Codec<ST>::store(f + pop_elem<ST>(l, off, LS), 0.0f, l, q, n0);
     }
 }
 
@@ -101,7 +102,7 @@ __global__ void import_f_kernel(Grid g, const float* in, typename Codec<ST>::T* 
         else { sx = min(max(sx, 0), g.nx - 1); sy = min(max(sy, 0), g.ny - 1); sz = min(max(sz, 0), g.nz - 1); }
         const int64_t src = ((int64_t)sz * g.ny + sy) * g.nx + sx;
         for (int l = 0; l < kL; ++l)
-            Codec<ST>::store(f + l * lattice_stride(g) + pop_off(q, (uint32_t)node),
+            Codec<ST>::store(f + pop_elem<ST>(l, pop_off(q, (uint32_t)node), lattice_stride(g)),
                              in[(int64_t)(l * kQ + q) * g.N + src], l, q, n0);
     }
 }

@@ -60,7 +60,6 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
 
     const int64_t LS = lattice_stride(g);
     T* const fo0 = static_cast<T*>(a.fout);
-    T* const fo[kL] = {fo0, fo0 + LS, fo0 + 2 * LS, fo0 + 3 * LS};
     const float u[3] = {beta[0] * a.lat, beta[1] * a.lat, beta[2] * a.lat};
     float phi[kQ];
     eq_factors(u, phi);
@@ -71,46 +70,55 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
 #pragma unroll
             for (int q = 0; q < kQ; ++q) f[l][q] = A[l] * phi[q];
     }
+    // Collide in place, lattice pair by lattice pair; FP32 stores each value
+    // as it is made, the 16-bit forms store each pair of lattices as 32-bit
+    // words (pop_elem).
     const float om = a.omega;
 #pragma unroll
-    for (int l = 0; l < kL; ++l) {
-        const float Fl = l == 0 ? 0.0f : F[l - 1] * a.dt;
-        if (COLL == 2) {
-            // streaming only: f* = f
+    for (int pr = 0; pr < kL / 2; ++pr) {
+#pragma unroll
+        for (int l = 2 * pr; l < 2 * pr + 2; ++l) {
+            const float Fl = l == 0 ? 0.0f : F[l - 1] * a.dt;
+            if (COLL == 0) {
+                // BGK, Eq. 7, plus the source of Eq. 10
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) f[l][q] = f[l][q] + om * (A[l] * phi[q] - f[l][q]) + wq(q) * Fl;
+            } else if (COLL == 1) {
+                // Regularized: relax only the first Hermite moment of f - f^eq,
+                // Pi = sum_i xi_i (f_i - A phi_i) = sum_i xi_i f_i - A u
+                // (sum_i xi_i phi_i = u exactly for the D3Q19 weights).
+                float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+#pragma unroll
+                for (int q = 1; q < kQ; ++q) {
+                    if (xi_x(q) > 0) m0 += f[l][q]; else if (xi_x(q) < 0) m0 -= f[l][q];
+                    if (xi_y(q) > 0) m1 += f[l][q]; else if (xi_y(q) < 0) m1 -= f[l][q];
+                    if (xi_z(q) > 0) m2 += f[l][q]; else if (xi_z(q) < 0) m2 -= f[l][q];
+                }
+                const float k3 = 3.0f * (1.0f - om);
+                const float P0 = k3 * (m0 - A[l] * u[0]);
+                const float P1 = k3 * (m1 - A[l] * u[1]);
+                const float P2 = k3 * (m2 - A[l] * u[2]);
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) {
+                    float xp = 0.0f;
+                    if (xi_x(q)) xp += (float)xi_x(q) * P0;
+                    if (xi_y(q)) xp += (float)xi_y(q) * P1;
+                    if (xi_z(q)) xp += (float)xi_z(q) * P2;
+                    f[l][q] = A[l] * phi[q] + wq(q) * (xp + Fl);
+                }
+            }
+            // (stream only: f* = f)
+            if constexpr (ST == 0) {
+#pragma unroll
+                for (int q = 0; q < kQ; ++q)
+                    Codec<ST>::store(fo0 + pop_elem<ST>(l, pop_off(q, node), LS), f[l][q], l, q, a.n0);
+            }
+        }
+        if constexpr (ST != 0) {
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                Codec<ST>::store(fo[l] + pop_off(q, node), f[l][q], l, q, a.n0);
-        } else if (COLL == 0) {
-            // BGK, Eq. 7, plus the source of Eq. 10
-#pragma unroll
-            for (int q = 0; q < kQ; ++q) {
-                const float fs = f[l][q] + om * (A[l] * phi[q] - f[l][q]) + wq(q) * Fl;
-                Codec<ST>::store(fo[l] + pop_off(q, node), fs, l, q, a.n0);
-            }
-        } else {
-            // Regularized: relax only the first Hermite moment of f - f^eq,
-            // Pi = sum_i xi_i (f_i - A phi_i) = sum_i xi_i f_i - A u
-            // (sum_i xi_i phi_i = u exactly for the D3Q19 weights).
-            float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
-#pragma unroll
-            for (int q = 1; q < kQ; ++q) {
-                if (xi_x(q) > 0) m0 += f[l][q]; else if (xi_x(q) < 0) m0 -= f[l][q];
-                if (xi_y(q) > 0) m1 += f[l][q]; else if (xi_y(q) < 0) m1 -= f[l][q];
-                if (xi_z(q) > 0) m2 += f[l][q]; else if (xi_z(q) < 0) m2 -= f[l][q];
-            }
-            const float k3 = 3.0f * (1.0f - om);
-            const float P0 = k3 * (m0 - A[l] * u[0]);
-            const float P1 = k3 * (m1 - A[l] * u[1]);
-            const float P2 = k3 * (m2 - A[l] * u[2]);
-#pragma unroll
-            for (int q = 0; q < kQ; ++q) {
-                float xp = 0.0f;
-                if (xi_x(q)) xp += (float)xi_x(q) * P0;
-                if (xi_y(q)) xp += (float)xi_y(q) * P1;
-                if (xi_z(q)) xp += (float)xi_z(q) * P2;
-                const float fs = A[l] * phi[q] + wq(q) * (xp + Fl);
-                Codec<ST>::store(fo[l] + pop_off(q, node), fs, l, q, a.n0);
-            }
+                Codec<ST>::store2(fo0 + pop_elem<ST>(2 * pr, pop_off(q, node), LS), f[2 * pr][q], f[2 * pr + 1][q],
+                                  2 * pr, q, a.n0);
         }
     }
 

@@ -55,6 +55,8 @@ template <> struct Codec<0> {
     static __device__ __forceinline__ float load(const T* p, int, int, float) { return __ldg(p); }
     static __device__ __forceinline__ void store(T* p, float v, int, int, float) { __stcs(p, v); }
 };
+// The 16-bit codecs also move the pair of lattices (l0, l0 + 1) that share a
+// 32-bit word (see pop_elem): p points at the word's first (even) element.
 template <> struct Codec<1> {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float load(const T* p, int l, int q, float n0) {
@@ -62,6 +64,15 @@ template <> struct Codec<1> {
     }
     static __device__ __forceinline__ void store(T* p, float v, int l, int q, float n0) {
         *p = __float2bfloat16_rn(v - dev_base(l, q, n0));
+    }
+    static __device__ __forceinline__ void load2(const T* p, int l0, int q, float n0, float& v0, float& v1) {
+        const float2 w = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+        v0 = w.x + dev_base(l0, q, n0);
+        v1 = w.y + dev_base(l0 + 1, q, n0);
+    }
+    static __device__ __forceinline__ void store2(T* p, float v0, float v1, int l0, int q, float n0) {
+        *reinterpret_cast<__nv_bfloat162*>(p) =
+            __floats2bfloat162_rn(v0 - dev_base(l0, q, n0), v1 - dev_base(l0 + 1, q, n0));
     }
 };
 template <> struct Codec<2> {
@@ -71,6 +82,15 @@ template <> struct Codec<2> {
     }
     static __device__ __forceinline__ void store(T* p, float v, int l, int q, float n0) {
         *p = __float2half_rn((v - dev_base(l, q, n0)) * (kF16Scale / wq(q)));
+    }
+    static __device__ __forceinline__ void load2(const T* p, int l0, int q, float n0, float& v0, float& v1) {
+        const float2 w = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+        v0 = w.x * (wq(q) / kF16Scale) + dev_base(l0, q, n0);
+        v1 = w.y * (wq(q) / kF16Scale) + dev_base(l0 + 1, q, n0);
+    }
+    static __device__ __forceinline__ void store2(T* p, float v0, float v1, int l0, int q, float n0) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn((v0 - dev_base(l0, q, n0)) * (kF16Scale / wq(q)),
+                                                            (v1 - dev_base(l0 + 1, q, n0)) * (kF16Scale / wq(q)));
     }
 };
 
@@ -92,6 +112,16 @@ __host__ __device__ __forceinline__ uint32_t pop_off(int q, uint32_t node) {
     return (node >> 5) * (uint32_t)(kQ * 32) + (uint32_t)q * 32u + (node & 31u);
 }
 __host__ __device__ __forceinline__ int64_t lattice_stride(const Grid& g) { return (int64_t)kQ * g.Np; }
+
+// Element index of population (l, i) at chunked offset off (LS = 19 Np).
+// FP32 keeps one block per lattice. The 16-bit forms pair the lattices
+// (0, 1) and (2, 3) in 32-bit words, so that a thread's loads and stores each
+// move two values: pair block p holds 19 Np words and word off holds
+// {lattice 2p, lattice 2p + 1}. Both forms take 76 Np elements.
+template <int ST>
+__host__ __device__ __forceinline__ int64_t pop_elem(int l, uint32_t off, int64_t LS) {
+    return ST == 0 ? (int64_t)l * LS + off : (int64_t)(l >> 1) * 2 * LS + 2 * (int64_t)off + (l & 1);
+}
 
 // One instance's device state as the step kernels see it.
 struct StepArgs {
