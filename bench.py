@@ -237,7 +237,11 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         sim = lbm.Simulation(w, stream=stream)
         sim.step(args.warmup)
-        sim.autotune(3)
+        if args.launch:
+            # fixed shape, no autotuner trial launches (profiling captures)
+            sim.set_launch(*(int(v) for v in args.launch.lower().split("x")))
+        else:
+            sim.autotune(3)
         launch_shape = sim.get_launch()
         fluid_variant = ["direct", "staged"][sim.get_fluid_variant()]
         sim.kernel_times()  # reset counters
@@ -561,6 +565,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", default="", help="override the grid as ZxYxX (profiling captures)")
+    ap.add_argument("--launch", default="", help="fixed fluid block shape BXxBY instead of the autotuner "
+                                                 "(profiling captures)")
     ap.add_argument("--no-extra", action="store_true", help="skip the BF16/FP16 and adjoint lines")
     ap.add_argument("--adjoint-steps", type=int, default=500)
     ap.add_argument("--only", default="", choices=["", "storage", "adjoint", "batched", "window", "axisymmetric", "pic"],

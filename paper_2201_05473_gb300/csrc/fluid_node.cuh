@@ -60,6 +60,8 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
 
     const int64_t LS = lattice_stride(g);
     T* const fo0 = static_cast<T*>(a.fout);
+    // per-lattice (FP32) or per-pair (16-bit) base pointers, 32-bit offsets
+    T* const fo[kL] = {fo0, fo0 + LS, fo0 + 2 * LS, fo0 + 3 * LS};
     const float u[3] = {beta[0] * a.lat, beta[1] * a.lat, beta[2] * a.lat};
     float phi[kQ];
     eq_factors(u, phi);
@@ -110,15 +112,13 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
             // (stream only: f* = f)
             if constexpr (ST == 0) {
 #pragma unroll
-                for (int q = 0; q < kQ; ++q)
-                    Codec<ST>::store(fo0 + pop_elem<ST>(l, pop_off(q, node), LS), f[l][q], l, q, a.n0);
+                for (int q = 0; q < kQ; ++q) Codec<ST>::store(fo[l] + pop_off(q, node), f[l][q], l, q, a.n0);
             }
         }
         if constexpr (ST != 0) {
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
-                Codec<ST>::store2(fo0 + pop_elem<ST>(2 * pr, pop_off(q, node), LS), f[2 * pr][q], f[2 * pr + 1][q],
-                                  2 * pr, q, a.n0);
+                Codec<ST>::store2(fo[2 * pr] + 2 * pop_off(q, node), f[2 * pr][q], f[2 * pr + 1][q], 2 * pr, q, a.n0);
         }
     }
 

@@ -36,6 +36,9 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
         bnd = (xs != x) | (ys != y) | (zs != z);
     }
     const int64_t LS = lattice_stride(g);
+    // per-lattice (FP32) or per-pair (16-bit) base pointers; 32-bit offsets
+    const T* __restrict__ fl[kL] = {fin, fin + LS, fin + 2 * LS, fin + 3 * LS};
+    const T* __restrict__ fp[2] = {fin, fin + 2 * LS};
     const uint32_t sxy = (uint32_t)g.nx * (uint32_t)g.ny;
     const uint32_t nodec =
         ((uint32_t)zs * (uint32_t)g.ny + (uint32_t)ys) * (uint32_t)g.nx + (uint32_t)xs + (PER ? 0u : src_shift);
@@ -51,10 +54,10 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
         const uint32_t off = pop_off(q, src);
         if constexpr (ST == 0) {
 #pragma unroll
-            for (int l = 0; l < kL; ++l) f[l][q] = Codec<ST>::load(fin + pop_elem<ST>(l, off, LS), l, q, n0);
+            for (int l = 0; l < kL; ++l) f[l][q] = Codec<ST>::load(fl[l] + off, l, q, n0);
         } else {
-            Codec<ST>::load2(fin + pop_elem<ST>(0, off, LS), 0, q, n0, f[0][q], f[1][q]);
-            Codec<ST>::load2(fin + pop_elem<ST>(2, off, LS), 2, q, n0, f[2][q], f[3][q]);
+            Codec<ST>::load2(fp[0] + 2 * off, 0, q, n0, f[0][q], f[1][q]);
+            Codec<ST>::load2(fp[1] + 2 * off, 2, q, n0, f[2][q], f[3][q]);
         }
     }
 }
