@@ -103,8 +103,10 @@ struct pwfa_lbm {
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph2 = nullptr;  // two steps (both parities)
     // fused per-step diagnostics: per-block records and per-instance results
-    double* d_step_partials = nullptr;
-    int64_t step_partials_cap = 0;
+    float* d_step_records = nullptr;  // fused-diagnostics records (fluid blocks, then Faraday blocks)
+    int64_t step_records_cap = 0;
+    int64_t step_energy_cap = 0;
+    double* d_step_scratch = nullptr;  // kDiagBlocks FP64 records of the two-level reduction
     double* d_step_diag = nullptr;
 };
 
@@ -500,12 +502,21 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
     }
     StepArgs a = make_args(in);
     int rc;
+    DiagOut dg{};
+    if (diag) dg = *diag;
     if (in.p.couple) {
-        rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(a, s); });
+        // with diagnostics the Faraday launch also takes the field energy of
+        // the entering state (it reads E and B(t_n) anyway)
+        float* energy = nullptr;
+        if (diag && faraday_blocks(in.g) <= dg.energy_capacity) {
+            energy = dg.energy;
+            dg.nenergy = faraday_blocks(in.g);
+        }
+        rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(a, s, energy); });
         if (rc) return rc;
     }
     rc = timed_launch(h, PWFA_KERNEL_FLUID, "fluid kernel",
-                      [&] { return launch_fluid(a, in.p.storage, in.p.collision, s, diag); });
+                      [&] { return launch_fluid(a, in.p.storage, in.p.collision, s, diag ? &dg : nullptr); });
     if (rc) return rc;
     if (in.p.driver == PWFA_DRIVER_PIC) {
         for (int c = 0; c < 3; ++c)
@@ -729,26 +740,29 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
 
 
 int ensure_step_diag(pwfa_lbm* h) {
-    int64_t need = 1;
+    int64_t need = 1, need_e = 1;
     for (const auto& in : h->inst) {
         const int64_t b = (int64_t)((in.g.nx + in.bx - 1) / in.bx) * ((in.g.ny + in.by - 1) / in.by) * in.g.nz;
         need = std::max(need, b);
+        need_e = std::max(need_e, faraday_blocks(in.g));
     }
     if (!h->d_step_diag) {
-        if (cudaMalloc(&h->d_step_diag, sizeof(double) * 8 * h->inst.size()) != cudaSuccess) {
+        if (cudaMalloc(&h->d_step_diag, sizeof(double) * 8 * h->inst.size()) != cudaSuccess ||
+            cudaMalloc(&h->d_step_scratch, sizeof(double) * 8 * kDiagBlocks) != cudaSuccess) {
             cudaGetLastError();
             return fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics results failed");
         }
     }
-    if (need > h->step_partials_cap) {
-        if (h->d_step_partials) cudaFree(h->d_step_partials);
-        h->d_step_partials = nullptr;
-        h->step_partials_cap = 0;
-        if (cudaMalloc(&h->d_step_partials, sizeof(double) * 8 * need) != cudaSuccess) {
+    if (need > h->step_records_cap || need_e > h->step_energy_cap) {
+        if (h->d_step_records) cudaFree(h->d_step_records);
+        h->d_step_records = nullptr;
+        h->step_records_cap = h->step_energy_cap = 0;
+        if (cudaMalloc(&h->d_step_records, sizeof(float) * (8 * need + need_e)) != cudaSuccess) {
             cudaGetLastError();
             return fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics records failed");
         }
-        h->step_partials_cap = need;
+        h->step_records_cap = need;
+        h->step_energy_cap = need_e;
     }
     return PWFA_OK;
 }
@@ -768,7 +782,14 @@ int pwfa_lbm_step_diag(pwfa_lbm_t* h, int32_t nsteps, double* host_diag) {
     if (rc) return rc;
     for (size_t i = 0; i < h->inst.size(); ++i) {
         Instance& in = h->inst[i];
-        DiagOut d{h->d_step_partials, h->step_partials_cap, h->d_step_diag + 8 * i, in.p.dx * in.p.dx * in.p.dx};
+        DiagOut d{};
+        d.records = h->d_step_records;
+        d.capacity = h->step_records_cap;
+        d.energy = h->d_step_records + 8 * h->step_records_cap;
+        d.energy_capacity = h->step_energy_cap;
+        d.scratch = h->d_step_scratch;
+        d.out = h->d_step_diag + 8 * i;
+        d.dxcube = in.p.dx * in.p.dx * in.p.dx;
         rc = step_instance(h, in, &d);
         if (rc) return rc;
     }
@@ -1182,8 +1203,9 @@ int pwfa_lbm_destroy(pwfa_lbm_t* h) {
     batch_release(h);
     if (h->d_entries) cudaFree(h->d_entries);
     if (h->d_steps) cudaFree(h->d_steps);
-    if (h->d_step_partials) cudaFree(h->d_step_partials);
+    if (h->d_step_records) cudaFree(h->d_step_records);
     if (h->d_step_diag) cudaFree(h->d_step_diag);
+    if (h->d_step_scratch) cudaFree(h->d_step_scratch);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;
     return PWFA_OK;

@@ -254,12 +254,41 @@ __global__ void __launch_bounds__(kDiagThreads) diag_finish_kernel(const double*
     diag_block_reduce(d, out);
 }
 
+// Block b combines FP32 fluid records [b per, (b + 1) per) and energy
+// records [b per_e, (b + 1) per_e) in FP64 into scratch[b].
+__global__ void __launch_bounds__(kDiagThreads) diag_chunk_kernel(const float* rec, int64_t nrec, int64_t per,
+                                                                  const float* en, int64_t nen, int64_t per_e,
+                                                                  double dxcube, double* scratch) {
+    Diag d{0, 0, 0, 0, 0, 1e300, 0, 0};
+    const int64_t b0 = (int64_t)blockIdx.x * per;
+    const int64_t b1 = b0 + per < nrec ? b0 + per : nrec;
+    for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+        const float4 p = reinterpret_cast<const float4*>(rec)[2 * b];
+        const float4 q = reinterpret_cast<const float4*>(rec)[2 * b + 1];
+        diag_combine(d, Diag{p.x, p.y, p.z, p.w, q.x, q.y >= 3.0e38f ? 1e300 : (double)q.y, q.z, q.w});
+    }
+    const int64_t e0 = (int64_t)blockIdx.x * per_e;
+    const int64_t e1 = e0 + per_e < nen ? e0 + per_e : nen;
+    for (int64_t b = e0 + threadIdx.x; b < e1; b += blockDim.x) d.en += en[b];
+    d.en *= dxcube;
+    diag_block_reduce(d, scratch + 8 * (int64_t)blockIdx.x);
+}
+
 dim3 node_grid(const Grid& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz); }
 
 }  // namespace
 
-cudaError_t launch_diag_finish(const double* partials, int64_t nparts, double* out, cudaStream_t s) {
-    diag_finish_kernel<<<1, kDiagThreads, 0, s>>>(partials, nparts, out);
+cudaError_t launch_diag_finish_step(const DiagOut& d, int64_t nrec, cudaStream_t s) {
+    int64_t chunks = (nrec + 1023) / 1024;
+    if (chunks < 1) chunks = 1;
+    if (chunks > kDiagBlocks) chunks = kDiagBlocks;
+    const int64_t per = (nrec + chunks - 1) / chunks;
+    const int64_t per_e = (d.nenergy + chunks - 1) / chunks;
+    diag_chunk_kernel<<<(unsigned)chunks, kDiagThreads, 0, s>>>(d.records, nrec, per, d.energy, d.nenergy, per_e,
+                                                                d.dxcube, d.scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diag_finish_kernel<<<1, kDiagThreads, 0, s>>>(d.scratch, chunks, d.out);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,35 @@ __global__ void __launch_bounds__(kBX * kBY) faraday_kernel(const StepArgs a) {
     faraday_node<PER>(a, i, j, blockIdx.z);
 }
 
+// Faraday with the field energy of its nodes: (|E|^2 + |Bc|^2)/2 at each
+// node's index (the six staggered components stored there), summed in FP32
+// over the block (256 nodes) into energy[block].
+template <bool PER>
+__global__ void __launch_bounds__(kBX * kBY) faraday_energy_kernel(const StepArgs a, float* energy) {
+    const int i = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y;
+    float e2 = 0.0f;
+    if (i < a.g.nx && j < a.g.ny) {
+        faraday_node<PER>(a, i, j, blockIdx.z);
+        const int64_t o = ((int64_t)blockIdx.z * a.g.ny + j) * a.g.nx + i;
+        for (int c = 0; c < 3; ++c) {
+            const float ev = __ldg(a.E[c] + o), bv = __ldg(a.Bc[c] + o);
+            e2 += ev * ev + bv * bv;
+        }
+        e2 *= 0.5f;
+    }
+    for (int off = 16; off > 0; off >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, off);
+    __shared__ float sh[kBX * kBY / 32];
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    if ((tid & 31) == 0) sh[tid >> 5] = e2;
+    __syncthreads();
+    if (tid < 32) {
+        e2 = tid < kBX * kBY / 32 ? sh[tid] : 0.0f;
+        for (int off = 16; off > 0; off >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, off);
+        if (tid == 0) energy[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = e2;
+    }
+}
+
 template <bool PER>
 __global__ void __launch_bounds__(kBX * kBY) ampere_kernel(const StepArgs a) {
     const int i = blockIdx.x * kBX + threadIdx.x;
@@ -88,10 +117,17 @@ cudaError_t launch_zero_walls(const StepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s) {
+int64_t faraday_blocks(const Grid& g) {
+    return (int64_t)((g.nx + kBX - 1) / kBX) * ((g.ny + kBY - 1) / kBY) * g.nz;
+}
+
+cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s, float* energy) {
     dim3 block(kBX, kBY, 1);
     dim3 grid((a.g.nx + kBX - 1) / kBX, (a.g.ny + kBY - 1) / kBY, a.g.nz);
-    if (a.g.periodic) faraday_kernel<true><<<grid, block, 0, s>>>(a);
+    if (energy) {
+        if (a.g.periodic) faraday_energy_kernel<true><<<grid, block, 0, s>>>(a, energy);
+        else faraday_energy_kernel<false><<<grid, block, 0, s>>>(a, energy);
+    } else if (a.g.periodic) faraday_kernel<true><<<grid, block, 0, s>>>(a);
     else faraday_kernel<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -28,39 +28,16 @@ __global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
     fluid_node<ST, COLL, PER>(a, x, y, blockIdx.z);
 }
 
-// The same step with the FP64 diagnostics of the entering state fused in:
-// each block writes one record (sum n, sum n p_k, field energy, min n,
-// max |beta|, non-finite count) to partials[block]; launch_diag_finish
-// reduces the records.
-template <int ST, int COLL, bool PER>
-__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
-    fluid_diag_kernel(const StepArgs a, double dxcube, double* partials) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    // per-node values and the warp-level reduction in FP32 (FP64 is slow on
-    // this part); warps are combined in FP64 by one thread per block
-    float v[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 3.0e38f, 0.0f, 0.0f};
-    if (x < a.g.nx && y < a.g.ny) {
-        NodeDiag nd;
-        fluid_node<ST, COLL, PER, true>(a, x, y, z, &nd);
-        const int64_t o = ((int64_t)z * a.g.ny + y) * a.g.nx + x;
-        float e2 = 0.0f;
-        for (int c = 0; c < 3; ++c) {
-            const float ev = __ldg(a.E[c] + o), bv = __ldg(a.Bc[c] + o);
-            e2 += ev * ev + bv * bv;
-        }
-        const bool fin = isfinite(nd.n) && isfinite(nd.a1) && isfinite(nd.a2) && isfinite(nd.a3);
-        v[0] = nd.n; v[1] = nd.a1; v[2] = nd.a2; v[3] = nd.a3;
-        v[4] = 0.5f * e2;
-        v[5] = nd.n;
-        v[6] = sqrtf(nd.beta2);
-        v[7] = fin ? 0.0f : 1.0f;
-    }
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nthr = blockDim.x * blockDim.y;
-    __shared__ double sh[PWFA_FLUID_MAX_THREADS / 32][8];
+// The same step with the diagnostics of the entering state fused in: each
+// block writes one FP32 record (sum n, sum n p_k, field energy / dx^3 when
+// fields is set, min n, max |beta|, non-finite count) to records[block];
+// launch_diag_finish_step combines the records in FP64. The block sums run
+// over at most PWFA_FLUID_MAX_THREADS nodes, so FP32 costs them ~1e-7
+// relative; FP64 arithmetic, slow on this part, stays out of this kernel.
+__device__ __forceinline__ void diag8_warp(float (&v)[8]) {
+#pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
         for (int c = 0; c < 8; ++c) {
             const float o2 = __shfl_down_sync(0xffffffffu, v[c], off);
             if (c == 5) v[c] = fminf(v[c], o2);
@@ -68,22 +45,49 @@ __global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
             else v[c] += o2;
         }
     }
-    if ((tid & 31) == 0)
-        for (int c = 0; c < 8; ++c) sh[tid >> 5][c] = (double)v[c];
-    __syncthreads();
-    if (tid == 0) {
-        double d[8];
-        for (int c = 0; c < 8; ++c) d[c] = sh[0][c];
-        for (int w = 1; w < (nthr + 31) / 32; ++w)
-            for (int c = 0; c < 8; ++c) {
-                if (c == 5) d[c] = fmin(d[c], sh[w][c]);
-                else if (c == 6) d[c] = fmax(d[c], sh[w][c]);
-                else d[c] += sh[w][c];
+}
+
+template <int ST, int COLL, bool PER>
+__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
+    fluid_diag_kernel(const StepArgs a, int fields, float* records) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    float v[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 3.0e38f, 0.0f, 0.0f};
+    if (x < a.g.nx && y < a.g.ny) {
+        NodeDiag nd;
+        fluid_node<ST, COLL, PER, true>(a, x, y, z, &nd);
+        if (fields) {
+            const int64_t o = ((int64_t)z * a.g.ny + y) * a.g.nx + x;
+            float e2 = 0.0f;
+            for (int c = 0; c < 3; ++c) {
+                const float ev = __ldg(a.E[c] + o), bv = __ldg(a.Bc[c] + o);
+                e2 += ev * ev + bv * bv;
             }
-        d[4] *= dxcube;
-        if (d[5] >= 3.0e38) d[5] = 1e300;
-        const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        for (int c = 0; c < 8; ++c) partials[8 * b + c] = d[c];
+            v[4] = 0.5f * e2;
+        }
+        const bool fin = isfinite(nd.n) && isfinite(nd.a1) && isfinite(nd.a2) && isfinite(nd.a3);
+        v[0] = nd.n; v[1] = nd.a1; v[2] = nd.a2; v[3] = nd.a3;
+        v[5] = nd.n;
+        v[6] = sqrtf(nd.beta2);
+        v[7] = fin ? 0.0f : 1.0f;
+    }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nwarps = (blockDim.x * blockDim.y) >> 5;
+    __shared__ float sh[8][PWFA_FLUID_MAX_THREADS / 32];
+    diag8_warp(v);
+    if ((tid & 31) == 0)
+        for (int c = 0; c < 8; ++c) sh[c][tid >> 5] = v[c];
+    __syncthreads();
+    if (tid < 32) {
+        for (int c = 0; c < 8; ++c) v[c] = tid < nwarps ? sh[c][tid] : (c == 5 ? 3.0e38f : 0.0f);
+        diag8_warp(v);
+        if (tid == 0) {
+            const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            float4* r = reinterpret_cast<float4*>(records) + 2 * b;
+            r[0] = make_float4(v[0], v[1], v[2], v[3]);
+            r[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
     }
 }
 
@@ -210,11 +214,12 @@ cudaError_t launch_fluid_t(const StepArgs& a, cudaStream_t s, const DiagOut* d) 
     dim3 grid((a.g.nx + bx - 1) / bx, (a.g.ny + by - 1) / by, a.g.nz);
     if (d) {
         if ((int64_t)grid.x * grid.y * grid.z > d->capacity) return cudaErrorInvalidValue;
-        if (a.g.periodic) fluid_diag_kernel<ST, COLL, true><<<grid, block, 0, s>>>(a, d->dxcube, d->partials);
-        else fluid_diag_kernel<ST, COLL, false><<<grid, block, 0, s>>>(a, d->dxcube, d->partials);
+        const int fields = d->nenergy > 0 ? 0 : 1;
+        if (a.g.periodic) fluid_diag_kernel<ST, COLL, true><<<grid, block, 0, s>>>(a, fields, d->records);
+        else fluid_diag_kernel<ST, COLL, false><<<grid, block, 0, s>>>(a, fields, d->records);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        return launch_diag_finish(d->partials, (int64_t)grid.x * grid.y * grid.z, d->out, s);
+        return launch_diag_finish_step(*d, (int64_t)grid.x * grid.y * grid.z, s);
     }
     if (a.g.periodic) fluid_kernel<ST, COLL, true><<<grid, block, 0, s>>>(a);
     else fluid_kernel<ST, COLL, false><<<grid, block, 0, s>>>(a);

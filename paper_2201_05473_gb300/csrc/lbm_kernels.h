@@ -8,11 +8,19 @@
 
 namespace pwfa {
 
-// Where the fused diagnostics of a fluid launch go: one record of 8 doubles
-// per thread block (capacity records), reduced into out[8].
+// Where the fused diagnostics of a step go. The fluid launch writes one FP32
+// record of 8 values per thread block (sum n, sum n p_x, p_y, p_z, field
+// energy / dx^3, min n, max |beta|, non-finite count); when the step's
+// Faraday launch took the field energy (nenergy > 0) it wrote one FP32 value
+// per block to energy and the fluid records carry 0 there. Both are combined
+// in FP64 into out[8] (scratch: kDiagBlocks FP64 records).
 struct DiagOut {
-    double* partials;
+    float* records;
     int64_t capacity;
+    float* energy;
+    int64_t energy_capacity;
+    int64_t nenergy;
+    double* scratch;
     double* out;
     double dxcube;
 };
@@ -23,11 +31,17 @@ struct DiagOut {
 cudaError_t launch_fluid(const StepArgs& a, int storage, int collision, cudaStream_t s,
                          const DiagOut* d = nullptr);
 
-// Reduce nparts diagnostics records into out[8].
-cudaError_t launch_diag_finish(const double* partials, int64_t nparts, double* out, cudaStream_t s);
+// Reduce the nrec fluid records and d.nenergy energy records of a fused step
+// into d.out: up to kDiagBlocks blocks combine contiguous chunks into
+// d.scratch, one block combines those (a single block over the ~2.6e5
+// records of a 512x256x256 grid was latency-bound at ~1 ms).
+cudaError_t launch_diag_finish_step(const DiagOut& d, int64_t nrec, cudaStream_t s);
 
-// Faraday, dB/dt = -curl E: Bn = Bc - dt curl_h E (Yee, Eq. 5).
-cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s);
+// Faraday, dB/dt = -curl E: Bn = Bc - dt curl_h E (Yee, Eq. 5). With energy
+// != NULL each block also writes the field energy (|E|^2 + |Bc|^2)/2 of its
+// nodes, per dx^3, to energy[block] (faraday_blocks(g) records).
+cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s, float* energy = nullptr);
+int64_t faraday_blocks(const Grid& g);
 
 // Ampere, dE/dt = curl B - J: E += dt (curl_h Bn - J_edge - J_b(t_{n+1})).
 cudaError_t launch_ampere(const StepArgs& a, cudaStream_t s);
