@@ -508,9 +508,9 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
         // with diagnostics the Faraday launch also takes the field energy of
         // the entering state (it reads E and B(t_n) anyway)
         float* energy = nullptr;
-        if (diag && faraday_blocks(in.g) <= dg.energy_capacity) {
+        if (diag && faraday_energy_records(in.g) <= dg.energy_capacity) {
             energy = dg.energy;
-            dg.nenergy = faraday_blocks(in.g);
+            dg.nenergy = faraday_energy_records(in.g);
         }
         rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(a, s, energy); });
         if (rc) return rc;
@@ -743,8 +743,8 @@ int ensure_step_diag(pwfa_lbm* h) {
     int64_t need = 1, need_e = 1;
     for (const auto& in : h->inst) {
         const int64_t b = (int64_t)((in.g.nx + in.bx - 1) / in.bx) * ((in.g.ny + in.by - 1) / in.by) * in.g.nz;
-        need = std::max(need, b);
-        need_e = std::max(need_e, faraday_blocks(in.g));
+        need = std::max(need, b * (in.bx * in.by / 32));  // one record per warp
+        need_e = std::max(need_e, faraday_energy_records(in.g));
     }
     if (!h->d_step_diag) {
         if (cudaMalloc(&h->d_step_diag, sizeof(double) * 8 * h->inst.size()) != cudaSuccess ||

@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(kDiagThreads) diag_finish_kernel(const double*
 }
 
 // Block b combines FP32 fluid records [b per, (b + 1) per) and energy
-// records [b per_e, (b + 1) per_e) in FP64 into scratch[b].
+// records [b per_e, (b + 1) per_e) in FP64 into scratch[b]. A fluid record's
+// slot 6 holds min(-|beta|^2) (3e38 when the warp had no node).
 __global__ void __launch_bounds__(kDiagThreads) diag_chunk_kernel(const float* rec, int64_t nrec, int64_t per,
                                                                   const float* en, int64_t nen, int64_t per_e,
                                                                   double dxcube, double* scratch) {
@@ -265,7 +266,8 @@ __global__ void __launch_bounds__(kDiagThreads) diag_chunk_kernel(const float* r
     for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
         const float4 p = reinterpret_cast<const float4*>(rec)[2 * b];
         const float4 q = reinterpret_cast<const float4*>(rec)[2 * b + 1];
-        diag_combine(d, Diag{p.x, p.y, p.z, p.w, q.x, q.y >= 3.0e38f ? 1e300 : (double)q.y, q.z, q.w});
+        diag_combine(d, Diag{p.x, p.y, p.z, p.w, q.x, q.y >= 3.0e38f ? 1e300 : (double)q.y,
+                             sqrt(fmax(0.0, -(double)q.z)), q.w});
     }
     const int64_t e0 = (int64_t)blockIdx.x * per_e;
     const int64_t e1 = e0 + per_e < nen ? e0 + per_e : nen;

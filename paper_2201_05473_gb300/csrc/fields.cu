@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(kBX * kBY) faraday_kernel(const StepArgs a) {
 
 // Faraday with the field energy of its nodes: (|E|^2 + |Bc|^2)/2 at each
 // node's index (the six staggered components stored there), summed in FP32
-// over the block (256 nodes) into energy[block].
+// over each warp (32 nodes) into energy[warp].
 template <bool PER>
 __global__ void __launch_bounds__(kBX * kBY) faraday_energy_kernel(const StepArgs a, float* energy) {
     const int i = blockIdx.x * kBX + threadIdx.x;
@@ -36,14 +36,10 @@ __global__ void __launch_bounds__(kBX * kBY) faraday_energy_kernel(const StepArg
         e2 *= 0.5f;
     }
     for (int off = 16; off > 0; off >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, off);
-    __shared__ float sh[kBX * kBY / 32];
     const int tid = threadIdx.y * kBX + threadIdx.x;
-    if ((tid & 31) == 0) sh[tid >> 5] = e2;
-    __syncthreads();
-    if (tid < 32) {
-        e2 = tid < kBX * kBY / 32 ? sh[tid] : 0.0f;
-        for (int off = 16; off > 0; off >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, off);
-        if (tid == 0) energy[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = e2;
+    if ((tid & 31) == 0) {
+        const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        energy[b * (kBX * kBY / 32) + (tid >> 5)] = e2;
     }
 }
 
@@ -117,8 +113,8 @@ cudaError_t launch_zero_walls(const StepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int64_t faraday_blocks(const Grid& g) {
-    return (int64_t)((g.nx + kBX - 1) / kBX) * ((g.ny + kBY - 1) / kBY) * g.nz;
+int64_t faraday_energy_records(const Grid& g) {
+    return (int64_t)((g.nx + kBX - 1) / kBX) * ((g.ny + kBY - 1) / kBY) * g.nz * (kBX * kBY / 32);
 }
 
 cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s, float* energy) {

@@ -29,22 +29,41 @@ __global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
 }
 
 // The same step with the diagnostics of the entering state fused in: each
-// block writes one FP32 record (sum n, sum n p_k, field energy / dx^3 when
-// fields is set, min n, max |beta|, non-finite count) to records[block];
-// launch_diag_finish_step combines the records in FP64. The block sums run
-// over at most PWFA_FLUID_MAX_THREADS nodes, so FP32 costs them ~1e-7
-// relative; FP64 arithmetic, slow on this part, stays out of this kernel.
-__device__ __forceinline__ void diag8_warp(float (&v)[8]) {
+// warp writes one FP32 record of 8 slots (sum n, sum n p_x, p_y, p_z, field
+// energy / dx^3 when fields is set, min n, min of -|beta|^2, non-finite
+// count) to records[warp]; launch_diag_finish_step combines the records in
+// FP64. A warp's sums run over 32 nodes, so FP32 costs them ~1e-7 relative;
+// FP64 arithmetic, slow on this part, and block barriers stay out of this
+// kernel.
+__device__ __forceinline__ float diag_comb(int slot, float a, float b) {
+    return (slot == 5 || slot == 6) ? fminf(a, b) : a + b;
+}
+
+// Warp reduction of 8 values per lane by recursive halving: at offsets 16, 8
+// and 4 a lane keeps the half of its slots chosen by that lane bit and
+// combines it with the partner's copy (4 + 2 + 1 shuffles), which leaves lane
+// L with slot (L >> 2) & 7 reduced over 8 lanes; offsets 2 and 1 finish it.
+// Nine shuffles instead of the forty of eight separate tree reductions.
+__device__ __forceinline__ float diag8_warp(const float (&v)[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float w[4];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float o2 = __shfl_down_sync(0xffffffffu, v[c], off);
-            if (c == 5) v[c] = fminf(v[c], o2);
-            else if (c == 6) v[c] = fmaxf(v[c], o2);
-            else v[c] += o2;
-        }
+    for (int k = 0; k < 4; ++k) {
+        const float keep = b4 ? v[k + 4] : v[k];
+        const float send = b4 ? v[k] : v[k + 4];
+        w[k] = diag_comb(b4 ? k + 4 : k, keep, __shfl_xor_sync(0xffffffffu, send, 16));
     }
+    float u[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float keep = b3 ? w[j + 2] : w[j];
+        const float send = b3 ? w[j] : w[j + 2];
+        u[j] = diag_comb((b4 ? 4 : 0) + (b3 ? 2 : 0) + j, keep, __shfl_xor_sync(0xffffffffu, send, 8));
+    }
+    const int slot = (lane >> 2) & 7;
+    float s = diag_comb(slot, b2 ? u[1] : u[0], __shfl_xor_sync(0xffffffffu, b2 ? u[0] : u[1], 4));
+    s = diag_comb(slot, s, __shfl_xor_sync(0xffffffffu, s, 2));
+    return diag_comb(slot, s, __shfl_xor_sync(0xffffffffu, s, 1));
 }
 
 template <int ST, int COLL, bool PER>
@@ -53,7 +72,7 @@ __global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    float v[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 3.0e38f, 0.0f, 0.0f};
+    float v[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 3.0e38f, 3.0e38f, 0.0f};
     if (x < a.g.nx && y < a.g.ny) {
         NodeDiag nd;
         fluid_node<ST, COLL, PER, true>(a, x, y, z, &nd);
@@ -69,25 +88,16 @@ __global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
         const bool fin = isfinite(nd.n) && isfinite(nd.a1) && isfinite(nd.a2) && isfinite(nd.a3);
         v[0] = nd.n; v[1] = nd.a1; v[2] = nd.a2; v[3] = nd.a3;
         v[5] = nd.n;
-        v[6] = sqrtf(nd.beta2);
+        v[6] = -nd.beta2;
         v[7] = fin ? 0.0f : 1.0f;
     }
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nwarps = (blockDim.x * blockDim.y) >> 5;
-    __shared__ float sh[8][PWFA_FLUID_MAX_THREADS / 32];
-    diag8_warp(v);
-    if ((tid & 31) == 0)
-        for (int c = 0; c < 8; ++c) sh[c][tid >> 5] = v[c];
-    __syncthreads();
-    if (tid < 32) {
-        for (int c = 0; c < 8; ++c) v[c] = tid < nwarps ? sh[c][tid] : (c == 5 ? 3.0e38f : 0.0f);
-        diag8_warp(v);
-        if (tid == 0) {
-            const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            float4* r = reinterpret_cast<float4*>(records) + 2 * b;
-            r[0] = make_float4(v[0], v[1], v[2], v[3]);
-            r[1] = make_float4(v[4], v[5], v[6], v[7]);
-        }
+    const int lane = tid & 31;
+    const float s = diag8_warp(v, lane);
+    if ((lane & 3) == 0) {
+        const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        const int64_t w = b * ((blockDim.x * blockDim.y) >> 5) + (tid >> 5);
+        records[8 * w + (lane >> 2)] = s;
     }
 }
 
@@ -213,13 +223,14 @@ cudaError_t launch_fluid_t(const StepArgs& a, cudaStream_t s, const DiagOut* d) 
     dim3 block(bx, by, 1);
     dim3 grid((a.g.nx + bx - 1) / bx, (a.g.ny + by - 1) / by, a.g.nz);
     if (d) {
-        if ((int64_t)grid.x * grid.y * grid.z > d->capacity) return cudaErrorInvalidValue;
+        const int64_t nrec = (int64_t)grid.x * grid.y * grid.z * (bx * by / 32);
+        if (nrec > d->capacity) return cudaErrorInvalidValue;
         const int fields = d->nenergy > 0 ? 0 : 1;
         if (a.g.periodic) fluid_diag_kernel<ST, COLL, true><<<grid, block, 0, s>>>(a, fields, d->records);
         else fluid_diag_kernel<ST, COLL, false><<<grid, block, 0, s>>>(a, fields, d->records);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        return launch_diag_finish_step(*d, (int64_t)grid.x * grid.y * grid.z, s);
+        return launch_diag_finish_step(*d, nrec, s);
     }
     if (a.g.periodic) fluid_kernel<ST, COLL, true><<<grid, block, 0, s>>>(a);
     else fluid_kernel<ST, COLL, false><<<grid, block, 0, s>>>(a);

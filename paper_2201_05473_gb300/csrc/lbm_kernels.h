@@ -9,11 +9,11 @@
 namespace pwfa {
 
 // Where the fused diagnostics of a step go. The fluid launch writes one FP32
-// record of 8 values per thread block (sum n, sum n p_x, p_y, p_z, field
-// energy / dx^3, min n, max |beta|, non-finite count); when the step's
-// Faraday launch took the field energy (nenergy > 0) it wrote one FP32 value
-// per block to energy and the fluid records carry 0 there. Both are combined
-// in FP64 into out[8] (scratch: kDiagBlocks FP64 records).
+// record of 8 values per warp (sum n, sum n p_x, p_y, p_z, field energy /
+// dx^3, min n, min -|beta|^2, non-finite count); when the step's Faraday
+// launch took the field energy (nenergy > 0) it wrote one FP32 value per warp
+// to energy and the fluid records carry 0 there. Both are combined in FP64
+// into out[8] (scratch: kDiagBlocks FP64 records).
 struct DiagOut {
     float* records;
     int64_t capacity;
@@ -38,10 +38,10 @@ cudaError_t launch_fluid(const StepArgs& a, int storage, int collision, cudaStre
 cudaError_t launch_diag_finish_step(const DiagOut& d, int64_t nrec, cudaStream_t s);
 
 // Faraday, dB/dt = -curl E: Bn = Bc - dt curl_h E (Yee, Eq. 5). With energy
-// != NULL each block also writes the field energy (|E|^2 + |Bc|^2)/2 of its
-// nodes, per dx^3, to energy[block] (faraday_blocks(g) records).
+// != NULL each warp also writes the field energy (|E|^2 + |Bc|^2)/2 of its
+// nodes, per dx^3, to energy[warp] (faraday_energy_records(g) records).
 cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s, float* energy = nullptr);
-int64_t faraday_blocks(const Grid& g);
+int64_t faraday_energy_records(const Grid& g);
 
 // Ampere, dE/dt = curl B - J: E += dt (curl_h Bn - J_edge - J_b(t_{n+1})).
 cudaError_t launch_ampere(const StepArgs& a, cudaStream_t s);

@@ -214,14 +214,14 @@ def test_production_grid_properties():
         assert nmx < 1e-5 and nmy < 1e-5, (nmx, nmy)
 
 
-# The fused diagnostics sum each thread block's nodes (<= 256) by a pairwise
-# FP32 shuffle tree, then combine the block sums in FP64. A pairwise FP32 sum
-# of 2^8 non-negative terms is within 8 u = 4.8e-7 of the exact sum (u = 2^-24),
-# so the positive totals (sum n, field energy) sit within 5e-7 relative (the
-# separate reduction sums 32-node FP32 partials: a tighter bound). The signed
-# momentum sums cancel, so their worst-case bound (5e-7 of the sum of
-# magnitudes) says little; rounding errors of random sign over ~2e4 nodes
-# stay two orders below the 1e-6 max(|ref|, 1) checked.
+# The fused diagnostics sum each warp's 32 nodes by a pairwise FP32 shuffle
+# tree, then combine the warp sums in FP64. A pairwise FP32 sum of 2^5
+# non-negative terms is within 5 u = 3.0e-7 of the exact sum (u = 2^-24), so
+# the positive totals (sum n, field energy) sit within 5e-7 relative (the
+# separate reduction also sums 32-node FP32 partials). The signed momentum
+# sums cancel, so their worst-case bound (3e-7 of the sum of magnitudes)
+# says little; rounding errors of random sign over ~2e4 nodes stay two orders
+# below the 1e-6 max(|ref|, 1) checked.
 FUSED_REL = 5e-7
 
 
