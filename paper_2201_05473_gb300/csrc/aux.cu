@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(kBX * kBY) export_f_kernel(const StepArgs a, f
     bool bnd;
     gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
     if (!PER && bnd) {
-        float A[kL], nn, beta[3], phi[kQ];
-        node_moments(f, a.n_floor, A, nn, beta);
+        float A[kL], inn, beta[3], phi[kQ];
+        node_moments(f, a.n_floor, A, inn, beta);
         const float u[3] = {beta[0] * a.lat, beta[1] * a.lat, beta[2] * a.lat};
         eq_factors(u, phi);
         for (int l = 0; l < kL; ++l)
@@ -121,8 +121,8 @@ __global__ void __launch_bounds__(kBX * kBY) export_fields_kernel(const StepArgs
         float f[kL][kQ];
         bool bnd;
         gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
-        float A[kL], nn, beta[3];
-        node_moments(f, a.n_floor, A, nn, beta);
+        float A[kL], inn, beta[3];
+        node_moments(f, a.n_floor, A, inn, beta);
         vals[0] = A[0];
         vals[1] = beta[0]; vals[2] = beta[1]; vals[3] = beta[2];
         vals[13] = A[1]; vals[14] = A[2]; vals[15] = A[3];
@@ -164,8 +164,8 @@ __global__ void linecut_kernel(const StepArgs a, double xr, float* out) {
         float f[kL][kQ];
         bool bnd;
         gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
-        float A[kL], nn, beta[3];
-        node_moments(f, a.n_floor, A, nn, beta);
+        float A[kL], inn, beta[3];
+        node_moments(f, a.n_floor, A, inn, beta);
         float e[3];
         node_E<PER>(g, a.E, x, y, z, e);
         nsum += wgt * A[0];
@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const StepArgs a, do
         float f[kL][kQ];
         bool bnd;
         gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
-        float A[kL], nn, beta[3];
-        node_moments(f, a.n_floor, A, nn, beta);
+        float A[kL], inn, beta[3];
+        node_moments(f, a.n_floor, A, inn, beta);
         const bool fin = isfinite(A[0]) && isfinite(A[1]) && isfinite(A[2]) && isfinite(A[3]);
         d.bad += fin ? 0.0 : 1.0;
         d.sn += A[0]; d.s1 += A[1]; d.s2 += A[2]; d.s3 += A[3];

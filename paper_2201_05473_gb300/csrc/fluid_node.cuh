@@ -31,8 +31,8 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
     const Grid& g = a.g;
     const uint32_t node = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x;
 
-    float A[kL], nn, beta[3];
-    node_moments(f, a.n_floor, A, nn, beta);
+    float A[kL], inn, beta[3];
+    node_moments(f, a.n_floor, A, inn, beta);
     const float n = A[0];
     if (DIAG) {
         nd->n = A[0];
@@ -96,17 +96,23 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
                     if (xi_y(q) > 0) m1 += f[l][q]; else if (xi_y(q) < 0) m1 -= f[l][q];
                     if (xi_z(q) > 0) m2 += f[l][q]; else if (xi_z(q) < 0) m2 -= f[l][q];
                 }
+                // w_i (xi_i . P + F dt) with the two weights of the moving
+                // directions (1/18 axis, 1/36 diagonal) folded into P and F:
+                // f = A phi_i + one or two adds of +-P_k w + F w.
                 const float k3 = 3.0f * (1.0f - om);
-                const float P0 = k3 * (m0 - A[l] * u[0]);
-                const float P1 = k3 * (m1 - A[l] * u[1]);
-                const float P2 = k3 * (m2 - A[l] * u[2]);
+                const float P[3] = {k3 * (m0 - A[l] * u[0]), k3 * (m1 - A[l] * u[1]), k3 * (m2 - A[l] * u[2])};
+                const float Pa[3] = {P[0] * (1.0f / 18.0f), P[1] * (1.0f / 18.0f), P[2] * (1.0f / 18.0f)};
+                const float Pd[3] = {P[0] * (1.0f / 36.0f), P[1] * (1.0f / 36.0f), P[2] * (1.0f / 36.0f)};
+                const float Fa = Fl * (1.0f / 18.0f), Fd = Fl * (1.0f / 36.0f);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
-                    float xp = 0.0f;
-                    if (xi_x(q)) xp += (float)xi_x(q) * P0;
-                    if (xi_y(q)) xp += (float)xi_y(q) * P1;
-                    if (xi_z(q)) xp += (float)xi_z(q) * P2;
-                    f[l][q] = A[l] * phi[q] + wq(q) * (xp + Fl);
+                    const int nz = (xi_x(q) != 0) + (xi_y(q) != 0) + (xi_z(q) != 0);
+                    const float* Pw = nz == 2 ? Pd : Pa;
+                    float s = nz == 0 ? Fl * (1.0f / 3.0f) : (nz == 2 ? Fd : Fa);
+                    if (xi_x(q) > 0) s += Pw[0]; else if (xi_x(q) < 0) s -= Pw[0];
+                    if (xi_y(q) > 0) s += Pw[1]; else if (xi_y(q) < 0) s -= Pw[1];
+                    if (xi_z(q) > 0) s += Pw[2]; else if (xi_z(q) < 0) s -= Pw[2];
+                    f[l][q] = fmaf(A[l], phi[q], s);
                 }
             }
             // (stream only: f* = f)
@@ -123,13 +129,13 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
     }
 
     // Node current for Ampere: J = -n beta(p*), p* = (A_k + F_k dt) / nn.
-    const float ps0 = (A[1] + F[0] * a.dt) / nn;
-    const float ps1 = (A[2] + F[1] * a.dt) / nn;
-    const float ps2 = (A[3] + F[2] * a.dt) / nn;
-    const float gs = sqrtf(1.0f + ps0 * ps0 + ps1 * ps1 + ps2 * ps2);
-    __stcs(a.J[0] + node, -n * ps0 / gs);
-    __stcs(a.J[1] + node, -n * ps1 / gs);
-    __stcs(a.J[2] + node, -n * ps2 / gs);
+    const float ps0 = (A[1] + F[0] * a.dt) * inn;
+    const float ps1 = (A[2] + F[1] * a.dt) * inn;
+    const float ps2 = (A[3] + F[2] * a.dt) * inn;
+    const float ngs = -n * rsqrtf(1.0f + ps0 * ps0 + ps1 * ps1 + ps2 * ps2);
+    __stcs(a.J[0] + node, ngs * ps0);
+    __stcs(a.J[1] + node, ngs * ps1);
+    __stcs(a.J[2] + node, ngs * ps2);
 }
 
 template <int ST, int COLL, bool PER, bool DIAG = false>
