@@ -271,10 +271,11 @@ int pwfa_lbm_set_launch(pwfa_lbm_t* h, int32_t instance, int32_t bx, int32_t by)
 int pwfa_lbm_get_launch(pwfa_lbm_t* h, int32_t instance, int32_t* bx, int32_t* by);
 
 /* Fluid kernel variants. DIRECT: one thread per node, the 76 pulled values
- * loaded straight into registers. STAGED (FP32 storage only): persistent
- * 128-thread tiles, software pipelined: each thread's 76 values of its next
- * tile arrive in shared memory by cp.async while it computes the current
- * node; needs bx * by = 128. */
+ * loaded straight into registers. STAGED: persistent 128-thread tiles,
+ * software pipelined: each thread's pulled values of its next tile (76 FP32
+ * words, or 38 words of 16-bit lattice pairs) arrive in shared memory by
+ * cp.async while it computes the current node; needs bx * by = 128 (other
+ * shapes run the direct kernel). */
 #define PWFA_FLUID_DIRECT 0
 #define PWFA_FLUID_STAGED 1
 int pwfa_lbm_set_fluid_variant(pwfa_lbm_t* h, int32_t instance, int32_t variant);

@@ -196,7 +196,7 @@ StepArgs make_args(const Instance& in) {
     a.dx = (float)p.dx;
     a.bx = in.bx;
     a.by = in.by;
-    a.staged = in.variant == PWFA_FLUID_STAGED && in.p.storage == PWFA_F32 && in.bx * in.by == 128;
+    a.staged = in.variant == PWFA_FLUID_STAGED && in.bx * in.by == 128;
     for (int c = 0; c < 3; ++c) a.Jb[c] = in.Jb[c];
     return a;
 }
@@ -1110,8 +1110,6 @@ int pwfa_lbm_set_fluid_variant(pwfa_lbm_t* h, int32_t instance, int32_t variant)
     int rc = check_instance(h, instance);
     if (rc) return rc;
     if (variant != PWFA_FLUID_DIRECT && variant != PWFA_FLUID_STAGED) return fail(PWFA_ERR_PARAM, "unknown variant");
-    if (variant == PWFA_FLUID_STAGED && h->inst[instance].p.storage != PWFA_F32)
-        return fail(PWFA_ERR_PARAM, "the staged fluid kernel needs FP32 storage");
     h->inst[instance].variant = variant;
     h->batch_valid = false;
     return PWFA_OK;
@@ -1153,7 +1151,6 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
         for (int ci = 0; ci < ncand; ++ci) {
             const int* c = batched ? cand_batch[ci] : cand_all[ci];
             if (c[0] > 2 * in.g.nx && c[0] > 32) continue;  // mostly idle lanes
-            if (c[2] == PWFA_FLUID_STAGED && in.p.storage != PWFA_F32) continue;
             in.bx = c[0];
             in.by = c[1];
             in.variant = c[2];

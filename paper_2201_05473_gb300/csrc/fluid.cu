@@ -102,13 +102,16 @@ __global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
 }
 
 // ---------------------------------------------------------------- staged
-// Software-pipelined variant (FP32 storage): persistent CTAs of 128 threads
-// walk the node tiles; while a thread computes its node of tile k from
-// registers, the 76 pulled populations of its node of tile k+1 are already
-// in flight into its own column of shared memory through 4-byte cp.async
-// copies. A thread reads back only the values it copied itself, so the only
-// wait is cp.async.wait_group on its own copies (no barrier, no spin).
+// Software-pipelined variant: persistent CTAs of 128 threads walk the node
+// tiles; while a thread computes its node of tile k from registers, the
+// pulled populations of its node of tile k+1 are already in flight into its
+// own column of shared memory through 4-byte cp.async copies (76 values in
+// FP32, 38 words of lattice pairs in the 16-bit forms). A thread reads back
+// only the words it copied itself, so the only wait is cp.async.wait_group
+// on its own copies (no barrier, no spin).
 constexpr int kStageThreads = 128;
+template <int ST>
+constexpr int stage_words() { return ST == 0 ? kPop : kPop / 2; }
 
 __device__ __forceinline__ void cp_async4(uint32_t smem, const void* g) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem), "l"(g) : "memory");
@@ -135,7 +138,9 @@ __device__ __forceinline__ TileNode tile_node(const StepArgs& a, int64_t tile, i
     return n;
 }
 
-template <bool PER>
+// Word (l, q) of a thread's column: FP32 word l * 19 + q is f_l,q; 16-bit
+// word p * 19 + q holds lattices 2p and 2p + 1 of direction q.
+template <int ST, bool PER>
 __device__ __forceinline__ void stage_copies(const StepArgs& a, const TileNode& n, uint32_t col) {
     const Grid& g = a.g;
     int xs = n.x, ys = n.y, zs = n.z;
@@ -144,51 +149,67 @@ __device__ __forceinline__ void stage_copies(const StepArgs& a, const TileNode& 
         ys = min(max(n.y, 1), g.ny - 2);
         zs = min(max(n.z, 1), g.nz - 2);
     }
-    const float* fin = static_cast<const float*>(a.fin);
+    using T = typename Codec<ST>::T;
+    const T* fin = static_cast<const T*>(a.fin);
     const int64_t LS = lattice_stride(g);
-    const float* fl[kL] = {fin, fin + LS, fin + 2 * LS, fin + 3 * LS};
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
         const uint32_t off = pop_off(q, (uint32_t)src_index<PER>(g, xs, ys, zs, q));
+        if constexpr (ST == 0) {
 #pragma unroll
-        for (int l = 0; l < kL; ++l)
-            cp_async4(col + 4u * (uint32_t)((l * kQ + q) * kStageThreads), fl[l] + off);
+            for (int l = 0; l < kL; ++l)
+                cp_async4(col + 4u * (uint32_t)((l * kQ + q) * kStageThreads), fin + l * LS + off);
+        } else {
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+                cp_async4(col + 4u * (uint32_t)((p * kQ + q) * kStageThreads), fin + 2 * p * LS + 2 * off);
+        }
     }
 }
 
-template <int COLL, bool PER>
+template <int ST, int COLL, bool PER>
 __global__ void __launch_bounds__(kStageThreads, 4) fluid_staged_kernel(const StepArgs a, int tiles_x, int tiles_y,
                                                                          int64_t ntiles) {
-    extern __shared__ float stage[];  // [76][kStageThreads]
+    extern __shared__ uint32_t stage[];  // [stage_words<ST>()][kStageThreads]
     const uint32_t col = (uint32_t)__cvta_generic_to_shared(stage + threadIdx.x);
     int64_t tile = blockIdx.x;
     TileNode cur = tile_node(a, tile, tiles_x, tiles_y);
-    if (tile < ntiles && cur.valid) stage_copies<PER>(a, cur, col);
+    if (tile < ntiles && cur.valid) stage_copies<ST, PER>(a, cur, col);
     cp_async_commit();
     while (tile < ntiles) {
         cp_async_wait_all();
         float f[kL][kQ];
+        if constexpr (ST == 0) {
 #pragma unroll
-        for (int l = 0; l < kL; ++l)
+            for (int l = 0; l < kL; ++l)
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) f[l][q] = stage[(l * kQ + q) * kStageThreads + threadIdx.x];
+                for (int q = 0; q < kQ; ++q)
+                    f[l][q] = __uint_as_float(stage[(l * kQ + q) * kStageThreads + threadIdx.x]);
+        } else {
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int q = 0; q < kQ; ++q)
+                    Codec<ST>::from_word(stage[(p * kQ + q) * kStageThreads + threadIdx.x], 2 * p, q, a.n0,
+                                         f[2 * p][q], f[2 * p + 1][q]);
+        }
         const int64_t nxt = tile + gridDim.x;
         const TileNode nn = tile_node(a, nxt, tiles_x, tiles_y);
-        if (nxt < ntiles && nn.valid) stage_copies<PER>(a, nn, col);
+        if (nxt < ntiles && nn.valid) stage_copies<ST, PER>(a, nn, col);
         cp_async_commit();
         if (cur.valid) {
             bool bnd = false;
             if (!PER)
                 bnd = cur.x == 0 || cur.y == 0 || cur.z == 0 || cur.x == a.g.nx - 1 || cur.y == a.g.ny - 1 ||
                       cur.z == a.g.nz - 1;
-            fluid_compute<0, COLL, PER>(a, cur.x, cur.y, cur.z, f, bnd);
+            fluid_compute<ST, COLL, PER>(a, cur.x, cur.y, cur.z, f, bnd);
         }
         tile = nxt;
         cur = nn;
     }
 }
 
-template <int COLL>
+template <int ST, int COLL>
 cudaError_t launch_staged_t(const StepArgs& a, cudaStream_t s) {
     const int bx = a.bx;
     if (bx <= 0 || kStageThreads % bx) return cudaErrorInvalidConfiguration;
@@ -197,27 +218,31 @@ cudaError_t launch_staged_t(const StepArgs& a, cudaStream_t s) {
     const int64_t ntiles = (int64_t)tiles_x * tiles_y * a.g.nz;
     static int grid_cache[2] = {0, 0};
     int& grid = grid_cache[a.g.periodic ? 1 : 0];
-    const size_t smem = sizeof(float) * kPop * kStageThreads;
+    const size_t smem = sizeof(uint32_t) * stage_words<ST>() * kStageThreads;
     if (grid == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaError_t e = a.g.periodic
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_staged_kernel<COLL, true>, kStageThreads, smem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_staged_kernel<COLL, false>, kStageThreads, smem);
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_staged_kernel<ST, COLL, true>, kStageThreads,
+                                                            smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fluid_staged_kernel<ST, COLL, false>, kStageThreads,
+                                                            smem);
         if (e != cudaSuccess) return e;
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     const int blocks = (int)std::min<int64_t>(grid, ntiles);
-    if (a.g.periodic) fluid_staged_kernel<COLL, true><<<blocks, kStageThreads, smem, s>>>(a, tiles_x, tiles_y, ntiles);
-    else fluid_staged_kernel<COLL, false><<<blocks, kStageThreads, smem, s>>>(a, tiles_x, tiles_y, ntiles);
+    if (a.g.periodic)
+        fluid_staged_kernel<ST, COLL, true><<<blocks, kStageThreads, smem, s>>>(a, tiles_x, tiles_y, ntiles);
+    else
+        fluid_staged_kernel<ST, COLL, false><<<blocks, kStageThreads, smem, s>>>(a, tiles_x, tiles_y, ntiles);
     return cudaGetLastError();
 }
 
 template <int ST, int COLL>
 cudaError_t launch_fluid_t(const StepArgs& a, cudaStream_t s, const DiagOut* d) {
     // (a window-moving step pulls one plane up: direct kernel)
-    if (ST == 0 && a.staged && !d && a.src_shift == 0) return launch_staged_t<COLL>(a, s);
+    if (a.staged && !d && a.src_shift == 0) return launch_staged_t<ST, COLL>(a, s);
     const int bx = a.bx, by = a.by;
     if (bx * by > PWFA_FLUID_MAX_THREADS || bx <= 0 || by <= 0 || (bx * by) % 32) return cudaErrorInvalidConfiguration;
     dim3 block(bx, by, 1);

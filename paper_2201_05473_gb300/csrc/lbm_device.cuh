@@ -65,10 +65,13 @@ template <> struct Codec<1> {
     static __device__ __forceinline__ void store(T* p, float v, int l, int q, float n0) {
         *p = __float2bfloat16_rn(v - dev_base(l, q, n0));
     }
-    static __device__ __forceinline__ void load2(const T* p, int l0, int q, float n0, float& v0, float& v1) {
-        const float2 w = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+    static __device__ __forceinline__ void from_word(uint32_t u, int l0, int q, float n0, float& v0, float& v1) {
+        const float2 w = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
         v0 = w.x + dev_base(l0, q, n0);
         v1 = w.y + dev_base(l0 + 1, q, n0);
+    }
+    static __device__ __forceinline__ void load2(const T* p, int l0, int q, float n0, float& v0, float& v1) {
+        from_word(__ldg(reinterpret_cast<const unsigned int*>(p)), l0, q, n0, v0, v1);
     }
     static __device__ __forceinline__ void store2(T* p, float v0, float v1, int l0, int q, float n0) {
         *reinterpret_cast<__nv_bfloat162*>(p) =
@@ -83,10 +86,13 @@ template <> struct Codec<2> {
     static __device__ __forceinline__ void store(T* p, float v, int l, int q, float n0) {
         *p = __float2half_rn((v - dev_base(l, q, n0)) * (kF16Scale / wq(q)));
     }
-    static __device__ __forceinline__ void load2(const T* p, int l0, int q, float n0, float& v0, float& v1) {
-        const float2 w = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+    static __device__ __forceinline__ void from_word(uint32_t u, int l0, int q, float n0, float& v0, float& v1) {
+        const float2 w = __half22float2(*reinterpret_cast<const __half2*>(&u));
         v0 = w.x * (wq(q) / kF16Scale) + dev_base(l0, q, n0);
         v1 = w.y * (wq(q) / kF16Scale) + dev_base(l0 + 1, q, n0);
+    }
+    static __device__ __forceinline__ void load2(const T* p, int l0, int q, float n0, float& v0, float& v1) {
+        from_word(__ldg(reinterpret_cast<const unsigned int*>(p)), l0, q, n0, v0, v1);
     }
     static __device__ __forceinline__ void store2(T* p, float v0, float v1, int l0, int q, float n0) {
         *reinterpret_cast<__half2*>(p) = __floats2half2_rn((v0 - dev_base(l0, q, n0)) * (kF16Scale / wq(q)),
