@@ -125,10 +125,11 @@ __global__ void __launch_bounds__(kBR * kBZ) fluid_kernel(const Args a) {
     }
     if (!out) return;
     const int64_t o = (int64_t)k * a.nr + j;
-    const float nn = A[0] > a.n_floor ? A[0] : a.n_floor;
-    const float pz = A[1] / nn, pr = A[2] / nn;
-    const float gam = sqrtf(1.0f + pz * pz + pr * pr);
-    const float bz = pz / gam, br = pr / gam;
+    // one division and one reciprocal square root (p = A_k / n, beta = p / gamma)
+    const float inn = 1.0f / (A[0] > a.n_floor ? A[0] : a.n_floor);
+    const float pz = A[1] * inn, pr = A[2] * inn;
+    const float ig = rsqrtf(1.0f + pz * pz + pr * pr);
+    const float bz = pz * ig, br = pr * ig;
     const float uz = bz * a.lat, ur = br * a.lat;
     // equilibrium factors shared by the three lattices: f^eq_l,i = A_l phi_i
     float phi[kQ];
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kBR * kBZ) fluid_kernel(const Args a) {
             for (int dk = -1; dk <= 0; ++dk)
 #pragma unroll
                 for (int dj = -1; dj <= 0; ++dj) bs += yee(a.Bt, a, k + dk, j + dj) + faraday_bt(a, k + dk, j + dj);
-            const float bt = bs / 8.0f;
+            const float bt = bs * 0.125f;
             // F_z = -n (E_z + beta_r B_theta), F_r = -n (E_r - beta_z B_theta)
             S[1] = -A[0] * (ez + br * bt);
             S[2] = -A[0] * (er - bz * bt);
@@ -179,22 +180,27 @@ __global__ void __launch_bounds__(kBR * kBZ) fluid_kernel(const Args a) {
     }
     // collide and store (row 1 also writes its mirror image into the axis row)
     const int64_t om = (int64_t)k * a.nr;  // axis row node of this column
+    const float omc = 1.0f - a.omega;
 #pragma unroll
     for (int l = 0; l < kL; ++l) {
         float* fo = a.fout + (int64_t)l * kQ * a.Np;
         const float sg = l == 2 ? -1.0f : 1.0f;
+        // f* = (1 - omega) f + omega A phi_i + w_i S dt, the weights applied
+        // once per lattice
+        const float oA = a.omega * A[l], sdt = S[l] * a.dt;
+        const float sw[3] = {sdt * w9(0), sdt * w9(1), sdt * w9(5)};
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             float fs = f[l][q];
-            if (a.collision != 2) fs = fs - a.omega * (fs - A[l] * phi[q]) + w9(q) * S[l] * a.dt;
+            if (a.collision != 2) fs = fmaf(fs, omc, fmaf(oA, phi[q], sw[q == 0 ? 0 : (q <= 4 ? 1 : 2)]));
             fo[(int64_t)q * a.Np + o] = fs;
             if (j == 1) fo[(int64_t)rrefl(q) * a.Np + om] = sg * fs;
         }
     }
-    const float nsn = nst > a.n_floor ? nst : a.n_floor;
-    const float qz = pzs / nsn, qr = prs / nsn;
-    const float gs = sqrtf(1.0f + qz * qz + qr * qr);
-    const float jz = -nst * qz / gs, jr = -nst * qr / gs;
+    const float insn = 1.0f / (nst > a.n_floor ? nst : a.n_floor);
+    const float qz = pzs * insn, qr = prs * insn;
+    const float ngs = -nst * rsqrtf(1.0f + qz * qz + qr * qr);
+    const float jz = ngs * qz, jr = ngs * qr;
     if (a.couple) a.Btn[o] = faraday_bt(a, k, j);
     a.Jz[o] = jz;
     a.Jr[o] = jr;
