@@ -42,8 +42,7 @@ __device__ __forceinline__ bool act_B(const Grid& g, int c, int i, int j, int k)
     return i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2;
 }
 
-// Read a[c] at (i,j,k): wraps on periodic grids; on open grids zero outside
-// the grid and, when mask_e / mask_b, at inactive Yee components.
+// Read a at (i,j,k): wraps on periodic grids; zero outside an open grid.
 template <bool PER>
 __device__ __forceinline__ float rd(const Grid& g, const float* a, int i, int j, int k) {
     if (PER) {
@@ -53,45 +52,89 @@ __device__ __forceinline__ float rd(const Grid& g, const float* a, int i, int j,
     }
     return a[((int64_t)k * g.ny + j) * g.nx + i];
 }
-template <bool PER>
-__device__ __forceinline__ float rdE(const Grid& g, const float* a, int c, int i, int j, int k) {
-    if (!PER && (!in_grid(g, i, j, k) || !act_E(g, c, i, j, k))) return 0.0f;
-    return rd<PER>(g, a, i, j, k);
+// Open-grid neighbours of node o for the field adjoints: the index offsets
+// of the +-1 neighbours on each axis (0 where the neighbour lies outside the
+// grid, so that every load stays valid and can be issued at once) and the
+// matching in-grid flags that mask the loaded values.
+struct Nbr {
+    int64_t pi, pj, pk, mi, mj, mk;
+    bool ip, jp, kp, im, jm, km;
+};
+__device__ __forceinline__ Nbr nbr_of(const Grid& g, int i, int j, int k) {
+    Nbr n;
+    n.ip = i + 1 < g.nx; n.jp = j + 1 < g.ny; n.kp = k + 1 < g.nz;
+    n.im = i > 0; n.jm = j > 0; n.km = k > 0;
+    const int64_t sx = g.nx, sxy = (int64_t)g.nx * g.ny;
+    n.pi = n.ip ? 1 : 0; n.pj = n.jp ? sx : 0; n.pk = n.kp ? sxy : 0;
+    n.mi = n.im ? 1 : 0; n.mj = n.jm ? sx : 0; n.mk = n.km ? sxy : 0;
+    return n;
 }
+__device__ __forceinline__ float msk(bool ok, float v) { return ok ? v : 0.0f; }
 
 // ------------------------------------------------------------------- R1
+// Every load of a node is issued before any is used; the driver-gradient
+// terms are formed and summed over the warp in FP32 (FP64 arithmetic is slow
+// on this part) and each warp adds its three sums to an FP64 slot (no block
+// barrier). On open grids E_bar is zero at every inactive component (the
+// seed is masked before the sweep, R4 writes zeros there), so a neighbour
+// read needs only its grid bound: past the upper walls the clamped index
+// lands on an inactive component, below the lower ones the bound masks it.
 template <bool PER>
 __global__ void __launch_bounds__(kBX * kBY) adj_ampere_kernel(const AdjArgs a) {
     const Grid& g = a.f.g;
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
     const int k = blockIdx.z;
-    double g3[3] = {0.0, 0.0, 0.0};
+    float g3[3] = {0.0f, 0.0f, 0.0f};
     if (i < g.nx && j < g.ny) {
         const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
         const float c = a.f.cdt, dt = a.f.dt;
         const float* Ex = a.Ebar[0];
         const float* Ey = a.Ebar[1];
         const float* Ez = a.Ebar[2];
-        const float ex = rdE<PER>(g, Ex, 0, i, j, k);
-        const float ey = rdE<PER>(g, Ey, 1, i, j, k);
-        const float ez = rdE<PER>(g, Ez, 2, i, j, k);
-        float bx = 0.0f, by = 0.0f, bz = 0.0f;
-        if (PER || act_B(g, 0, i, j, k))
-            bx = a.Bbar[0][o] + c * (ey - rdE<PER>(g, Ey, 1, i, j, k + 1) - ez + rdE<PER>(g, Ez, 2, i, j + 1, k));
-        if (PER || act_B(g, 1, i, j, k))
-            by = a.Bbar[1][o] + c * (-ex + rdE<PER>(g, Ex, 0, i, j, k + 1) + ez - rdE<PER>(g, Ez, 2, i + 1, j, k));
-        if (PER || act_B(g, 2, i, j, k))
-            bz = a.Bbar[2][o] + c * (ex - rdE<PER>(g, Ex, 0, i, j + 1, k) - ey + rdE<PER>(g, Ey, 1, i + 1, j, k));
-        a.Bnp[0][o] = bx;
-        a.Bnp[1][o] = by;
-        a.Bnp[2][o] = bz;
-        a.Jbar[0][o] = -0.5f * dt * (ex + rdE<PER>(g, Ex, 0, i - 1, j, k));
-        a.Jbar[1][o] = -0.5f * dt * (ey + rdE<PER>(g, Ey, 1, i, j - 1, k));
-        a.Jbar[2][o] = -0.5f * dt * (ez + rdE<PER>(g, Ez, 2, i, j, k - 1));
-        // driver: E_z += dt alpha gauss  =>  d/d(alpha, sigma_r, sigma_z).
-        // The node term is the derivative of the forward's FP32 Gaussian,
-        // evaluated the same way; only the sum over nodes is FP64.
+        float ex, ey, ez, ey_k, ez_j, ex_k, ez_i, ex_j, ey_i, ex_m, ey_m, ez_m;
+        if (PER) {
+            ex = rd<true>(g, Ex, i, j, k);
+            ey = rd<true>(g, Ey, i, j, k);
+            ez = rd<true>(g, Ez, i, j, k);
+            ey_k = rd<true>(g, Ey, i, j, k + 1);
+            ez_j = rd<true>(g, Ez, i, j + 1, k);
+            ex_k = rd<true>(g, Ex, i, j, k + 1);
+            ez_i = rd<true>(g, Ez, i + 1, j, k);
+            ex_j = rd<true>(g, Ex, i, j + 1, k);
+            ey_i = rd<true>(g, Ey, i + 1, j, k);
+            ex_m = rd<true>(g, Ex, i - 1, j, k);
+            ey_m = rd<true>(g, Ey, i, j - 1, k);
+            ez_m = rd<true>(g, Ez, i, j, k - 1);
+        } else {
+            const Nbr n = nbr_of(g, i, j, k);
+            ex = Ex[o];
+            ey = Ey[o];
+            ez = Ez[o];
+            const float v0 = Ey[o + n.pk], v1 = Ez[o + n.pj], v2 = Ex[o + n.pk], v3 = Ez[o + n.pi], v4 = Ex[o + n.pj],
+                        v5 = Ey[o + n.pi], v6 = Ex[o - n.mi], v7 = Ey[o - n.mj], v8 = Ez[o - n.mk];
+            ey_k = msk(n.kp, v0);
+            ez_j = msk(n.jp, v1);
+            ex_k = msk(n.kp, v2);
+            ez_i = msk(n.ip, v3);
+            ex_j = msk(n.jp, v4);
+            ey_i = msk(n.ip, v5);
+            ex_m = msk(n.im, v6);
+            ey_m = msk(n.jm, v7);
+            ez_m = msk(n.km, v8);
+        }
+        const float b0 = a.Bbar[0][o], b1 = a.Bbar[1][o], b2 = a.Bbar[2][o];
+        const bool cx = PER || act_B(g, 0, i, j, k);
+        const bool cy = PER || act_B(g, 1, i, j, k);
+        const bool cz = PER || act_B(g, 2, i, j, k);
+        a.Bnp[0][o] = cx ? b0 + c * (ey - ey_k - ez + ez_j) : 0.0f;
+        a.Bnp[1][o] = cy ? b1 + c * (-ex + ex_k + ez - ez_i) : 0.0f;
+        a.Bnp[2][o] = cz ? b2 + c * (ex - ex_j - ey + ey_i) : 0.0f;
+        a.Jbar[0][o] = -0.5f * dt * (ex + ex_m);
+        a.Jbar[1][o] = -0.5f * dt * (ey + ey_m);
+        a.Jbar[2][o] = -0.5f * dt * (ez + ez_m);
+        // driver: E_z += dt alpha gauss  =>  d/d(alpha, sigma_r, sigma_z),
+        // the derivative of the forward's FP32 Gaussian evaluated the same way
         if (ez != 0.0f) {
             const float xr = ((float)i - 0.5f * (float)(g.nx - 1)) * a.f.dx;
             const float yr = ((float)j - 0.5f * (float)(g.ny - 1)) * a.f.dx;
@@ -99,24 +142,35 @@ __global__ void __launch_bounds__(kBX * kBY) adj_ampere_kernel(const AdjArgs a) 
             const float r2 = xr * xr + yr * yr;
             const float ga = expf(-r2 * a.f.inv2sr2 - zeta * zeta * a.f.inv2sz2);
             const float w = dt * ez * ga;
-            g3[0] = (double)w;
-            g3[1] = (double)(w * (a.f.alpha / (a.sr * a.sr * a.sr)) * r2);
-            g3[2] = (double)(w * (a.f.alpha / (a.sz * a.sz * a.sz)) * (zeta * zeta));
+            g3[0] = w;
+            g3[1] = w * a.csr * r2;
+            g3[2] = w * a.csz * (zeta * zeta);
         }
     }
-    // block reduction of the three driver partials, one FP64 atomic each
-    __shared__ double sh[3][kBX * kBY / 32];
     for (int c3 = 0; c3 < 3; ++c3)
         for (int off = 16; off > 0; off >>= 1) g3[c3] += __shfl_down_sync(0xffffffffu, g3[c3], off);
     const int t = threadIdx.y * kBX + threadIdx.x;
-    if ((t & 31) == 0)
-        for (int c3 = 0; c3 < 3; ++c3) sh[c3][t >> 5] = g3[c3];
-    __syncthreads();
-    if (t < 3) {
-        double s = 0.0;
-        for (int w = 0; w < kBX * kBY / 32; ++w) s += sh[t][w];
-        if (s != 0.0) atomicAdd(a.grad + t, s);
+    if ((t & 31) == 0 && (g3[0] != 0.0f || g3[1] != 0.0f || g3[2] != 0.0f)) {
+        const uint32_t w = ((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (kBX * kBY / 32) +
+                           (uint32_t)(t >> 5);
+        double* slot = a.gslots + 3 * (w % kGradSlots);
+        for (int c3 = 0; c3 < 3; ++c3) atomicAdd(slot + c3, (double)g3[c3]);
     }
+}
+
+__global__ void __launch_bounds__(256) adj_grad_finish_kernel(const double* gslots, double* grad) {
+    __shared__ double sh[3][256];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < kGradSlots; i += blockDim.x)
+        for (int c = 0; c < 3; ++c) s[c] += gslots[3 * i + c];
+    for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] = s[c];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) grad[threadIdx.x] += sh[threadIdx.x][0];
 }
 
 // ------------------------------------------------------------------- R2
@@ -446,22 +500,30 @@ __global__ void __launch_bounds__(kBX * kBY) adj_faces_kernel(const AdjArgs a) {
     const float* bx = a.bbar[0];
     const float* by = a.bbar[1];
     const float* bz = a.bbar[2];
-    const float sx = 0.125f * (rd<PER>(g, bx, i, j, k) + rd<PER>(g, bx, i, j + 1, k) + rd<PER>(g, bx, i, j, k + 1)
-                               + rd<PER>(g, bx, i, j + 1, k + 1));
-    const float sy = 0.125f * (rd<PER>(g, by, i, j, k) + rd<PER>(g, by, i + 1, j, k) + rd<PER>(g, by, i, j, k + 1)
-                               + rd<PER>(g, by, i + 1, j, k + 1));
-    const float sz = 0.125f * (rd<PER>(g, bz, i, j, k) + rd<PER>(g, bz, i + 1, j, k) + rd<PER>(g, bz, i, j + 1, k)
-                               + rd<PER>(g, bz, i + 1, j + 1, k));
+    float sx, sy, sz;
+    if (PER) {
+        sx = 0.125f * (rd<true>(g, bx, i, j, k) + rd<true>(g, bx, i, j + 1, k) + rd<true>(g, bx, i, j, k + 1)
+                       + rd<true>(g, bx, i, j + 1, k + 1));
+        sy = 0.125f * (rd<true>(g, by, i, j, k) + rd<true>(g, by, i + 1, j, k) + rd<true>(g, by, i, j, k + 1)
+                       + rd<true>(g, by, i + 1, j, k + 1));
+        sz = 0.125f * (rd<true>(g, bz, i, j, k) + rd<true>(g, bz, i + 1, j, k) + rd<true>(g, bz, i, j + 1, k)
+                       + rd<true>(g, bz, i + 1, j + 1, k));
+    } else {
+        const Nbr n = nbr_of(g, i, j, k);
+        const float x0 = bx[o], x1 = bx[o + n.pj], x2 = bx[o + n.pk], x3 = bx[o + n.pj + n.pk];
+        const float y0 = by[o], y1 = by[o + n.pi], y2 = by[o + n.pk], y3 = by[o + n.pi + n.pk];
+        const float z0 = bz[o], z1 = bz[o + n.pi], z2 = bz[o + n.pj], z3 = bz[o + n.pi + n.pj];
+        sx = 0.125f * (x0 + msk(n.jp, x1) + msk(n.kp, x2) + msk(n.jp && n.kp, x3));
+        sy = 0.125f * (y0 + msk(n.ip, y1) + msk(n.kp, y2) + msk(n.ip && n.kp, y3));
+        sz = 0.125f * (z0 + msk(n.ip, z1) + msk(n.jp, z2) + msk(n.ip && n.jp, z3));
+    }
     const float s3[3] = {sx, sy, sz};
+    const float bn[3] = {a.Bnp[0][o], a.Bnp[1][o], a.Bnp[2][o]};
     for (int c = 0; c < 3; ++c) {
-        if (PER || act_B(g, c, i, j, k)) {
-            const float bnt = a.Bnp[c][o] + s3[c];
-            a.Bnp[c][o] = bnt;
-            a.Bbar[c][o] = bnt + s3[c];
-        } else {
-            a.Bnp[c][o] = 0.0f;
-            a.Bbar[c][o] = 0.0f;
-        }
+        const bool on = PER || act_B(g, c, i, j, k);
+        const float bnt = bn[c] + s3[c];
+        a.Bnp[c][o] = on ? bnt : 0.0f;
+        a.Bbar[c][o] = on ? bnt + s3[c] : 0.0f;
     }
 }
 
@@ -481,24 +543,45 @@ __global__ void __launch_bounds__(kBX * kBY) adj_edges_kernel(const AdjArgs a) {
     const float* ex = a.ebar[0];
     const float* ey = a.ebar[1];
     const float* ez = a.ebar[2];
-    if (PER || act_E(g, 0, i, j, k))
-        a.Ebar[0][o] = a.Ebar[0][o] + 0.5f * (rd<PER>(g, ex, i, j, k) + rd<PER>(g, ex, i + 1, j, k))
-                     + c * (rd<PER>(g, By, i, j, k) - rd<PER>(g, By, i, j, k - 1) - rd<PER>(g, Bz, i, j, k)
-                            + rd<PER>(g, Bz, i, j - 1, k));
-    else
-        a.Ebar[0][o] = 0.0f;
-    if (PER || act_E(g, 1, i, j, k))
-        a.Ebar[1][o] = a.Ebar[1][o] + 0.5f * (rd<PER>(g, ey, i, j, k) + rd<PER>(g, ey, i, j + 1, k))
-                     + c * (-rd<PER>(g, Bx, i, j, k) + rd<PER>(g, Bx, i, j, k - 1) + rd<PER>(g, Bz, i, j, k)
-                            - rd<PER>(g, Bz, i - 1, j, k));
-    else
-        a.Ebar[1][o] = 0.0f;
-    if (PER || act_E(g, 2, i, j, k))
-        a.Ebar[2][o] = a.Ebar[2][o] + 0.5f * (rd<PER>(g, ez, i, j, k) + rd<PER>(g, ez, i, j, k + 1))
-                     + c * (rd<PER>(g, Bx, i, j, k) - rd<PER>(g, Bx, i, j - 1, k) - rd<PER>(g, By, i, j, k)
-                            + rd<PER>(g, By, i - 1, j, k));
-    else
-        a.Ebar[2][o] = 0.0f;
+    float bx, by, bz, by_k, bz_j, bx_k, bz_i, bx_j, by_i, e0, e1, e2;
+    if (PER) {
+        bx = rd<true>(g, Bx, i, j, k);
+        by = rd<true>(g, By, i, j, k);
+        bz = rd<true>(g, Bz, i, j, k);
+        by_k = rd<true>(g, By, i, j, k - 1);
+        bz_j = rd<true>(g, Bz, i, j - 1, k);
+        bx_k = rd<true>(g, Bx, i, j, k - 1);
+        bz_i = rd<true>(g, Bz, i - 1, j, k);
+        bx_j = rd<true>(g, Bx, i, j - 1, k);
+        by_i = rd<true>(g, By, i - 1, j, k);
+        e0 = rd<true>(g, ex, i, j, k) + rd<true>(g, ex, i + 1, j, k);
+        e1 = rd<true>(g, ey, i, j, k) + rd<true>(g, ey, i, j + 1, k);
+        e2 = rd<true>(g, ez, i, j, k) + rd<true>(g, ez, i, j, k + 1);
+    } else {
+        const Nbr n = nbr_of(g, i, j, k);
+        bx = Bx[o];
+        by = By[o];
+        bz = Bz[o];
+        const float v0 = By[o - n.mk], v1 = Bz[o - n.mj], v2 = Bx[o - n.mk], v3 = Bz[o - n.mi], v4 = Bx[o - n.mj],
+                    v5 = By[o - n.mi];
+        const float x0 = ex[o], x1 = ex[o + n.pi], y0 = ey[o], y1 = ey[o + n.pj], z0 = ez[o], z1 = ez[o + n.pk];
+        by_k = msk(n.km, v0);
+        bz_j = msk(n.jm, v1);
+        bx_k = msk(n.km, v2);
+        bz_i = msk(n.im, v3);
+        bx_j = msk(n.jm, v4);
+        by_i = msk(n.im, v5);
+        e0 = x0 + msk(n.ip, x1);
+        e1 = y0 + msk(n.jp, y1);
+        e2 = z0 + msk(n.kp, z1);
+    }
+    const float E0 = a.Ebar[0][o], E1 = a.Ebar[1][o], E2 = a.Ebar[2][o];
+    const bool a0 = PER || act_E(g, 0, i, j, k);
+    const bool a1 = PER || act_E(g, 1, i, j, k);
+    const bool a2 = PER || act_E(g, 2, i, j, k);
+    a.Ebar[0][o] = a0 ? E0 + 0.5f * e0 + c * (by - by_k - bz + bz_j) : 0.0f;
+    a.Ebar[1][o] = a1 ? E1 + 0.5f * e1 + c * (-bx + bx_k + bz - bz_i) : 0.0f;
+    a.Ebar[2][o] = a2 ? E2 + 0.5f * e2 + c * (bx - bx_j - by + by_i) : 0.0f;
 }
 
 // ------------------------------------------------------------- profile
@@ -581,7 +664,15 @@ cudaError_t launch_adj_fluid_s(const AdjArgs& a, int collision, cudaStream_t s) 
 
 }  // namespace
 
-cudaError_t launch_adjoint_step(const AdjArgs& a, int storage, int collision, cudaStream_t s) {
+cudaError_t launch_adjoint_grad_finish(const double* gslots, double* grad, cudaStream_t s) {
+    adj_grad_finish_kernel<<<1, 256, 0, s>>>(gslots, grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_step(const AdjArgs& a0, int storage, int collision, cudaStream_t s) {
+    AdjArgs a = a0;
+    a.csr = a.f.alpha / (a.sr * a.sr * a.sr);
+    a.csz = a.f.alpha / (a.sz * a.sz * a.sz);
     const Grid& g = a.f.g;
     const dim3 grid = grid_of(g, kBX, kBY), block(kBX, kBY, 1);
     const bool per = g.periodic;

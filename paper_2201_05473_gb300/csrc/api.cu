@@ -589,7 +589,8 @@ int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_ever
     const size_t fb = fbytes_of(in), vb = vbytes_of(in);
     r.cp_stride = fb + 6 * vb;
     r.seg_stride = fb + 6 * vb;  // per step: populations, E, B (plus one trailing B)
-    const size_t adj_bytes = 2 * align_up((size_t)in.g.Np * kPop * sizeof(float)) + 22 * vb + align_up(sizeof(double) * 260);
+    const size_t adj_bytes = 2 * align_up((size_t)in.g.Np * kPop * sizeof(float)) + 22 * vb +
+                             align_up(sizeof(double) * (260 + 3 * kGradSlots));
     if (cudaMalloc(&r.cp, r.cp_stride * (r.ncp + 1)) != cudaSuccess ||
         cudaMalloc(&r.seg, r.seg_stride * r.K + 3 * vb) != cudaSuccess ||
         cudaMalloc(&r.adj, adj_bytes) != cudaSuccess) {
@@ -642,11 +643,23 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
     double* grad = (double*)p;
     for (int c = 0; c < 3; ++c) { a.Ebar[c] = Ebar[c]; a.Bbar[c] = Bbar[c]; }
     a.grad = grad;
+    a.gslots = grad + 260;
     a.sr = (float)in.p.sigma_r;
     a.sz = (float)in.p.sigma_z;
-    PWFA_CUDA(cudaMemsetAsync(r.adj, 0, (size_t)(p - (char*)r.adj) + sizeof(double) * 260, s), "cudaMemsetAsync");
+    PWFA_CUDA(cudaMemsetAsync(r.adj, 0, (size_t)(p - (char*)r.adj) + sizeof(double) * (260 + 3 * kGradSlots), s),
+              "cudaMemsetAsync");
     for (int c = 0; c < 3; ++c)
         PWFA_CUDA(cudaMemcpyAsync(Ebar[c], seed_E + c * N, sizeof(float) * N, cudaMemcpyDefault, s), "seed copy");
+    if (!in.g.periodic) {
+        // the adjoint keeps E_bar zero at the components the conducting walls
+        // hold at zero; the seed's values there never enter the forward
+        StepArgs z = make_args(in);
+        for (int c = 0; c < 3; ++c) {
+            z.Eout[c] = Ebar[c];
+            z.Bc[c] = Bbar[c];
+        }
+        PWFA_CUDA(launch_zero_walls(z, s), "seed mask");
+    }
     int cur = 0;
     for (int seg = r.ncp - 1; seg >= 0; --seg) {
         const int64_t s0 = (int64_t)seg * r.K, s1 = std::min<int64_t>(r.T, s0 + r.K);
@@ -727,6 +740,7 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
             cur = 1 - cur;
         }
     }
+    PWFA_CUDA(launch_adjoint_grad_finish(a.gslots, grad, s), "driver gradient");
     PWFA_CUDA(launch_adjoint_profile(in.g, Sbar[cur], (float)in.p.n0, np, in.p.profile_rmax, in.p.dx, grad + 3, s),
               "profile gradient");
     PWFA_CUDA(cudaMemcpyAsync(host_grad, grad, sizeof(double) * (3 + np), cudaMemcpyDeviceToHost, s), "grad copy");

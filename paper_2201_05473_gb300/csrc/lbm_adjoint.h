@@ -5,6 +5,12 @@
 
 namespace pwfa {
 
+// Driver-gradient accumulation slots: each warp of the Ampere adjoint adds
+// its three partial sums to FP64 slot (warp % kGradSlots), which spreads the
+// atomics over 3 kGradSlots addresses; the slots are summed into grad[0..2]
+// once, after the sweep.
+constexpr int kGradSlots = 1024;
+
 struct AdjArgs {
     StepArgs f;           // forward state of the reversed step: fin = S^{n-1},
                           // E = E^n, Bc = B(t_n), Bn = B(t_{n+1}), driver at t_{n+1}
@@ -17,12 +23,17 @@ struct AdjArgs {
     float* ebar[3];       // scratch: adjoint of the node-averaged E
     float* bbar[3];       // scratch: adjoint of the node-averaged B (each time level)
     float* Abnd[4];       // scratch: moment adjoints of Eq. 14 boundary nodes
-    double* grad;         // d/d(alpha, sigma_r, sigma_z), accumulated
+    double* grad;         // d/d(alpha, sigma_r, sigma_z), then the profile gradient
+    double* gslots;       // [kGradSlots][3] partial sums of d/d(alpha, sigma_r, sigma_z)
     float sr, sz;         // driver sigma_r, sigma_z
+    float csr, csz;       // alpha / sigma_r^3, alpha / sigma_z^3 (set by launch_adjoint_step)
 };
 
 // R1..R4 of one reversed step on stream s.
 cudaError_t launch_adjoint_step(const AdjArgs& a, int storage, int collision, cudaStream_t s);
+
+// grad[0..2] = the sums of the driver-gradient slots.
+cudaError_t launch_adjoint_grad_finish(const double* gslots, double* grad, cudaStream_t s);
 
 // Profile gradient from the adjoint of the initial stored populations
 // (lattice 0 block of Sbar, population layout); n_profile <= 256.
