@@ -337,19 +337,40 @@ __global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_ke
     const bool proj = COLL == 1 && !bnd;
 
     // ---- this lattice's reductions over the 19 directions
-    float Gb = 0.0f, sphi = 0.0f, P[3] = {0.0f, 0.0f, 0.0f}, W[3] = {0.0f, 0.0f, 0.0f};
+    // Gb = sum w S, P = sum w S xi, W = sum w S xi (xi.u) and
+    // sphi = sum w S phi_i / w_i = base Gb + 3 u.P + 4.5 u.W (since
+    // sum w S (xi.u)^2 = u.W): per direction only signed adds into the sums
+    // of its weight class (axis 1/18, diagonal 1/36), weighted once at the end.
+    float Gb, sphi, P[3], W[3];
     {
-        const float base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        float G1 = 0.0f, G2 = 0.0f, P1[3] = {0.0f, 0.0f, 0.0f}, P2[3] = {0.0f, 0.0f, 0.0f};
+        float W1[3] = {0.0f, 0.0f, 0.0f}, W2[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            const float xu = (float)xi_x(q) * u[0] + (float)xi_y(q) * u[1] + (float)xi_z(q) * u[2];
-            const float ws = wq(q) * S[q];
-            Gb += ws;
-            sphi += ws * (base + 3.0f * xu + 4.5f * xu * xu);
-            if (xi_x(q)) { P[0] += (float)xi_x(q) * ws; W[0] += (float)xi_x(q) * ws * xu; }
-            if (xi_y(q)) { P[1] += (float)xi_y(q) * ws; W[1] += (float)xi_y(q) * ws * xu; }
-            if (xi_z(q)) { P[2] += (float)xi_z(q) * ws; W[2] += (float)xi_z(q) * ws * xu; }
+        for (int q = 1; q < kQ; ++q) {
+            float xu = 0.0f;
+            if (xi_x(q) > 0) xu += u[0]; else if (xi_x(q) < 0) xu -= u[0];
+            if (xi_y(q) > 0) xu += u[1]; else if (xi_y(q) < 0) xu -= u[1];
+            if (xi_z(q) > 0) xu += u[2]; else if (xi_z(q) < 0) xu -= u[2];
+            const float sx = S[q] * xu;
+            const bool diag = q > 6;
+            float& G = diag ? G2 : G1;
+            float* Pc = diag ? P2 : P1;
+            float* Wc = diag ? W2 : W1;
+            G += S[q];
+            if (xi_x(q) > 0) { Pc[0] += S[q]; Wc[0] += sx; } else if (xi_x(q) < 0) { Pc[0] -= S[q]; Wc[0] -= sx; }
+            if (xi_y(q) > 0) { Pc[1] += S[q]; Wc[1] += sx; } else if (xi_y(q) < 0) { Pc[1] -= S[q]; Wc[1] -= sx; }
+            if (xi_z(q) > 0) { Pc[2] += S[q]; Wc[2] += sx; } else if (xi_z(q) < 0) { Pc[2] -= S[q]; Wc[2] -= sx; }
         }
+        const float wa = 1.0f / 18.0f, wd = 1.0f / 36.0f;
+        Gb = wq(0) * S[0] + wa * G1 + wd * G2;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            P[c] = wa * P1[c] + wd * P2[c];
+            W[c] = wa * W1[c] + wd * W2[c];
+        }
+        const float base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        sphi = base * Gb + 3.0f * (u[0] * P[0] + u[1] * P[1] + u[2] * P[2]) +
+               4.5f * (u[0] * W[0] + u[1] * W[1] + u[2] * W[2]);
     }
     // u_bar share: d(A_l phi_i)/du through phi_i = w_i (base + 3 xi.u + 4.5 (xi.u)^2),
     // plus the regularized projection's -k3 A_l P_l
