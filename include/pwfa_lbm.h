@@ -265,7 +265,7 @@ int pwfa_lbm_profile(pwfa_lbm_t* h, int32_t enable);
 int pwfa_lbm_kernel_times(pwfa_lbm_t* h, double* ms, int64_t* launches);
 
 /* Thread-block shape (bx * by threads, bx along x) of the fused fluid kernel
- * for one instance. bx, by >= 1, bx * by a multiple of 32 and at most 256;
+ * for one instance. bx, by >= 1, bx * by a multiple of 32 and at most 128;
  * PWFA_ERR_PARAM otherwise. */
 int pwfa_lbm_set_launch(pwfa_lbm_t* h, int32_t instance, int32_t bx, int32_t by);
 int pwfa_lbm_get_launch(pwfa_lbm_t* h, int32_t instance, int32_t* bx, int32_t* by);

@@ -1112,8 +1112,8 @@ int pwfa_lbm_kernel_times(pwfa_lbm_t* h, double* ms, int64_t* launches) {
 int pwfa_lbm_set_launch(pwfa_lbm_t* h, int32_t instance, int32_t bx, int32_t by) {
     int rc = check_instance(h, instance);
     if (rc) return rc;
-    if (bx < 1 || by < 1 || bx * by > 256 || (bx * by) % 32)
-        return fail(PWFA_ERR_PARAM, "block shape must be a multiple of 32 threads, at most 256");
+    if (bx < 1 || by < 1 || bx * by > PWFA_FLUID_MAX_THREADS || (bx * by) % 32)
+        return fail(PWFA_ERR_PARAM, "block shape must be a multiple of 32 threads, at most 128");
     h->inst[instance].bx = bx;
     h->inst[instance].by = by;
     h->batch_valid = false;
@@ -1148,12 +1148,12 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
     if (reps < 1) return fail(PWFA_ERR_PARAM, "reps must be >= 1");
     // {bx, by, variant}: direct shapes, then the staged kernel's 128-thread tiles
-    static const int cand_all[][3] = {{32, 4, 0}, {32, 8, 0}, {64, 2, 0}, {64, 4, 0}, {128, 1, 0}, {128, 2, 0},
-                                      {256, 1, 0}, {32, 4, 1}, {64, 2, 1}, {128, 1, 1}};
+    static const int cand_all[][3] = {{32, 4, 0}, {64, 2, 0}, {128, 1, 0}, {32, 4, 1}, {64, 2, 1}, {128, 1, 1}};
     // the batched kernels take tiles of kBatchTile nodes
     static const int cand_batch[][3] = {{32, 4, 0}, {64, 2, 0}, {128, 1, 0}};
     const bool batched = batch_eligible(h);
-    const int ncand = batched ? 3 : 10;
+    const int ncand = batched ? (int)(sizeof cand_batch / sizeof cand_batch[0])
+                              : (int)(sizeof cand_all / sizeof cand_all[0]);
     h->batch_valid = false;
     cudaEvent_t e0, e1;
     PWFA_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
@@ -1165,6 +1165,7 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
         for (int ci = 0; ci < ncand; ++ci) {
             const int* c = batched ? cand_batch[ci] : cand_all[ci];
             if (c[0] > 2 * in.g.nx && c[0] > 32) continue;  // mostly idle lanes
+            if (c[0] * c[1] > PWFA_FLUID_MAX_THREADS) continue;
             in.bx = c[0];
             in.by = c[1];
             in.variant = c[2];

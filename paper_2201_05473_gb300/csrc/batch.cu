@@ -4,6 +4,7 @@
 // CUDA graph. Each tile is 128 nodes of one z-plane in the instance's
 // autotuned shape (bx x by, bx * by = 128). No inter-CTA waits.
 #include "lbm_batch.h"
+#include "lbm_kernels.h"
 #include "fields_node.cuh"
 #include "fluid_node.cuh"
 
@@ -19,11 +20,12 @@ constexpr int kThreads = kBatchTile;
 __constant__ BatchEntry c_entries[kMaxBatch];
 static_assert(sizeof(BatchEntry) * kMaxBatch <= 60 * 1024, "instance table exceeds constant memory");
 
-// Resident blocks per SM: the fluid phase needs up to 128 registers (4 blocks
-// of 128 threads); the light field phases run 8 blocks (64 registers).
-template <int PHASE>
+// Resident blocks per SM: the fluid phase as the single-instance fluid
+// kernel (FluidOcc: 96 or 128 registers); the light field phases run 8
+// blocks (64 registers).
+template <int PHASE, int COLL>
 struct PhaseOcc {
-    static constexpr int blocks = PHASE == 1 ? 4 : 8;
+    static constexpr int blocks = PHASE == 1 ? FluidOcc<COLL>::blocks : 8;
 };
 
 // Work items are handed out in order by a global counter (one atomic per
@@ -36,7 +38,7 @@ struct PhaseOcc {
 constexpr int kFieldGrab = 4;
 
 template <int ST, int COLL, bool PER, int PHASE>
-__global__ void __launch_bounds__(kThreads, PhaseOcc<PHASE>::blocks) batch_kernel(int ninst, int nitems,
+__global__ void __launch_bounds__(kThreads, PhaseOcc<PHASE, COLL>::blocks) batch_kernel(int ninst, int nitems,
                                                                                   int parity, int* counter) {
     constexpr int grab = PHASE == 1 ? 1 : kFieldGrab;
     __shared__ int s_next[2];
@@ -92,7 +94,7 @@ __global__ void batch_advance_kernel(const BatchEntry* ent, int ninst, int* coun
 template <int ST, int COLL, bool PER>
 cudaError_t launch_phase(const BatchLaunch& b, int phase, int parity, cudaStream_t s) {
     const int g1 = b.grid;                                     // fluid phase
-    const int gf = b.grid / PhaseOcc<1>::blocks * PhaseOcc<0>::blocks;  // field phases
+    const int gf = b.grid / PhaseOcc<1, COLL>::blocks * PhaseOcc<0, COLL>::blocks;  // field phases
     switch (phase) {
         case 0: batch_kernel<ST, COLL, PER, 0><<<gf, kThreads, 0, s>>>(b.ninst, (int)b.nitems, parity, b.counters); break;
         case 1: batch_kernel<ST, COLL, PER, 1><<<g1, kThreads, 0, s>>>(b.ninst, (int)b.nitems, parity, b.counters + 1); break;

@@ -13,15 +13,8 @@ namespace pwfa {
 
 namespace {
 
-#ifndef PWFA_FLUID_MAX_THREADS
-#define PWFA_FLUID_MAX_THREADS 256
-#endif
-#ifndef PWFA_FLUID_MIN_BLOCKS
-#define PWFA_FLUID_MIN_BLOCKS 2
-#endif
-
 template <int ST, int COLL, bool PER>
-__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS) fluid_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, FluidOcc<COLL>::blocks) fluid_kernel(const StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.g.nx || y >= a.g.ny) return;
@@ -67,7 +60,7 @@ __device__ __forceinline__ float diag8_warp(const float (&v)[8], int lane) {
 }
 
 template <int ST, int COLL, bool PER>
-__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, PWFA_FLUID_MIN_BLOCKS)
+__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, FluidOcc<COLL>::blocks)
     fluid_diag_kernel(const StepArgs a, int fields, float* records) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;

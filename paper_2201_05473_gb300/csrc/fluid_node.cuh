@@ -22,6 +22,20 @@ struct NodeDiag {
     float n, a1, a2, a3, beta2;
 };
 
+// m = sum_i xi_i f_i over one lattice's 19 values (signed adds, q ascending).
+__device__ __forceinline__ void first_moments(const float (&fl)[kQ], float (&m)[3]) {
+    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+#pragma unroll
+    for (int q = 1; q < kQ; ++q) {
+        if (xi_x(q) > 0) m0 += fl[q]; else if (xi_x(q) < 0) m0 -= fl[q];
+        if (xi_y(q) > 0) m1 += fl[q]; else if (xi_y(q) < 0) m1 -= fl[q];
+        if (xi_z(q) > 0) m2 += fl[q]; else if (xi_z(q) < 0) m2 -= fl[q];
+    }
+    m[0] = m0;
+    m[1] = m1;
+    m[2] = m2;
+}
+
 // Everything after the gather: moments, source, collision, stores, current.
 // f holds the pulled populations f^n(x) (of the clamped node when bnd).
 template <int ST, int COLL, bool PER, bool DIAG = false>
@@ -34,6 +48,14 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
     float A[kL], inn, beta[3];
     node_moments(f, a.n_floor, A, inn, beta);
     const float n = A[0];
+    // Regularized: the first moments m_l = sum_i xi_i f_l,i, taken here so
+    // that the 76 pulled values are dead before the fields are read (a
+    // boundary node recomputes them from its equilibrium below).
+    float m[kL][3];
+    if (COLL == 1) {
+#pragma unroll
+        for (int l = 0; l < kL; ++l) first_moments(f[l], m[l]);
+    }
     if (DIAG) {
         nd->n = A[0];
         nd->a1 = A[1];
@@ -68,9 +90,11 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
     if (!PER && bnd) {
         // Eq. 14: a boundary node holds the equilibrium of the clamped node.
 #pragma unroll
-        for (int l = 0; l < kL; ++l)
+        for (int l = 0; l < kL; ++l) {
 #pragma unroll
             for (int q = 0; q < kQ; ++q) f[l][q] = A[l] * phi[q];
+            if (COLL == 1) first_moments(f[l], m[l]);
+        }
     }
     // Collide in place, lattice pair by lattice pair; FP32 stores each value
     // as it is made, the 16-bit forms store each pair of lattices as 32-bit
@@ -89,13 +113,7 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
                 // Regularized: relax only the first Hermite moment of f - f^eq,
                 // Pi = sum_i xi_i (f_i - A phi_i) = sum_i xi_i f_i - A u
                 // (sum_i xi_i phi_i = u exactly for the D3Q19 weights).
-                float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
-#pragma unroll
-                for (int q = 1; q < kQ; ++q) {
-                    if (xi_x(q) > 0) m0 += f[l][q]; else if (xi_x(q) < 0) m0 -= f[l][q];
-                    if (xi_y(q) > 0) m1 += f[l][q]; else if (xi_y(q) < 0) m1 -= f[l][q];
-                    if (xi_z(q) > 0) m2 += f[l][q]; else if (xi_z(q) < 0) m2 -= f[l][q];
-                }
+                const float m0 = m[l][0], m1 = m[l][1], m2 = m[l][2];
                 // w_i (xi_i . P + F dt) with the two weights of the moving
                 // directions (1/18 axis, 1/36 diagonal) folded into P and F:
                 // f = A phi_i + one or two adds of +-P_k w + F w.

@@ -8,6 +8,25 @@
 
 namespace pwfa {
 
+// Launch bounds of the fluid kernels: blocks of at most 128 threads; five
+// per SM (a 96-register budget) for the regularized form, four (128
+// registers) for BGK and stream-only. With its first moments taken right
+// after the gather the regularized kernel fits 96 registers without spilling
+// and the extra warps hide the pull's latency (production grid: FP32 3.24 ->
+// 3.17 ms, BF16 2.05 -> 1.86 ms against 128 registers and four blocks). BGK
+// and stream-only carry every pulled value itself through the source
+// computation and would spill at 96.
+#ifndef PWFA_FLUID_MAX_THREADS
+#define PWFA_FLUID_MAX_THREADS 128
+#endif
+#ifndef PWFA_FLUID_MIN_BLOCKS
+#define PWFA_FLUID_MIN_BLOCKS 5
+#endif
+template <int COLL>
+struct FluidOcc {
+    static constexpr int blocks = COLL == 1 ? PWFA_FLUID_MIN_BLOCKS : 4;
+};
+
 // Where the fused diagnostics of a step go. The fluid launch writes one FP32
 // record of 8 values per warp (sum n, sum n p_x, p_y, p_z, field energy /
 // dx^3, min n, min -|beta|^2, non-finite count); when the step's Faraday
