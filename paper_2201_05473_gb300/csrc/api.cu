@@ -50,6 +50,7 @@ struct Instance {
     float* Ealt[3] = {nullptr, nullptr, nullptr};  // moving window: E is moved into it
     float* Jb[3] = {nullptr, nullptr, nullptr};    // PIC driver: deposited current
     float* particles = nullptr;                    // PIC driver: [6][np]
+    int* jbox = nullptr;                           // PIC driver: deposit boxes of the two step parities
     int64_t np = 0;
     double pweight = 0.0;
     float* B[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -198,6 +199,8 @@ StepArgs make_args(const Instance& in) {
     a.by = in.by;
     a.staged = in.variant == PWFA_FLUID_STAGED && in.bx * in.by == 128;
     for (int c = 0; c < 3; ++c) a.Jb[c] = in.Jb[c];
+    a.jbox = in.jbox ? in.jbox + 6 * (in.steps & 1) : nullptr;
+    a.jbox_next = in.jbox ? in.jbox + 6 * ((in.steps + 1) & 1) : nullptr;
     return a;
 }
 
@@ -234,6 +237,8 @@ void free_instance(Instance& in) {
     free_recording(in);
     if (in.particles) cudaFree(in.particles);
     in.particles = nullptr;
+    if (in.jbox) cudaFree(in.jbox);
+    in.jbox = nullptr;
     if (in.arena) cudaFree(in.arena);
     in.arena = nullptr;
 }
@@ -269,6 +274,16 @@ int alloc_instance(Instance& in, cudaStream_t s) {
     if (in.p.driver == PWFA_DRIVER_PIC)
         for (int c = 0; c < 3; ++c) { in.Jb[c] = (float*)(base + pad); base += vbytes; }
     in.d_profile = (double*)base;
+    if (in.p.driver == PWFA_DRIVER_PIC) {
+        // deposit boxes of both step parities, empty
+        const int empty[12] = {0x7fffffff, 0x7fffffff, 0x7fffffff, -1, -1, -1,
+                               0x7fffffff, 0x7fffffff, 0x7fffffff, -1, -1, -1};
+        if (cudaMalloc(&in.jbox, sizeof empty) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the deposit boxes failed");
+        }
+        PWFA_CUDA(cudaMemcpy(in.jbox, empty, sizeof empty, cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
     // Fields, currents, their guard planes and the second population buffer
     // start at zero.
     PWFA_CUDA(cudaMemsetAsync(in.f[1], 0, fbytes, s), "cudaMemsetAsync");
@@ -519,8 +534,6 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
                       [&] { return launch_fluid(a, in.p.storage, in.p.collision, s, diag ? &dg : nullptr); });
     if (rc) return rc;
     if (in.p.driver == PWFA_DRIVER_PIC) {
-        for (int c = 0; c < 3; ++c)
-            PWFA_CUDA(cudaMemsetAsync(in.Jb[c], 0, sizeof(float) * in.g.N, s), "cudaMemsetAsync");
         rc = timed_launch(h, PWFA_KERNEL_AUX, "particle kernel",
                           [&] { return launch_push_deposit(a, in.particles, in.np, in.pweight, in.Jb, s); });
         if (rc) return rc;

@@ -47,6 +47,11 @@ template <bool PER>
 __global__ void __launch_bounds__(kBX * kBY) ampere_kernel(const StepArgs a) {
     const int i = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y;
+    if (a.jbox_next && i == 0 && j == 0 && blockIdx.z == 0) {
+        // the next step's deposit box starts empty
+        a.jbox_next[0] = a.jbox_next[1] = a.jbox_next[2] = 0x7fffffff;
+        a.jbox_next[3] = a.jbox_next[4] = a.jbox_next[5] = -1;
+    }
     if (i >= a.g.nx || j >= a.g.ny) return;
     ampere_node<PER>(a, i, j, blockIdx.z, a.zc);
 }

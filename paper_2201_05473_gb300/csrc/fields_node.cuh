@@ -72,7 +72,16 @@ __device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int
     const float j1 = yee_ld<PER>(g, a.J[1], i, j, k), j1_j = yee_ld<PER>(g, a.J[1], i, jp, k);
     const float j2 = yee_ld<PER>(g, a.J[2], i, j, k), j2_k = yee_ld<PER>(g, a.J[2], i, j, kp);
     const float e0 = a.Eout[0][o], e1 = a.Eout[1][o], e2 = a.Eout[2][o];
-    const float jb0 = a.Jb[0] ? a.Jb[0][o] : 0.0f, jb1 = a.Jb[1] ? a.Jb[1][o] : 0.0f;
+    // PIC deposit: read (and clear for the next step) only inside its box
+    const bool inbox = a.Jb[0] && i >= a.jbox[0] && j >= a.jbox[1] && k >= a.jbox[2] && i <= a.jbox[3] &&
+                       j <= a.jbox[4] && k <= a.jbox[5];
+    const float jb0 = inbox ? a.Jb[0][o] : 0.0f, jb1 = inbox ? a.Jb[1][o] : 0.0f;
+    const float jb2 = inbox ? a.Jb[2][o] : 0.0f;
+    if (inbox) {
+        a.Jb[0][o] = 0.0f;
+        a.Jb[1][o] = 0.0f;
+        a.Jb[2][o] = 0.0f;
+    }
     const bool cx = PER || (i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2);
     const bool cy = PER || (i >= 1 && i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2);
     const bool cz = PER || (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2);
@@ -90,7 +99,7 @@ __device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int
         const float je = 0.5f * (j2 + j2_k);
         float jb = 0.0f;
         if (a.Jb[2]) {
-            jb = a.Jb[2][o];
+            jb = jb2;
         } else if (a.alpha != 0.0f) {
             const float xr = ((float)i - 0.5f * (float)(nx - 1)) * a.dx;
             const float yr = ((float)j - 0.5f * (float)(ny - 1)) * a.dx;

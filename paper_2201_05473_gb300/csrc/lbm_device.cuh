@@ -148,7 +148,12 @@ struct StepArgs {
     int couple;
     // driver: J_b,z = -alpha exp(-r^2/(2 sr^2) - (z - zc)^2/(2 sz^2)) at t_{n+1}
     float alpha, inv2sr2, inv2sz2, zc, dx;
-    const float* Jb[3];   // PIC driver: deposited current on the E edges (else null)
+    float* Jb[3];         // PIC driver: deposited current on the E edges (else null);
+                          // Ampere zeroes what it consumes, so the arrays stay
+                          // zero outside the box of the last deposit
+    int* jbox;            // PIC driver: [lo x, y, z, hi x, y, z] node box of this
+                          // step's deposit (hi < lo: none)
+    int* jbox_next;       // the other step parity's box, emptied by Ampere
     uint32_t src_shift;   // added to every pulled source node: nx*ny on a step
                           // that moves the window (the streaming source is
                           // read one plane up), else 0

@@ -82,8 +82,9 @@ cudaError_t launch_window_move(const WindowMove& w, cudaStream_t s);
 
 // PIC driver: push np macro-electrons (xp[6][np]: x, y, z at t_{n+1/2},
 // p_x, p_y, p_z at t_n) with the step's fields and add the current of their
-// moves to Jb (E-edge arrays, zeroed by the caller). weight: electrons per
-// macro-particle in units of n0 (c/omega_p)^3.
+// moves to Jb (E-edge arrays, zero outside a.jbox: Ampere clears what it
+// consumes), growing the node box a.jbox to cover every deposit. weight:
+// electrons per macro-particle in units of n0 (c/omega_p)^3.
 cudaError_t launch_push_deposit(const StepArgs& a, float* xp, int64_t np, double weight, float* const Jb[3],
                                 cudaStream_t s);
 

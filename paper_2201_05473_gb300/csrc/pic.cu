@@ -8,7 +8,9 @@
 // x_{n+3/2} = x_{n+1/2} + dt p_{n+1}/gamma; the current of the move added to
 // J_b on the E edges by Esirkepov's charge-conserving scheme (Comput. Phys.
 // Commun. 135, 2001) for the linear shape, with FP32 atomics. Particles
-// outside an open grid see no field and deposit only on in-grid edges.
+// outside an open grid see no field and deposit only on in-grid edges. Each
+// block also grows the step's deposit box, so that Ampere's law reads (and
+// clears) J_b only where particles deposited instead of over the whole grid.
 #include "lbm_kernels.h"
 
 namespace pwfa {
@@ -59,10 +61,40 @@ __device__ __forceinline__ void add_edge(const Grid& g, float* a, int i, int j, 
     atomicAdd(a + ((int64_t)k * g.ny + j) * g.nx + i, v);
 }
 
-__global__ void __launch_bounds__(128) push_deposit_kernel(const StepArgs a, float* xp, int64_t np, float coef,
-                                                           float* jx, float* jy, float* jz) {
-    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= np) return;
+// Node box of the block's deposits, merged into a.jbox: per axis the 3-node
+// stencil [base, base + 2] of every particle, clamped to the grid (the whole
+// grid when periodic, where the stencil may wrap). Warp reductions, then
+// shared-memory atomics, then six global atomics per block.
+__device__ __forceinline__ void merge_box(const StepArgs& a, bool valid, const int base[3]) {
+    __shared__ int sbox[6];
+    if (threadIdx.x < 6) sbox[threadIdx.x] = threadIdx.x < 3 ? 0x7fffffff : -1;
+    __syncthreads();
+    const int n[3] = {a.g.nx, a.g.ny, a.g.nz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int lo = 0x7fffffff, hi = -1;
+        if (valid) {
+            lo = a.g.periodic ? 0 : max(base[d], 0);
+            hi = a.g.periodic ? n[d] - 1 : min(base[d] + 2, n[d] - 1);
+        }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if ((threadIdx.x & 31) == 0 && lo <= hi) {
+            atomicMin(sbox + d, lo);
+            atomicMax(sbox + 3 + d, hi);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 && sbox[threadIdx.x] <= sbox[3 + threadIdx.x]) {
+        atomicMin(a.jbox + threadIdx.x, sbox[threadIdx.x]);
+        atomicMax(a.jbox + 3 + threadIdx.x, sbox[3 + threadIdx.x]);
+    }
+}
+
+// Particle m: push, move, deposit; base = the lower corner of its deposit
+// stencil.
+__device__ __forceinline__ void push_deposit(const StepArgs& a, float* xp, int64_t np, float coef, float* jx,
+                                             float* jy, float* jz, int64_t m, int base[3]) {
     const Grid& g = a.g;
     float* px = xp;
     float* py = xp + np;
@@ -103,7 +135,6 @@ __global__ void __launch_bounds__(128) push_deposit_kernel(const StepArgs a, flo
         g1[c] = xn[c] * inv_dx;
     }
     // Esirkepov deposit on a 3-node stencil per axis
-    int base[3];
     float s0[3][3], ds[3][3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -164,6 +195,15 @@ __global__ void __launch_bounds__(128) push_deposit_kernel(const StepArgs a, flo
         xp[c * np + m] = v;
         xp[(3 + c) * np + m] = pn[c];
     }
+}
+
+__global__ void __launch_bounds__(128) push_deposit_kernel(const StepArgs a, float* xp, int64_t np, float coef,
+                                                           float* jx, float* jy, float* jz) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int base[3] = {0, 0, 0};
+    const bool valid = m < np;
+    if (valid) push_deposit(a, xp, np, coef, jx, jy, jz, m, base);
+    if (a.jbox) merge_box(a, valid, base);
 }
 
 }  // namespace
