@@ -151,6 +151,12 @@ def dist_env():
     return rank, world, local
 
 
+def workload_config(w, storage: str) -> dict:
+    """The keys naming the workload, shared by both arms' JSON lines."""
+    return {"workload": w.name, "grid_zyx": [w.nz, w.ny, w.nx], "dx": w.dx, "dt": w.dt, "tau": w.tau,
+            "driver": {"nb_over_n0": w.alpha, "sigma_r": w.sigma_r, "sigma_z": w.sigma_z}, "storage": storage}
+
+
 def oracle_rate(target_seconds: float, shape=(128, 64, 64)):
     """Node-steps per second of the FP64 oracle, as it stands, on a (z, y, x)
     sub-box of the production workload with the same physics, stepped until
@@ -218,8 +224,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": W.production().name, "sample": f"{w.nz}x{w.ny}x{w.nx} sub-box per step",
-                       "parallelism": "host cores"},
+            "config": {**workload_config(W.production(), "f32"),
+                       "sample": f"{w.nz}x{w.ny}x{w.nx} sub-box per step", "parallelism": "host cores"},
             "cpu_baseline": {"value": val, "unit": "GLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
                              "kind": "oracle", "sample": f"{w.nz}x{w.ny}x{w.nx} sub-box of the "
                                                           f"512x256x256 regularized workload, {args.steps} steps"},
@@ -518,9 +524,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": w.name, "grid_zyx": [w.nz, w.ny, w.nx], "dx": w.dx, "dt": w.dt, "tau": w.tau,
-                   "driver": {"nb_over_n0": w.alpha, "sigma_r": w.sigma_r, "sigma_z": w.sigma_z},
-                   "storage": args.storage,
+        "config": {**workload_config(w, args.storage),
                    "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * 76 * (4 if w.storage == W.F32 else 2) * N / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "fluid_block": list(launch_shape), "fluid_variant": fluid_variant},
