@@ -82,6 +82,13 @@ def _create(lib, **changes):
     (dict(moving_window=2), "moving_window"),
     (dict(moving_window=1, boundary=1), "moving window"),
     (dict(moving_window=1, window_z=float("inf")), "window_z"),
+    # maximum sizes: the x-y plane, the z extent and the 32-bit population
+    # offsets (19 Np < 2^32: 512 x 512 x 900 nodes is past it)
+    (dict(nx=1 << 16, ny=1 << 15), "grid too large"),
+    (dict(nz=70000), "grid too large"),
+    (dict(nx=512, ny=512, nz=900), "nodes * 19"),
+    (dict(driver=5), "unknown driver"),
+    (dict(driver=1, moving_window=1), "PIC driver"),
 ])
 def test_invalid_params_rejected(lib, change, needle):
     rc, h, msg = _create(lib, **change)
