@@ -271,6 +271,25 @@ def test_fused_step_diagnostics_two_instances():
             _check_fused(d[i], refs[i])
 
 
+@pytest.mark.parametrize("storage", [W.F32, W.BF16, W.F16])
+@pytest.mark.parametrize("collision", [W.BGK, W.REGULARIZED])
+def test_plasma_at_rest_stays_at_rest(storage, collision):
+    """Degenerate case: no driver, uniform plasma at rest. The momentum
+    lattices, u, E, B and J stay exactly zero (every source term is a product
+    with an exact zero), and n stays n0 up to the rounding of the lattice sum
+    (one FP32 rounding of sum_i w_i n0 per step, 16-bit storage of the
+    resulting deviation)."""
+    w = W.parity_small().replace(nx=20, ny=18, nz=24, alpha=0.0, collision=collision, storage=storage)
+    with lbm.Simulation(w) as sim:
+        sim.step(200)
+        zero = (lbm.FIELD_UX | lbm.FIELD_UY | lbm.FIELD_UZ | lbm.FIELD_EX | lbm.FIELD_EY | lbm.FIELD_EZ |
+                lbm.FIELD_BX | lbm.FIELD_BY | lbm.FIELD_BZ | lbm.FIELD_JX | lbm.FIELD_JY | lbm.FIELD_JZ |
+                lbm.FIELD_PX | lbm.FIELD_PY | lbm.FIELD_PZ)
+        assert int(torch.count_nonzero(sim.fields(zero))) == 0
+        n = sim.fields(lbm.FIELD_N)[0].double()
+        assert float((n - w.n0).abs().max()) <= 200 * 4e-7 * w.n0
+
+
 def test_linecut_and_bubble_length():
     """Line cuts of n and E_z along z at offset r, and the bubble length
     L_b = dz * #(n < 0.95) on the axis (Sec. IV), against the oracle's node
