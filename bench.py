@@ -188,6 +188,19 @@ def cpu_baseline(target_seconds: float = 12.0):
            "kind": "oracle",
            "sample": f"FP64 oracle, {r['box']} sub-box of the 512x256x256 regularized workload, "
                      f"{r['steps']} steps in {r['seconds']:.1f} s"}
+    # the 64x32x32 parity workload (200 steps of BGK with the linear driver) in full
+    import oracle
+    wp = W.parity_small()
+    o = oracle.Oracle(wp.nx, wp.ny, wp.nz, wp.dx, wp.dt, wp.tau, collision=wp.collision, alpha=wp.alpha,
+                      sigma_r=wp.sigma_r, sigma_z=wp.sigma_z, z0=wp.z0)
+    t0 = time.perf_counter()
+    o.step(wp.steps)
+    tp = time.perf_counter() - t0
+    o.close()
+    out["parity_workload_full"] = {"value": wp.nodes * wp.steps / tp / 1e9, "unit": "GLUPS",
+                                   "cores": int(os.environ["OMP_NUM_THREADS"]),
+                                   "sample": f"FP64 oracle, {wp.nz}x{wp.ny}x{wp.nx}, all {wp.steps} steps "
+                                             f"in {tp:.2f} s"}
     try:
         code = ("import sys, json; sys.path.insert(0, %r); import bench; "
                 "print(json.dumps(bench.oracle_rate(4.0, (64, 32, 32))))" % ROOT)

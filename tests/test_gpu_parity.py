@@ -290,6 +290,32 @@ def test_plasma_at_rest_stays_at_rest(storage, collision):
         assert float((n - w.n0).abs().max()) <= 200 * 4e-7 * w.n0
 
 
+@pytest.mark.parametrize("defect", ["nan", "negative"])
+def test_unstable_state_is_reported(defect):
+    """Failure detection on the host side of the ABI: a non-finite population
+    or a node with n < 0 in an imported state makes the FP64 diagnostics
+    return PWFA_ERR_UNSTABLE (-3), both the separate reduction and the fused
+    step diagnostics; the diagnostics themselves are still filled in."""
+    w = W.parity_small().replace(nx=12, ny=10, nz=14, boundary=W.PERIODIC, alpha=0.0)
+    f0 = W.random_populations((w.nz, w.ny, w.nx), seed=3).astype(np.float32)
+    E0 = np.zeros((3, w.nz, w.ny, w.nx), np.float32)
+    z, y, x = 7, 4, 5
+    if defect == "nan":
+        f0[0, 3, z, y, x] = np.nan
+    else:
+        f0[0, :, z, y, x] = -1.0
+    with lbm.Simulation(w) as sim:
+        sim.set_state(f0, E0, E0)
+        with pytest.raises(lbm.LBMError) as e:
+            sim.diag()
+        assert e.value.code == -3
+        d = sim.diag(check=False)
+        assert (d[7] >= 1) if defect == "nan" else (d[5] < 0)
+        with pytest.raises(lbm.LBMError) as e:
+            sim.step_diag(1)
+        assert e.value.code == -3
+
+
 def test_linecut_and_bubble_length():
     """Line cuts of n and E_z along z at offset r, and the bubble length
     L_b = dz * #(n < 0.95) on the axis (Sec. IV), against the oracle's node
