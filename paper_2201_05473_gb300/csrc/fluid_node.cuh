@@ -36,26 +36,58 @@ __device__ __forceinline__ void first_moments(const float (&fl)[kQ], float (&m)[
     m[2] = m2;
 }
 
+// Lattice sums and first moments of one lattice from values s in stored
+// units of a 16-bit form, f = kappa_i s + w_i n0 delta_l0: the rest, axis and
+// diagonal directions are summed apart and weighted once (kappa is 1 for
+// BF16, w_i / 1024 for FP16; sum_i w_i = 1 and sum_i xi_i w_i = 0 give the
+// base terms).
+template <int ST>
+__device__ __forceinline__ void raw_moments(const float (&s)[kQ], float base, float& A, float (&m)[3]) {
+    float sa = 0.0f, sd = 0.0f, ma[3] = {0.0f, 0.0f, 0.0f}, md[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int q = 1; q < kQ; ++q) {
+        float* mc = q <= 6 ? ma : md;
+        if (q <= 6) sa += s[q]; else sd += s[q];
+        if (xi_x(q) > 0) mc[0] += s[q]; else if (xi_x(q) < 0) mc[0] -= s[q];
+        if (xi_y(q) > 0) mc[1] += s[q]; else if (xi_y(q) < 0) mc[1] -= s[q];
+        if (xi_z(q) > 0) mc[2] += s[q]; else if (xi_z(q) < 0) mc[2] -= s[q];
+    }
+    constexpr float k0 = Codec<ST>::kappa(0), ka = Codec<ST>::kappa(1), kd = Codec<ST>::kappa(7);
+    A = base + (k0 * s[0] + ka * sa + kd * sd);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[c] = ka * ma[c] + kd * md[c];
+}
+
 // Everything after the gather: moments, source, collision, stores, current.
-// f holds the pulled populations f^n(x) (of the clamped node when bnd).
-template <int ST, int COLL, bool PER, bool DIAG = false>
+// f holds the pulled populations f^n(x) (of the clamped node when bnd); with
+// RAW (16-bit storage, regularized collision) in stored units, and the
+// post-collision values are formed in stored units too, so that neither the
+// decode nor the encode of the deviations costs a per-value operation.
+template <int ST, int COLL, bool PER, bool DIAG = false, bool RAW = false>
 __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, int z, float (&f)[kL][kQ], bool bnd,
                                               NodeDiag* nd = nullptr) {
     using T = typename Codec<ST>::T;
+    constexpr bool RAWR = RAW && ST != 0 && COLL == 1;
     const Grid& g = a.g;
     const uint32_t node = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x;
 
     float A[kL], inn, beta[3];
-    node_moments(f, a.n_floor, A, inn, beta);
-    const float n = A[0];
     // Regularized: the first moments m_l = sum_i xi_i f_l,i, taken here so
     // that the 76 pulled values are dead before the fields are read (a
     // boundary node recomputes them from its equilibrium below).
     float m[kL][3];
-    if (COLL == 1) {
+    if constexpr (RAWR) {
 #pragma unroll
-        for (int l = 0; l < kL; ++l) first_moments(f[l], m[l]);
+        for (int l = 0; l < kL; ++l) raw_moments<ST>(f[l], l == 0 ? a.n0 : 0.0f, A[l], m[l]);
+        node_velocity(A, a.n_floor, inn, beta);
+    } else {
+        node_moments(f, a.n_floor, A, inn, beta);
+        if (COLL == 1) {
+#pragma unroll
+            for (int l = 0; l < kL; ++l) first_moments(f[l], m[l]);
+        }
     }
+    const float n = A[0];
     if (DIAG) {
         nd->n = A[0];
         nd->a1 = A[1];
@@ -85,15 +117,22 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
     // per-lattice (FP32) or per-pair (16-bit) base pointers, 32-bit offsets
     T* const fo[kL] = {fo0, fo0 + LS, fo0 + 2 * LS, fo0 + 3 * LS};
     const float u[3] = {beta[0] * a.lat, beta[1] * a.lat, beta[2] * a.lat};
+    // (the FP16 stored-unit path keeps phi_i / w_i)
+    constexpr bool UNW = RAWR && ST == 2;
     float phi[kQ];
-    eq_factors(u, phi);
+    eq_factors<!UNW>(u, phi);
     if (!PER && bnd) {
         // Eq. 14: a boundary node holds the equilibrium of the clamped node.
 #pragma unroll
         for (int l = 0; l < kL; ++l) {
+            float fe[kQ];
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) f[l][q] = A[l] * phi[q];
-            if (COLL == 1) first_moments(f[l], m[l]);
+            for (int q = 0; q < kQ; ++q) fe[q] = UNW ? A[l] * (wq(q) * phi[q]) : A[l] * phi[q];
+            if (COLL == 1) first_moments(fe, m[l]);
+            if constexpr (!RAWR) {
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) f[l][q] = fe[q];
+            }
         }
     }
     // Collide in place, lattice pair by lattice pair; FP32 stores each value
@@ -119,18 +158,37 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
                 // f = A phi_i + one or two adds of +-P_k w + F w.
                 const float k3 = 3.0f * (1.0f - om);
                 const float P[3] = {k3 * (m0 - A[l] * u[0]), k3 * (m1 - A[l] * u[1]), k3 * (m2 - A[l] * u[2])};
-                const float Pa[3] = {P[0] * (1.0f / 18.0f), P[1] * (1.0f / 18.0f), P[2] * (1.0f / 18.0f)};
-                const float Pd[3] = {P[0] * (1.0f / 36.0f), P[1] * (1.0f / 36.0f), P[2] * (1.0f / 36.0f)};
-                const float Fa = Fl * (1.0f / 18.0f), Fd = Fl * (1.0f / 36.0f);
+                if constexpr (RAWR && ST == 2) {
+                    // FP16 stores (f - w_i n0 delta_l0) 1024 / w_i
+                    //   = 1024 (A phi_i / w_i + xi_i . P + F dt - n0 delta_l0)
+                    const float A1 = kF16Scale * A[l];
+                    const float P1[3] = {kF16Scale * P[0], kF16Scale * P[1], kF16Scale * P[2]};
+                    const float G1 = kF16Scale * (Fl - (l == 0 ? a.n0 : 0.0f));
 #pragma unroll
-                for (int q = 0; q < kQ; ++q) {
-                    const int nz = (xi_x(q) != 0) + (xi_y(q) != 0) + (xi_z(q) != 0);
-                    const float* Pw = nz == 2 ? Pd : Pa;
-                    float s = nz == 0 ? Fl * (1.0f / 3.0f) : (nz == 2 ? Fd : Fa);
-                    if (xi_x(q) > 0) s += Pw[0]; else if (xi_x(q) < 0) s -= Pw[0];
-                    if (xi_y(q) > 0) s += Pw[1]; else if (xi_y(q) < 0) s -= Pw[1];
-                    if (xi_z(q) > 0) s += Pw[2]; else if (xi_z(q) < 0) s -= Pw[2];
-                    f[l][q] = fmaf(A[l], phi[q], s);
+                    for (int q = 0; q < kQ; ++q) {
+                        float s = G1;
+                        if (xi_x(q) > 0) s += P1[0]; else if (xi_x(q) < 0) s -= P1[0];
+                        if (xi_y(q) > 0) s += P1[1]; else if (xi_y(q) < 0) s -= P1[1];
+                        if (xi_z(q) > 0) s += P1[2]; else if (xi_z(q) < 0) s -= P1[2];
+                        f[l][q] = fmaf(A1, phi[q], s);
+                    }
+                } else {
+                    // FP32 / BF16 (BF16 stores f - w_i n0 delta_l0: the base
+                    // enters with the source)
+                    const float G = RAWR ? Fl - (l == 0 ? a.n0 : 0.0f) : Fl;
+                    const float Pa[3] = {P[0] * (1.0f / 18.0f), P[1] * (1.0f / 18.0f), P[2] * (1.0f / 18.0f)};
+                    const float Pd[3] = {P[0] * (1.0f / 36.0f), P[1] * (1.0f / 36.0f), P[2] * (1.0f / 36.0f)};
+                    const float Ga = G * (1.0f / 18.0f), Gd = G * (1.0f / 36.0f);
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) {
+                        const int nz = (xi_x(q) != 0) + (xi_y(q) != 0) + (xi_z(q) != 0);
+                        const float* Pw = nz == 2 ? Pd : Pa;
+                        float s = nz == 0 ? G * (1.0f / 3.0f) : (nz == 2 ? Gd : Ga);
+                        if (xi_x(q) > 0) s += Pw[0]; else if (xi_x(q) < 0) s -= Pw[0];
+                        if (xi_y(q) > 0) s += Pw[1]; else if (xi_y(q) < 0) s -= Pw[1];
+                        if (xi_z(q) > 0) s += Pw[2]; else if (xi_z(q) < 0) s -= Pw[2];
+                        f[l][q] = fmaf(A[l], phi[q], s);
+                    }
                 }
             }
             // (stream only: f* = f)
@@ -139,7 +197,11 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
                 for (int q = 0; q < kQ; ++q) Codec<ST>::store(fo[l] + pop_off(q, node), f[l][q], l, q, a.n0);
             }
         }
-        if constexpr (ST != 0) {
+        if constexpr (RAWR) {
+#pragma unroll
+            for (int q = 0; q < kQ; ++q)
+                Codec<ST>::store2raw(fo[2 * pr] + 2 * pop_off(q, node), f[2 * pr][q], f[2 * pr + 1][q]);
+        } else if constexpr (ST != 0) {
 #pragma unroll
             for (int q = 0; q < kQ; ++q)
                 Codec<ST>::store2(fo[2 * pr] + 2 * pop_off(q, node), f[2 * pr][q], f[2 * pr + 1][q], 2 * pr, q, a.n0);
@@ -161,8 +223,10 @@ __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int 
     using T = typename Codec<ST>::T;
     float f[kL][kQ];
     bool bnd;
-    gather<ST, PER>(a.g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, a.src_shift);
-    fluid_compute<ST, COLL, PER, DIAG>(a, x, y, z, f, bnd, nd);
+    // the 16-bit regularized form works in stored units (see fluid_compute)
+    constexpr bool RAW = ST != 0 && COLL == 1;
+    gather<ST, PER, RAW>(a.g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, a.src_shift);
+    fluid_compute<ST, COLL, PER, DIAG, RAW>(a, x, y, z, f, bnd, nd);
 }
 
 }  // namespace pwfa

@@ -77,6 +77,17 @@ template <> struct Codec<1> {
         *reinterpret_cast<__nv_bfloat162*>(p) =
             __floats2bfloat162_rn(v0 - dev_base(l0, q, n0), v1 - dev_base(l0 + 1, q, n0));
     }
+    // stored units: f = kappa(q) s + dev_base (raw access, no conversion)
+    static __host__ __device__ constexpr float kappa(int) { return 1.0f; }
+    static __device__ __forceinline__ void load2raw(const T* p, float& s0, float& s1) {
+        const unsigned int u = __ldg(reinterpret_cast<const unsigned int*>(p));
+        const float2 w = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+        s0 = w.x;
+        s1 = w.y;
+    }
+    static __device__ __forceinline__ void store2raw(T* p, float s0, float s1) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(s0, s1);
+    }
 };
 template <> struct Codec<2> {
     using T = __half;
@@ -97,6 +108,16 @@ template <> struct Codec<2> {
     static __device__ __forceinline__ void store2(T* p, float v0, float v1, int l0, int q, float n0) {
         *reinterpret_cast<__half2*>(p) = __floats2half2_rn((v0 - dev_base(l0, q, n0)) * (kF16Scale / wq(q)),
                                                             (v1 - dev_base(l0 + 1, q, n0)) * (kF16Scale / wq(q)));
+    }
+    static __host__ __device__ constexpr float kappa(int q) { return wq(q) / kF16Scale; }
+    static __device__ __forceinline__ void load2raw(const T* p, float& s0, float& s1) {
+        const unsigned int u = __ldg(reinterpret_cast<const unsigned int*>(p));
+        const float2 w = __half22float2(*reinterpret_cast<const __half2*>(&u));
+        s0 = w.x;
+        s1 = w.y;
+    }
+    static __device__ __forceinline__ void store2raw(T* p, float s0, float s1) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(s0, s1);
     }
 };
 

@@ -22,7 +22,9 @@ __device__ __forceinline__ int64_t src_index(const Grid& g, int x, int y, int z,
 // node by that many nodes: nx*ny pulls from one plane up, which is how a
 // moving-window step reads the moved streaming source (the plane above the
 // box holds fresh plasma).
-template <int ST, bool PER>
+// RAW (16-bit storage): the values are left in stored units (the
+// deviation, scaled for FP16) for a caller that works in those units.
+template <int ST, bool PER, bool RAW = false>
 __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::T* __restrict__ fin,
                                        float n0, int x, int y, int z, float f[kL][kQ], bool& bnd,
                                        uint32_t src_shift = 0) {
@@ -55,6 +57,9 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
         if constexpr (ST == 0) {
 #pragma unroll
             for (int l = 0; l < kL; ++l) f[l][q] = Codec<ST>::load(fl[l] + off, l, q, n0);
+        } else if constexpr (RAW) {
+            Codec<ST>::load2raw(fp[0] + 2 * off, f[0][q], f[1][q]);
+            Codec<ST>::load2raw(fp[1] + 2 * off, f[2][q], f[3][q]);
         } else {
             Codec<ST>::load2(fp[0] + 2 * off, 0, q, n0, f[0][q], f[1][q]);
             Codec<ST>::load2(fp[1] + 2 * off, 2, q, n0, f[2][q], f[3][q]);
@@ -62,10 +67,20 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
     }
 }
 
-// Lattice sums A_l, the reciprocal inn of the floored density and
+// From the lattice sums A_l: the reciprocal inn of the floored density and
 // beta = p / sqrt(1 + p^2), p = A_{1..3} / max(n, n_floor). One division and
 // one reciprocal square root per node (six IEEE divisions and a square root
 // were ~5 % of the fluid kernel's instructions).
+__device__ __forceinline__ void node_velocity(const float A[kL], float n_floor, float& inn, float beta[3]) {
+    inn = 1.0f / (A[0] > n_floor ? A[0] : n_floor);
+    const float p0 = A[1] * inn, p1 = A[2] * inn, p2 = A[3] * inn;
+    const float ig = rsqrtf(1.0f + p0 * p0 + p1 * p1 + p2 * p2);
+    beta[0] = p0 * ig;
+    beta[1] = p1 * ig;
+    beta[2] = p2 * ig;
+}
+
+// Lattice sums A_l of the pulled values, then node_velocity.
 __device__ __forceinline__ void node_moments(const float f[kL][kQ], float n_floor, float A[kL],
                                              float& inn, float beta[3]) {
 #pragma unroll
@@ -75,22 +90,20 @@ __device__ __forceinline__ void node_moments(const float f[kL][kQ], float n_floo
         for (int q = 0; q < kQ; ++q) s += f[l][q];
         A[l] = s;
     }
-    inn = 1.0f / (A[0] > n_floor ? A[0] : n_floor);
-    const float p0 = A[1] * inn, p1 = A[2] * inn, p2 = A[3] * inn;
-    const float ig = rsqrtf(1.0f + p0 * p0 + p1 * p1 + p2 * p2);
-    beta[0] = p0 * ig;
-    beta[1] = p1 * ig;
-    beta[2] = p2 * ig;
+    node_velocity(A, n_floor, inn, beta);
 }
 
 // phi_i = w_i (1 + 3 xi.u + 4.5 (xi.u)^2 - 1.5 u.u): f^eq_{l,i} = A_l phi_i,
 // shared by the four lattices (one advecting velocity, Eq. 4).
+// WEIGHTED = false leaves out the weight: phi_i / w_i.
+template <bool WEIGHTED = true>
 __device__ __forceinline__ void eq_factors(const float u[3], float phi[kQ]) {
     const float base = 1.0f - 1.5f * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
         const float xu = (float)xi_x(q) * u[0] + (float)xi_y(q) * u[1] + (float)xi_z(q) * u[2];
-        phi[q] = wq(q) * (base + 3.0f * xu + 4.5f * xu * xu);
+        const float b = base + 3.0f * xu + 4.5f * xu * xu;
+        phi[q] = WEIGHTED ? wq(q) * b : b;
     }
 }
 

@@ -372,22 +372,21 @@ def test_staged_fluid_kernel(boundary, collision):
 @pytest.mark.parametrize("boundary,collision", [(W.OPEN, W.REGULARIZED), (W.PERIODIC, W.BGK)])
 def test_staged_fluid_kernel_16bit(storage, boundary, collision):
     """The staged kernel on 16-bit storage (38 words of lattice pairs per
-    node through shared memory) against the direct kernel on the same
-    storage: the same words decoded by the same codec and the same per-node
-    arithmetic, on a ragged grid. The two kernels may contract an FP32
-    intermediate differently (one ulp), which now and then flips the 16-bit
-    rounding of a stored population; the bound 2e-5 sits far below the
-    storage error itself (>= 1e-4 against the FP64 oracle) and far above
-    those flips (~1e-6 after 60 steps)."""
+    node through shared memory, decoded to FP32 populations) and the direct
+    kernel (which for the regularized form works in stored units) against the
+    FP64 oracle on a ragged grid, both to the reduced-precision bar of 1e-3
+    for FP16 and 3e-3 for BF16 (whose 8-bit mantissa misses 1e-3 on beta
+    within ~100 steps of the 256x128x128 precision run). Each rounds its FP32 intermediates to 8 or 11 bits in its own way, so the
+    two differ from each other by about the sum of their errors (~4e-4 on
+    E_z for BF16 after 60 steps), not by FP32 rounding."""
     w = W.parity_small().replace(nx=37, ny=22, nz=30, boundary=boundary, collision=collision, alpha=0.5,
                                  z0=-1.0, tau=0.6, storage=storage)
-    with lbm.Simulation(w) as a, lbm.Simulation(w) as b:
-        a.set_launch(64, 2)
-        a.set_fluid_variant(lbm.Simulation.STAGED)
-        b.set_launch(64, 2)
-        a.step(60)
-        b.step(60)
-        m = lbm.FIELD_N | lbm.FIELD_UZ | lbm.FIELD_EZ | lbm.RAW_YEE
-        ga, gb = a.fields(m).double(), b.fields(m).double()
-        for c in range(3):
-            assert float((ga[c] - gb[c]).norm()) <= 2e-5 * float(gb[c].norm())
+    o = make_oracle(w)
+    o.step(60)
+    for variant in (lbm.Simulation.STAGED, lbm.Simulation.DIRECT):
+        with lbm.Simulation(w) as s:
+            s.set_launch(64, 2)
+            s.set_fluid_variant(variant)
+            assert s.get_fluid_variant() == variant
+            s.step(60)
+            compare(o, s, tol=1e-3 if storage == W.F16 else 3e-3)
