@@ -491,7 +491,7 @@ def run_ours(args):
         batch_line = None
         if not args.no_extra and args.only in ("", "batched"):
             torch.cuda.empty_cache()
-            ws = W.batched_scan(64, seed=0)
+            ws = W.batched_scan(args.batch_instances, seed=0)
             tot = sum(x.nodes for x in ws)
             sb = lbm.Simulation(ws, stream=stream)
             sb.step(args.warmup + (args.warmup % 2))
@@ -623,6 +623,8 @@ def main():
                                                  "(profiling captures)")
     ap.add_argument("--no-extra", action="store_true", help="skip the BF16/FP16 and adjoint lines")
     ap.add_argument("--adjoint-steps", type=int, default=500)
+    ap.add_argument("--batch-instances", type=int, default=64,
+                    help="instances of the batched parameter scan (fewer: a small case for profiling captures)")
     ap.add_argument("--only", default="", choices=["", "storage", "bgk", "adjoint", "batched", "window", "axisymmetric", "pic"],
                     help="with a small --steps: run the main pass and one extra section (profiling captures)")
     ap.add_argument("--report", default="", choices=["", "precision"],
