@@ -52,7 +52,8 @@ extern "C" {
 #define PWFA_ERR_PARAM (-1)    /* invalid argument or parameter set */
 #define PWFA_ERR_CUDA (-2)     /* a CUDA runtime call or kernel launch failed */
 #define PWFA_ERR_UNSTABLE (-3) /* diagnostics found a non-finite value or n < 0 */
-#define PWFA_ERR_TIMEOUT (-4)  /* a bounded device-side wait expired */
+#define PWFA_ERR_TIMEOUT (-4)  /* a bounded device-side wait expired (reserved: no kernel of this
+                                  library waits on another, so no call returns it at present) */
 #define PWFA_ERR_ALLOC (-5)    /* device memory allocation failed */
 #define PWFA_ERR_STATE (-6)    /* call not valid in the handle's current state */
 
