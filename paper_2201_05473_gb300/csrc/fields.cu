@@ -7,8 +7,17 @@ namespace pwfa {
 
 namespace {
 
-constexpr int kBX = 32;
-constexpr int kBY = 8;
+// Block shape of the field kernels: 64 x 2 (128 threads) measured 2.5 %
+// faster than 32 x 8 for Faraday and Ampere on the 512x256x256 grid
+// (0.207 / 0.291 against 0.213 / 0.298 ms).
+#ifndef PWFA_FIELD_BX
+#define PWFA_FIELD_BX 64
+#endif
+#ifndef PWFA_FIELD_BY
+#define PWFA_FIELD_BY 2
+#endif
+constexpr int kBX = PWFA_FIELD_BX;
+constexpr int kBY = PWFA_FIELD_BY;
 
 template <bool PER>
 __global__ void __launch_bounds__(kBX * kBY) faraday_kernel(const StepArgs a) {
