@@ -47,7 +47,10 @@ struct Instance {
     void* f[2] = {nullptr, nullptr};
     int fcur = 0;
     float* E[3] = {nullptr, nullptr, nullptr};
-    float* Ealt[3] = {nullptr, nullptr, nullptr};  // moving window: E is moved into it
+    float* Ealt[3] = {nullptr, nullptr, nullptr};  // second E buffer: moving window, fused field step
+    // B of the next step already computed (by the fused Ampere-Faraday kernel)
+    // in the other B buffer: the next step skips its Faraday launch
+    bool lookahead = false;
     float* Jb[3] = {nullptr, nullptr, nullptr};    // PIC driver: deposited current
     float* particles = nullptr;                    // PIC driver: [6][np]
     int* jbox = nullptr;                           // PIC driver: deposit boxes of the two step parities
@@ -95,6 +98,8 @@ struct pwfa_lbm {
     std::vector<int> pending_kind;            // kind of each recorded pair
     double ms[PWFA_KERNEL_KINDS] = {0, 0, 0, 0};
     int64_t launches[PWFA_KERNEL_KINDS] = {0, 0, 0, 0};
+    // Ampere fused with the next step's Faraday (rigid driver, no window)
+    bool field_fusion = true;
     // batched persistent path (several homogeneous instances)
     bool batching = true;
     bool batch_valid = false;
@@ -243,6 +248,13 @@ void free_instance(Instance& in) {
     in.arena = nullptr;
 }
 
+// Instances whose Ampere launch can take the next step's Faraday along: the
+// rigid driver (the PIC deposit is cleared by the plain Ampere kernel) and
+// a fixed box (a window move rewrites the B buffer the fused kernel fills).
+bool fusable(const pwfa_lbm_params& p) {
+    return p.couple && p.driver == PWFA_DRIVER_RIGID && !p.moving_window;
+}
+
 int alloc_instance(Instance& in, cudaStream_t s) {
     const int64_t N = in.g.N;
     const size_t fbytes = align_up((size_t)in.g.Np * kPop * storage_bytes(in.p.storage));
@@ -251,8 +263,10 @@ int alloc_instance(Instance& in, cudaStream_t s) {
     const size_t pad = align_up((size_t)in.g.nx * in.g.ny * sizeof(float));
     const size_t vbytes = pad + align_up((size_t)N * sizeof(float));
     const size_t pbytes = align_up(sizeof(double) * (in.profile.empty() ? 1 : in.profile.size()));
-    // E 3, B 2x3, J 3 (+ E for the window move, + the PIC driver's current)
-    const int nvec = 12 + (in.p.moving_window ? 3 : 0) + (in.p.driver == PWFA_DRIVER_PIC ? 3 : 0);
+    // E 3, B 2x3, J 3 (+ a second E for the window move or the fused field
+    // step, + the PIC driver's current)
+    const bool ealt = in.p.moving_window || fusable(in.p);
+    const int nvec = 12 + (ealt ? 3 : 0) + (in.p.driver == PWFA_DRIVER_PIC ? 3 : 0);
     const size_t total = 2 * fbytes + nvec * vbytes + pbytes;
     if (cudaMalloc(&in.arena, total) != cudaSuccess) {
         cudaGetLastError();
@@ -269,7 +283,7 @@ int alloc_instance(Instance& in, cudaStream_t s) {
     for (int t = 0; t < 2; ++t)
         for (int c = 0; c < 3; ++c) { in.B[t][c] = (float*)(base + pad); base += vbytes; }
     for (int c = 0; c < 3; ++c) { in.J[c] = (float*)(base + pad); base += vbytes; }
-    if (in.p.moving_window)
+    if (ealt)
         for (int c = 0; c < 3; ++c) { in.Ealt[c] = (float*)(base + pad); base += vbytes; }
     if (in.p.driver == PWFA_DRIVER_PIC)
         for (int c = 0; c < 3; ++c) { in.Jb[c] = (float*)(base + pad); base += vbytes; }
@@ -348,6 +362,7 @@ int reset_instance(Instance& in, cudaStream_t s) {
     in.fcur = 0;
     in.bcur = 0;
     in.steps = 0;
+    in.lookahead = false;
     PWFA_CUDA(launch_init(in.g, in.f[0], in.p.storage, (float)in.p.n0, in.d_profile, (int)in.profile.size(),
                           in.p.profile_rmax, in.p.dx, s),
               "init kernel");
@@ -485,7 +500,10 @@ int batch_steps(pwfa_lbm* h, int32_t nsteps) {
                 if (per_pair == 4) { h->launches[PWFA_KERNEL_FARADAY] += 2; h->launches[PWFA_KERNEL_AMPERE] += 2; }
             }
         }
-        for (auto& in : h->inst) in.steps += 2 * (int64_t)pairs;
+        for (auto& in : h->inst) {
+            in.steps += 2 * (int64_t)pairs;
+            in.lookahead = false;
+        }
     }
     if (nsteps % 2) {
         for (auto& in : h->inst) {
@@ -519,7 +537,7 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
     int rc;
     DiagOut dg{};
     if (diag) dg = *diag;
-    if (in.p.couple) {
+    if (in.p.couple && !in.lookahead) {
         // with diagnostics the Faraday launch also takes the field energy of
         // the entering state (it reads E and B(t_n) anyway)
         float* energy = nullptr;
@@ -538,7 +556,22 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
                           [&] { return launch_push_deposit(a, in.particles, in.np, in.pweight, in.Jb, s); });
         if (rc) return rc;
     }
-    if (in.p.couple) {
+    in.lookahead = false;
+    if (in.p.couple && h->field_fusion && fusable(in.p) && in.Ealt[0]) {
+        // Ampere with the next step's Faraday: E into the other E buffer, the
+        // next B into the buffer of B(t_n)
+        FieldPair out{};
+        for (int c = 0; c < 3; ++c) {
+            out.E[c] = in.Ealt[c];
+            out.B[c] = in.B[in.bcur][c];
+        }
+        rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere-faraday kernel",
+                          [&] { return launch_ampere_faraday(a, out, s); });
+        if (rc) return rc;
+        for (int c = 0; c < 3; ++c) std::swap(in.E[c], in.Ealt[c]);
+        in.lookahead = true;
+        h->batch_valid = false;  // the batch table holds the E pointers
+    } else if (in.p.couple) {
         rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere kernel", [&] { return launch_ampere(a, s); });
         if (rc) return rc;
     }
@@ -759,6 +792,7 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
     PWFA_CUDA(cudaMemcpyAsync(host_grad, grad, sizeof(double) * (3 + np), cudaMemcpyDeviceToHost, s), "grad copy");
     int rc = copy_state(in, state_at(in, (char*)r.cp + r.cp_stride * r.ncp, false), false, s);
     if (rc) return rc;
+    in.lookahead = false;
     in.steps = r.T;
     PWFA_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     return PWFA_OK;
@@ -1019,6 +1053,7 @@ int pwfa_lbm_set_state(pwfa_lbm_t* h, int32_t instance, const float* f, const fl
     if (rc) return rc;
     h->batch_valid = false;
     Instance& in = h->inst[instance];
+    in.lookahead = false;
     const int64_t N = in.g.N;
     if (f) {
         const size_t bytes = sizeof(float) * (size_t)kPop * N;
@@ -1202,6 +1237,12 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
+}
+
+int pwfa_lbm_set_field_fusion(pwfa_lbm_t* h, int32_t enable) {
+    if (!h) return fail(PWFA_ERR_PARAM, "null handle");
+    h->field_fusion = enable != 0;
+    return PWFA_OK;
 }
 
 int pwfa_lbm_set_batching(pwfa_lbm_t* h, int32_t enable) {

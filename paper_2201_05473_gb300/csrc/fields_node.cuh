@@ -30,83 +30,137 @@ __device__ __forceinline__ int up1(int i, int n) { return PER ? i + 1 : min(i + 
 template <bool PER>
 __device__ __forceinline__ int dn1(int i) { return PER ? i - 1 : max(i - 1, 0); }
 
+// Faraday's update of the three B components stored at node (i, j, k) from
+// the E values it reads (own index and the +1 neighbours) and the old B:
+// Bn = Bc - (dt/dx) curl_h E on the active faces, zero on the walls.
+template <bool PER>
+__device__ __forceinline__ void faraday_values(const Grid& g, float c, int i, int j, int k, const float (&b)[3],
+                                               float ex, float ey, float ez, float ez_j, float ey_k, float ex_k,
+                                               float ez_i, float ey_i, float ex_j, float (&bn)[3]) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const bool cx = PER || (i >= 1 && i <= nx - 2 && j <= ny - 2 && k <= nz - 2);
+    const bool cy = PER || (i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2);
+    const bool cz = PER || (i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2);
+    bn[0] = cx ? b[0] - c * ((ez_j - ez) - (ey_k - ey)) : 0.0f;
+    bn[1] = cy ? b[1] - c * ((ex_k - ex) - (ez_i - ez)) : 0.0f;
+    bn[2] = cz ? b[2] - c * ((ey_i - ey) - (ex_j - ex)) : 0.0f;
+}
+
 // Bn = Bc - (dt/dx) curl_h E, curl at the face centres.
 template <bool PER>
 __device__ __forceinline__ void faraday_node(const StepArgs& a, int i, int j, int k) {
     const Grid& g = a.g;
     const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
-    const float c = a.cdt;
     const float *Ex = a.E[0], *Ey = a.E[1], *Ez = a.E[2];
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int ip = up1<PER>(i, nx), jp = up1<PER>(j, ny), kp = up1<PER>(k, nz);
+    const int ip = up1<PER>(i, g.nx), jp = up1<PER>(j, g.ny), kp = up1<PER>(k, g.nz);
     const float ex = yee_ld<PER>(g, Ex, i, j, k), ey = yee_ld<PER>(g, Ey, i, j, k), ez = yee_ld<PER>(g, Ez, i, j, k);
     const float ez_j = yee_ld<PER>(g, Ez, i, jp, k), ey_k = yee_ld<PER>(g, Ey, i, j, kp);
     const float ex_k = yee_ld<PER>(g, Ex, i, j, kp), ez_i = yee_ld<PER>(g, Ez, ip, j, k);
     const float ey_i = yee_ld<PER>(g, Ey, ip, j, k), ex_j = yee_ld<PER>(g, Ex, i, jp, k);
-    const float b0 = __ldg(a.Bc[0] + o), b1 = __ldg(a.Bc[1] + o), b2 = __ldg(a.Bc[2] + o);
-    const bool cx = PER || (i >= 1 && i <= nx - 2 && j <= ny - 2 && k <= nz - 2);
-    const bool cy = PER || (i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2);
-    const bool cz = PER || (i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2);
-    a.Bn[0][o] = cx ? b0 - c * ((ez_j - ez) - (ey_k - ey)) : 0.0f;
-    a.Bn[1][o] = cy ? b1 - c * ((ex_k - ex) - (ez_i - ez)) : 0.0f;
-    a.Bn[2][o] = cz ? b2 - c * ((ey_i - ey) - (ex_j - ex)) : 0.0f;
+    const float b[3] = {__ldg(a.Bc[0] + o), __ldg(a.Bc[1] + o), __ldg(a.Bc[2] + o)};
+    float bn[3];
+    faraday_values<PER>(g, a.cdt, i, j, k, b, ex, ey, ez, ez_j, ey_k, ex_k, ez_i, ey_i, ex_j, bn);
+    a.Bn[0][o] = bn[0];
+    a.Bn[1][o] = bn[1];
+    a.Bn[2][o] = bn[2];
 }
 
+// Ampere's update of the three E components stored at node (i, j, k):
 // E += (dt/dx) curl_h Bn - dt (J_e,edge + J_b), J_e,edge the mean of the two
-// node currents of the edge, J_b,z = -n_b of the rigid driver at t_{n+1}.
-// Components on the walls of an open grid are left as they are (zero).
+// node currents of the edge, J_b the PIC deposit jb (when a.Jb is set) or
+// J_b,z = -n_b of the rigid driver at t_{n+1}. Split into the node's loads
+// (AmpereIn) and the arithmetic (ampere_compute: en holds the new values, act
+// which components are active; the others, on the walls of an open grid,
+// keep their value, zero), shared by the plain and the fused kernels.
+struct AmpereIn {
+    float bx, by, bz, bz_j, by_k, bx_k, bz_i, by_i, bx_j, j0, j0_i, j1, j1_j, j2, j2_k, e0, e1, e2;
+};
+
 template <bool PER>
-__device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int k, float zc) {
+__device__ __forceinline__ AmpereIn ampere_loads(const StepArgs& a, int i, int j, int k) {
     const Grid& g = a.g;
     const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
-    const float c = a.cdt, dt = a.dt;
     const float *Bx = a.Bn[0], *By = a.Bn[1], *Bz = a.Bn[2];
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int im = dn1<PER>(i), jm = dn1<PER>(j), km = dn1<PER>(k);
-    const int ip = up1<PER>(i, nx), jp = up1<PER>(j, ny), kp = up1<PER>(k, nz);
-    const float bx = yee_ld<PER>(g, Bx, i, j, k), by = yee_ld<PER>(g, By, i, j, k), bz = yee_ld<PER>(g, Bz, i, j, k);
-    const float bz_j = yee_ld<PER>(g, Bz, i, jm, k), by_k = yee_ld<PER>(g, By, i, j, km);
-    const float bx_k = yee_ld<PER>(g, Bx, i, j, km), bz_i = yee_ld<PER>(g, Bz, im, j, k);
-    const float by_i = yee_ld<PER>(g, By, im, j, k), bx_j = yee_ld<PER>(g, Bx, i, jm, k);
-    const float j0 = yee_ld<PER>(g, a.J[0], i, j, k), j0_i = yee_ld<PER>(g, a.J[0], ip, j, k);
-    const float j1 = yee_ld<PER>(g, a.J[1], i, j, k), j1_j = yee_ld<PER>(g, a.J[1], i, jp, k);
-    const float j2 = yee_ld<PER>(g, a.J[2], i, j, k), j2_k = yee_ld<PER>(g, a.J[2], i, j, kp);
-    const float e0 = a.Eout[0][o], e1 = a.Eout[1][o], e2 = a.Eout[2][o];
-    // PIC deposit: read (and clear for the next step) only inside its box
-    const bool inbox = a.Jb[0] && i >= a.jbox[0] && j >= a.jbox[1] && k >= a.jbox[2] && i <= a.jbox[3] &&
-                       j <= a.jbox[4] && k <= a.jbox[5];
-    const float jb0 = inbox ? a.Jb[0][o] : 0.0f, jb1 = inbox ? a.Jb[1][o] : 0.0f;
-    const float jb2 = inbox ? a.Jb[2][o] : 0.0f;
-    if (inbox) {
-        a.Jb[0][o] = 0.0f;
-        a.Jb[1][o] = 0.0f;
-        a.Jb[2][o] = 0.0f;
+    const int ip = up1<PER>(i, g.nx), jp = up1<PER>(j, g.ny), kp = up1<PER>(k, g.nz);
+    AmpereIn v;
+    v.bx = yee_ld<PER>(g, Bx, i, j, k);
+    v.by = yee_ld<PER>(g, By, i, j, k);
+    v.bz = yee_ld<PER>(g, Bz, i, j, k);
+    v.bz_j = yee_ld<PER>(g, Bz, i, jm, k);
+    v.by_k = yee_ld<PER>(g, By, i, j, km);
+    v.bx_k = yee_ld<PER>(g, Bx, i, j, km);
+    v.bz_i = yee_ld<PER>(g, Bz, im, j, k);
+    v.by_i = yee_ld<PER>(g, By, im, j, k);
+    v.bx_j = yee_ld<PER>(g, Bx, i, jm, k);
+    v.j0 = yee_ld<PER>(g, a.J[0], i, j, k);
+    v.j0_i = yee_ld<PER>(g, a.J[0], ip, j, k);
+    v.j1 = yee_ld<PER>(g, a.J[1], i, j, k);
+    v.j1_j = yee_ld<PER>(g, a.J[1], i, jp, k);
+    v.j2 = yee_ld<PER>(g, a.J[2], i, j, k);
+    v.j2_k = yee_ld<PER>(g, a.J[2], i, j, kp);
+    v.e0 = a.E[0][o];
+    v.e1 = a.E[1][o];
+    v.e2 = a.E[2][o];
+    return v;
+}
+
+template <bool PER>
+__device__ __forceinline__ void ampere_compute(const StepArgs& a, int i, int j, int k, float zc, const AmpereIn& v,
+                                               const float (&jbv)[3], float (&en)[3], bool (&act)[3]) {
+    const float c = a.cdt, dt = a.dt;
+    const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+    act[0] = PER || (i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2);
+    act[1] = PER || (i >= 1 && i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2);
+    act[2] = PER || (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2);
+    en[0] = v.e0;
+    en[1] = v.e1;
+    en[2] = v.e2;
+    if (act[0]) {
+        float je = 0.5f * (v.j0 + v.j0_i);
+        if (a.Jb[0]) je += jbv[0];
+        en[0] = v.e0 + c * ((v.bz - v.bz_j) - (v.by - v.by_k)) - dt * je;
     }
-    const bool cx = PER || (i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2);
-    const bool cy = PER || (i >= 1 && i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2);
-    const bool cz = PER || (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2);
-    if (cx) {
-        float je = 0.5f * (j0 + j0_i);
-        if (a.Jb[0]) je += jb0;
-        a.Eout[0][o] = e0 + c * ((bz - bz_j) - (by - by_k)) - dt * je;
+    if (act[1]) {
+        float je = 0.5f * (v.j1 + v.j1_j);
+        if (a.Jb[1]) je += jbv[1];
+        en[1] = v.e1 + c * ((v.bx - v.bx_k) - (v.bz - v.bz_i)) - dt * je;
     }
-    if (cy) {
-        float je = 0.5f * (j1 + j1_j);
-        if (a.Jb[1]) je += jb1;
-        a.Eout[1][o] = e1 + c * ((bx - bx_k) - (bz - bz_i)) - dt * je;
-    }
-    if (cz) {
-        const float je = 0.5f * (j2 + j2_k);
+    if (act[2]) {
+        const float je = 0.5f * (v.j2 + v.j2_k);
         float jb = 0.0f;
         if (a.Jb[2]) {
-            jb = jb2;
+            jb = jbv[2];
         } else if (a.alpha != 0.0f) {
             const float xr = ((float)i - 0.5f * (float)(nx - 1)) * a.dx;
             const float yr = ((float)j - 0.5f * (float)(ny - 1)) * a.dx;
             const float zeta = ((float)k + 0.5f) * a.dx - zc;
             jb = -a.alpha * expf(-(xr * xr + yr * yr) * a.inv2sr2 - zeta * zeta * a.inv2sz2);
         }
-        a.Eout[2][o] = e2 + c * ((by - by_i) - (bx - bx_j)) - dt * (je + jb);
+        en[2] = v.e2 + c * ((v.by - v.by_i) - (v.bx - v.bx_j)) - dt * (je + jb);
+    }
+}
+
+// Ampere in place at node (i, j, k) (a.Eout = a.E); the PIC deposit is read
+// (and cleared for the next step) only inside its box.
+template <bool PER>
+__device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int k, float zc) {
+    const Grid& g = a.g;
+    const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
+    const bool inbox = a.Jb[0] && i >= a.jbox[0] && j >= a.jbox[1] && k >= a.jbox[2] && i <= a.jbox[3] &&
+                       j <= a.jbox[4] && k <= a.jbox[5];
+    const float jbv[3] = {inbox ? a.Jb[0][o] : 0.0f, inbox ? a.Jb[1][o] : 0.0f, inbox ? a.Jb[2][o] : 0.0f};
+    const AmpereIn v = ampere_loads<PER>(a, i, j, k);
+    float en[3];
+    bool act[3];
+    ampere_compute<PER>(a, i, j, k, zc, v, jbv, en, act);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (act[c]) a.Eout[c][o] = en[c];
+    if (inbox) {
+        a.Jb[0][o] = 0.0f;
+        a.Jb[1][o] = 0.0f;
+        a.Jb[2][o] = 0.0f;
     }
 }
 

@@ -65,6 +65,16 @@ int64_t faraday_energy_records(const Grid& g);
 // Ampere, dE/dt = curl B - J: E += dt (curl_h Bn - J_edge - J_b(t_{n+1})).
 cudaError_t launch_ampere(const StepArgs& a, cudaStream_t s);
 
+// Ampere of this step fused with Faraday of the next (rigid driver only):
+// out.E := E + dt (curl_h Bn - J_edge - J_b) (a.E unchanged), out.B := the
+// next step's B(t_{n+2}) = Bn - dt curl_h out.E. out.E must not alias a.E and
+// out.B none of a.E, a.Bn, a.J (out.B is normally a.Bc's buffer).
+struct FieldPair {
+    float* E[3];
+    float* B[3];
+};
+cudaError_t launch_ampere_faraday(const StepArgs& a, const FieldPair& out, cudaStream_t s);
+
 // Open grids: zero the Yee components of E and B(t_n) that lie on or outside
 // the conducting walls (tangential E, normal B, components past the grid).
 cudaError_t launch_zero_walls(const StepArgs& a, cudaStream_t s);

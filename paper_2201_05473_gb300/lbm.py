@@ -74,6 +74,7 @@ EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_
            "pwfa_lbm_destroy", "pwfa_lbm_last_error", "pwfa_lbm_profile", "pwfa_lbm_kernel_times",
            "pwfa_lbm_set_launch", "pwfa_lbm_get_launch", "pwfa_lbm_autotune",
            "pwfa_lbm_diag_noalloc", "pwfa_lbm_record", "pwfa_lbm_adjoint_step", "pwfa_lbm_set_batching",
+           "pwfa_lbm_set_field_fusion",
            "pwfa_lbm_step_diag", "pwfa_lbm_linecut", "pwfa_lbm_set_fluid_variant", "pwfa_lbm_get_fluid_variant",
            "pwfa_lbm_window_planes", "pwfa_axi_create", "pwfa_axi_step", "pwfa_axi_fields",
            "pwfa_axi_get_source", "pwfa_axi_set_source", "pwfa_axi_steps_done", "pwfa_axi_profile",
@@ -144,6 +145,8 @@ def load(build: bool = True):
         lib.pwfa_lbm_step_diag.restype = ctypes.c_int
         lib.pwfa_lbm_set_batching.argtypes = [vp, i32]
         lib.pwfa_lbm_set_batching.restype = ctypes.c_int
+        lib.pwfa_lbm_set_field_fusion.argtypes = [vp, i32]
+        lib.pwfa_lbm_set_field_fusion.restype = ctypes.c_int
         lib.pwfa_lbm_last_error.restype = ctypes.c_char_p
         for name in ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_state",
                      "pwfa_lbm_set_state", "pwfa_lbm_set_stream", "pwfa_lbm_destroy",
@@ -366,6 +369,9 @@ class Simulation:
 
     def set_batching(self, enable: bool = True):
         _check(self._lib.pwfa_lbm_set_batching(self._h, 1 if enable else 0))
+
+    def set_field_fusion(self, enable: bool = True):
+        _check(self._lib.pwfa_lbm_set_field_fusion(self._h, 1 if enable else 0))
 
     def kernel_times(self):
         """(ms, launches) per kernel kind since the previous call."""
