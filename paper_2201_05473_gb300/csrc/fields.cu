@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kBX * kBY) ampere_kernel(const StepArgs a) {
 constexpr int kAFX = 32, kAFY = PWFA_AF_Y, kAFZ = PWFA_AF_Z;
 
 template <bool PER>
-__global__ void __launch_bounds__(kAFX * kAFY) ampere_faraday_kernel(const StepArgs a, const FieldPair out) {
+__global__ void __launch_bounds__(kAFX * kAFY, 5) ampere_faraday_kernel(const StepArgs a, const FieldPair out) {
     const Grid& g = a.g;
     __shared__ float sE[2][3][kAFY][kAFX];
     const int tx = threadIdx.x, ty = threadIdx.y;

@@ -52,11 +52,21 @@ __device__ __forceinline__ void faraday_node(const StepArgs& a, int i, int j, in
     const Grid& g = a.g;
     const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
     const float *Ex = a.E[0], *Ey = a.E[1], *Ez = a.E[2];
-    const int ip = up1<PER>(i, g.nx), jp = up1<PER>(j, g.ny), kp = up1<PER>(k, g.nz);
-    const float ex = yee_ld<PER>(g, Ex, i, j, k), ey = yee_ld<PER>(g, Ey, i, j, k), ez = yee_ld<PER>(g, Ez, i, j, k);
-    const float ez_j = yee_ld<PER>(g, Ez, i, jp, k), ey_k = yee_ld<PER>(g, Ey, i, j, kp);
-    const float ex_k = yee_ld<PER>(g, Ex, i, j, kp), ez_i = yee_ld<PER>(g, Ez, ip, j, k);
-    const float ey_i = yee_ld<PER>(g, Ey, ip, j, k), ex_j = yee_ld<PER>(g, Ex, i, jp, k);
+    // +1 neighbours: wrapped (periodic) or clamped into the grid as offsets
+    int64_t pi, pj, pk;
+    if (PER) {
+        pi = wrapi(i + 1, g.nx) - i;
+        pj = (int64_t)(wrapi(j + 1, g.ny) - j) * g.nx;
+        pk = (int64_t)(wrapi(k + 1, g.nz) - k) * g.nx * g.ny;
+    } else {
+        pi = i < g.nx - 1 ? 1 : 0;
+        pj = j < g.ny - 1 ? (int64_t)g.nx : 0;
+        pk = k < g.nz - 1 ? (int64_t)g.nx * g.ny : 0;
+    }
+    const float ex = __ldg(Ex + o), ey = __ldg(Ey + o), ez = __ldg(Ez + o);
+    const float ez_j = __ldg(Ez + o + pj), ey_k = __ldg(Ey + o + pk);
+    const float ex_k = __ldg(Ex + o + pk), ez_i = __ldg(Ez + o + pi);
+    const float ey_i = __ldg(Ey + o + pi), ex_j = __ldg(Ex + o + pj);
     const float b[3] = {__ldg(a.Bc[0] + o), __ldg(a.Bc[1] + o), __ldg(a.Bc[2] + o)};
     float bn[3];
     faraday_values<PER>(g, a.cdt, i, j, k, b, ex, ey, ez, ez_j, ey_k, ex_k, ez_i, ey_i, ex_j, bn);
@@ -81,24 +91,40 @@ __device__ __forceinline__ AmpereIn ampere_loads(const StepArgs& a, int i, int j
     const Grid& g = a.g;
     const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
     const float *Bx = a.Bn[0], *By = a.Bn[1], *Bz = a.Bn[2];
-    const int im = dn1<PER>(i), jm = dn1<PER>(j), km = dn1<PER>(k);
-    const int ip = up1<PER>(i, g.nx), jp = up1<PER>(j, g.ny), kp = up1<PER>(k, g.nz);
     AmpereIn v;
-    v.bx = yee_ld<PER>(g, Bx, i, j, k);
-    v.by = yee_ld<PER>(g, By, i, j, k);
-    v.bz = yee_ld<PER>(g, Bz, i, j, k);
-    v.bz_j = yee_ld<PER>(g, Bz, i, jm, k);
-    v.by_k = yee_ld<PER>(g, By, i, j, km);
-    v.bx_k = yee_ld<PER>(g, Bx, i, j, km);
-    v.bz_i = yee_ld<PER>(g, Bz, im, j, k);
-    v.by_i = yee_ld<PER>(g, By, im, j, k);
-    v.bx_j = yee_ld<PER>(g, Bx, i, jm, k);
-    v.j0 = yee_ld<PER>(g, a.J[0], i, j, k);
-    v.j0_i = yee_ld<PER>(g, a.J[0], ip, j, k);
-    v.j1 = yee_ld<PER>(g, a.J[1], i, j, k);
-    v.j1_j = yee_ld<PER>(g, a.J[1], i, jp, k);
-    v.j2 = yee_ld<PER>(g, a.J[2], i, j, k);
-    v.j2_k = yee_ld<PER>(g, a.J[2], i, j, kp);
+    if (PER) {
+        const int im = dn1<PER>(i), jm = dn1<PER>(j), km = dn1<PER>(k);
+        const int ip = up1<PER>(i, g.nx), jp = up1<PER>(j, g.ny), kp = up1<PER>(k, g.nz);
+        v.bz_j = yee_ld<PER>(g, Bz, i, jm, k);
+        v.by_k = yee_ld<PER>(g, By, i, j, km);
+        v.bx_k = yee_ld<PER>(g, Bx, i, j, km);
+        v.bz_i = yee_ld<PER>(g, Bz, im, j, k);
+        v.by_i = yee_ld<PER>(g, By, im, j, k);
+        v.bx_j = yee_ld<PER>(g, Bx, i, jm, k);
+        v.j0_i = yee_ld<PER>(g, a.J[0], ip, j, k);
+        v.j1_j = yee_ld<PER>(g, a.J[1], i, jp, k);
+        v.j2_k = yee_ld<PER>(g, a.J[2], i, j, kp);
+    } else {
+        // neighbours clamped into the grid as index offsets from o
+        const int64_t sx = g.nx, sxy = (int64_t)g.nx * g.ny;
+        const int64_t di = i > 0 ? 1 : 0, dj = j > 0 ? sx : 0, dk = k > 0 ? sxy : 0;
+        const int64_t ui = i < g.nx - 1 ? 1 : 0, uj = j < g.ny - 1 ? sx : 0, uk = k < g.nz - 1 ? sxy : 0;
+        v.bz_j = __ldg(Bz + o - dj);
+        v.by_k = __ldg(By + o - dk);
+        v.bx_k = __ldg(Bx + o - dk);
+        v.bz_i = __ldg(Bz + o - di);
+        v.by_i = __ldg(By + o - di);
+        v.bx_j = __ldg(Bx + o - dj);
+        v.j0_i = __ldg(a.J[0] + o + ui);
+        v.j1_j = __ldg(a.J[1] + o + uj);
+        v.j2_k = __ldg(a.J[2] + o + uk);
+    }
+    v.bx = __ldg(Bx + o);
+    v.by = __ldg(By + o);
+    v.bz = __ldg(Bz + o);
+    v.j0 = __ldg(a.J[0] + o);
+    v.j1 = __ldg(a.J[1] + o);
+    v.j2 = __ldg(a.J[2] + o);
     v.e0 = a.E[0][o];
     v.e1 = a.E[1][o];
     v.e2 = a.E[2][o];
