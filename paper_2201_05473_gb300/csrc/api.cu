@@ -744,17 +744,19 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
                 f.E[c] = E_slot(j, c);
                 f.Bc[c] = B_slot(j, c);
                 f.Bn[c] = B_slot(j + 1, c);
-                f.Eout[c] = last ? in.E[c] : E_slot(j + 1, c);
-                PWFA_CUDA(cudaMemcpyAsync(f.Eout[c], f.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
-                          "E copy");
+                f.Eout[c] = last ? in.E[c] : E_slot(j + 1, c);  // Ampere out of place writes every component
             }
             if (in.p.couple) {
                 int rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(f, s); });
                 if (rc) return rc;
             } else {
-                for (int c = 0; c < 3; ++c)
+                // no Maxwell update: E and B pass through
+                for (int c = 0; c < 3; ++c) {
                     PWFA_CUDA(cudaMemcpyAsync(f.Bn[c], f.Bc[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
                               "B copy");
+                    PWFA_CUDA(cudaMemcpyAsync(f.Eout[c], f.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                              "E copy");
+                }
             }
             int rc = timed_launch(h, PWFA_KERNEL_FLUID, "fluid kernel",
                                   [&] { return launch_fluid(f, in.p.storage, in.p.collision, s); });

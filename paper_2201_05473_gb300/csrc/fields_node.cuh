@@ -167,8 +167,9 @@ __device__ __forceinline__ void ampere_compute(const StepArgs& a, int i, int j, 
     }
 }
 
-// Ampere in place at node (i, j, k) (a.Eout = a.E); the PIC deposit is read
-// (and cleared for the next step) only inside its box.
+// Ampere at node (i, j, k) from a.E into a.Eout (in place when they are the
+// same arrays); the PIC deposit is read (and cleared for the next step) only
+// inside its box.
 template <bool PER>
 __device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int k, float zc) {
     const Grid& g = a.g;
@@ -180,9 +181,11 @@ __device__ __forceinline__ void ampere_node(const StepArgs& a, int i, int j, int
     float en[3];
     bool act[3];
     ampere_compute<PER>(a, i, j, k, zc, v, jbv, en, act);
+    // in place (a.Eout = a.E) only the active components change; out of place
+    // every component is written (the inactive ones keep their value)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-        if (act[c]) a.Eout[c][o] = en[c];
+        if (act[c] || a.Eout[c] != a.E[c]) a.Eout[c][o] = en[c];
     if (inbox) {
         a.Jb[0][o] = 0.0f;
         a.Jb[1][o] = 0.0f;
