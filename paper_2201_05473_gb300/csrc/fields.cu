@@ -1,5 +1,7 @@
-// Yee FDTD field kernels of one step (bodies in fields_node.cuh) and the
-// wall-zeroing helper used after a state import.
+// Yee FDTD field kernels of one step (bodies in fields_node.cuh): Faraday,
+// Ampere (with the PIC deposit box), Ampere fused with the next step's
+// Faraday, the moving window's field move and the wall-zeroing helper used
+// after a state import.
 #include "lbm_kernels.h"
 #include "fields_node.cuh"
 
