@@ -298,13 +298,18 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps);
  * instances one after another with ordinary launches. */
 int pwfa_lbm_set_batching(pwfa_lbm_t* h, int32_t enable);
 
-/* Field-step fusion, on by default. For a coupled instance with the rigid
- * driver and a fixed box, the Ampere update of step n (Eq. 5) runs in one
- * kernel with the Faraday update of step n+1: B(t_n+1) is read once for
- * both, and step n+1 starts without its Faraday launch. Results are those of
- * the separate kernels. The kernel-time kind PWFA_KERNEL_AMPERE then covers
- * the fused kernel. enable = 0 keeps the separate launches. */
-int pwfa_lbm_set_field_fusion(pwfa_lbm_t* h, int32_t enable);
+/* Field-step fusion. For a coupled instance with the rigid driver and a
+ * fixed box, the Ampere update of step n (Eq. 5) can run in one kernel with
+ * the Faraday update of step n+1: B(t_n+1) is read once for both, and step
+ * n+1 starts without its Faraday launch. Results are those of the separate
+ * kernels, bit for bit. The kernel-time kind PWFA_KERNEL_AMPERE then covers
+ * the fused kernel. Modes: OFF (separate launches), AUTO (the default: fused
+ * on grids of 4 Mi nodes or more, where it is faster), ON (always);
+ * PWFA_ERR_PARAM for another value. */
+#define PWFA_FUSION_OFF 0
+#define PWFA_FUSION_AUTO 1
+#define PWFA_FUSION_ON 2
+int pwfa_lbm_set_field_fusion(pwfa_lbm_t* h, int32_t mode);
 
 /* Re-target all later work of the handle to another cudaStream_t. */
 int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream);

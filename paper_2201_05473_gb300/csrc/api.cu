@@ -98,8 +98,9 @@ struct pwfa_lbm {
     std::vector<int> pending_kind;            // kind of each recorded pair
     double ms[PWFA_KERNEL_KINDS] = {0, 0, 0, 0};
     int64_t launches[PWFA_KERNEL_KINDS] = {0, 0, 0, 0};
-    // Ampere fused with the next step's Faraday (rigid driver, no window)
-    bool field_fusion = true;
+    // Ampere fused with the next step's Faraday (rigid driver, no window):
+    // PWFA_FUSION_OFF / _AUTO (grids of kFuseMinNodes and more) / _ON
+    int field_fusion = PWFA_FUSION_AUTO;
     // batched persistent path (several homogeneous instances)
     bool batching = true;
     bool batch_valid = false;
@@ -254,6 +255,12 @@ void free_instance(Instance& in) {
 bool fusable(const pwfa_lbm_params& p) {
     return p.couple && p.driver == PWFA_DRIVER_RIGID && !p.moving_window;
 }
+
+// The fused kernel marches 16 planes per block, so small grids give it too
+// few blocks: on the GB300 it was slower up to 192x96x96 (1.8 M nodes: 225
+// against 223 us per step; 64x32x32: 27 against 18 us) and faster from
+// 256x128x128 (4.2 M nodes: 485 against 488 us; 512x256x256: 1.2 %).
+constexpr int64_t kFuseMinNodes = (int64_t)4 << 20;
 
 int alloc_instance(Instance& in, cudaStream_t s) {
     const int64_t N = in.g.N;
@@ -557,7 +564,9 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
         if (rc) return rc;
     }
     in.lookahead = false;
-    if (in.p.couple && h->field_fusion && fusable(in.p) && in.Ealt[0]) {
+    const bool fuse = h->field_fusion == PWFA_FUSION_ON ||
+                      (h->field_fusion == PWFA_FUSION_AUTO && in.g.N >= kFuseMinNodes);
+    if (in.p.couple && fuse && fusable(in.p) && in.Ealt[0]) {
         // Ampere with the next step's Faraday: E into the other E buffer, the
         // next B into the buffer of B(t_n)
         FieldPair out{};
@@ -1241,9 +1250,11 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
     return rc;
 }
 
-int pwfa_lbm_set_field_fusion(pwfa_lbm_t* h, int32_t enable) {
+int pwfa_lbm_set_field_fusion(pwfa_lbm_t* h, int32_t mode) {
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
-    h->field_fusion = enable != 0;
+    if (mode != PWFA_FUSION_OFF && mode != PWFA_FUSION_AUTO && mode != PWFA_FUSION_ON)
+        return fail(PWFA_ERR_PARAM, "unknown field-fusion mode");
+    h->field_fusion = mode;
     return PWFA_OK;
 }
 

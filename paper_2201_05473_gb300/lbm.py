@@ -370,8 +370,12 @@ class Simulation:
     def set_batching(self, enable: bool = True):
         _check(self._lib.pwfa_lbm_set_batching(self._h, 1 if enable else 0))
 
-    def set_field_fusion(self, enable: bool = True):
-        _check(self._lib.pwfa_lbm_set_field_fusion(self._h, 1 if enable else 0))
+    FUSION_OFF, FUSION_AUTO, FUSION_ON = 0, 1, 2
+
+    def set_field_fusion(self, mode: int = 1):
+        """Ampere fused with the next step's Faraday: FUSION_OFF, FUSION_AUTO
+        (large grids; the default) or FUSION_ON."""
+        _check(self._lib.pwfa_lbm_set_field_fusion(self._h, int(mode)))
 
     def kernel_times(self):
         """(ms, launches) per kernel kind since the previous call."""

@@ -326,7 +326,10 @@ def test_fused_field_step(boundary, collision):
     w = W.parity_small().replace(nx=70, ny=23, nz=37, boundary=boundary, collision=collision, alpha=0.5,
                                  z0=-1.0, tau=0.6)
     with lbm.Simulation(w) as a, lbm.Simulation(w) as b:
-        b.set_field_fusion(False)
+        a.set_field_fusion(lbm.Simulation.FUSION_ON)
+        b.set_field_fusion(lbm.Simulation.FUSION_OFF)
+        with pytest.raises(lbm.LBMError):
+            b.set_field_fusion(7)
         for s in (a, b):
             s.set_launch(64, 2)
             s.step(25)
