@@ -548,7 +548,9 @@ def run_ours(args):
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": ncu_traffic(N), "algorithmic_bytes_per_launch": fluid_bytes,
                      "avg_launch_ms": fluid_ms},
-        "kernel_ms_per_step": {k: kms[k] / max(kl[k], 1) for k in kms},
+        "kernel_ms_per_step": {k: kms[k] / max(kl[k], 1) for k in kms if kl[k]},
+        "field_step": ("ampere fused with the next step's faraday (one launch)" if kl.get("faraday", 0) == 0
+                       else "separate faraday and ampere launches"),
         "gpu_launches": int(sum(launches.values())),
         "e2e": {"value": e2e_val, "unit": "GLUPS",
                 "h2d_bytes_per_step": lbm.ctypes.sizeof(lbm.Params) / args.steps,
