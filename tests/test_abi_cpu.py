@@ -112,3 +112,6 @@ def test_null_arguments(lib):
     assert lib.pwfa_lbm_destroy(None) == 0
     assert lib.pwfa_lbm_fields(None, 0, 1, None, 0, None) == -1
     assert lib.pwfa_lbm_steps_done(None, 0) == -1
+    assert lib.pwfa_lbm_set_field_fusion(None, 1) == -1
+    assert lib.pwfa_lbm_set_batching(None, 1) == -1
+    assert lib.pwfa_lbm_step_diag(None, 1, None) == -1
