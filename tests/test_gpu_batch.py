@@ -57,6 +57,25 @@ def test_batched_equals_individual(nsteps):
             assert a.steps_done(i) == sum(nsteps)
 
 
+def test_batched_with_fused_field_steps_between():
+    """Per-instance steps with the fused field step (Ampere with the next
+    step's Faraday, which swaps the E buffers and leaves the next B computed)
+    interleaved with batched pairs, against unbatched steps with separate
+    field kernels: the batch table follows the swapped buffers and the
+    batched Faraday phase recomputes the look-ahead B."""
+    ws = scan(4, seed=5)
+    with lbm.Simulation(ws) as a, lbm.Simulation(ws) as b:
+        a.set_field_fusion(lbm.Simulation.FUSION_ON)
+        b.set_field_fusion(lbm.Simulation.FUSION_OFF)
+        b.set_batching(False)
+        for n in (3, 4, 1, 2, 5):  # odd counts end on a fused per-instance step
+            a.step(n)
+            b.step(n)
+        for i in range(len(ws)):
+            close(a.fields(MASK, instance=i), b.fields(MASK, instance=i), i)
+            assert a.steps_done(i) == 15
+
+
 def test_batched_with_autotuned_shapes_and_state_changes():
     ws = scan(4, seed=3)
     with lbm.Simulation(ws) as a, lbm.Simulation(ws) as b:
