@@ -7,6 +7,8 @@ roofline, on the production workload: 512x256x256 nodes (z, y, x), dx = 0.05
 c/omega_p, non-linear driver n_b/n0 = 1, sigma_z = 0.5, sigma_r = 0.3,
 regularized collision, FP32. Synthetic inputs: the initial condition is the
 paper's cold plasma at rest with a rigid Gaussian driver (no dataset exists).
+The timed steps carry the non-linear wake: the driver starts inside the box
+(z0 = 4 sigma_z) and an untimed prelude of steps forms the wake first.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 run under torchrun: every rank advances its own replica (the path
@@ -32,13 +34,22 @@ from paper_2201_05473_gb300 import workloads as W  # noqa: E402
 METRIC = "GLUPS & %HBM peak, fused fwd and adjoint step, FP32 vs BF16-store"
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
-# Algorithmic bytes per node of the fused fluid kernel (FP32 storage):
-# 76 populations read + 76 written (608 B), E (12 B) and B at t_n and t_{n+1}
-# (24 B) read, node current J (12 B) written.
-FLUID_BYTES_F32 = 76 * 4 * 2 + 12 + 24 + 12
+# Algorithmic bytes per node of the fused fluid kernel: the 76 populations
+# read and written (FP32 608 B, 16-bit 304 B) and the fields E and B read
+# (24 B). The node current it stores (12 B) and the second B level it reads
+# (12 B) are not counted: the method need not store J.
+FLUID_BYTES = {W.F32: 608 + 24, W.BF16: 304 + 24, W.F16: 304 + 24}
 # Algorithmic bytes per node-step of the whole step: populations read+write
 # plus E and B read+write.
 STEP_BYTES = {W.F32: 608 + 48, W.BF16: 304 + 48, W.F16: 304 + 48}
+# Adjoint: per reversed node-step the populations' adjoint read + written
+# (608 B), the forward populations read (304 B), forward E and B read (24 B)
+# and the fields' adjoints read + written (48 B), plus the forward step
+# recomputed from the checkpoint (656 B).
+ADJOINT_BYTES = 984 + 656
+# Untimed steps before the warm-up: the driver, started inside the box at
+# z0 = 4 sigma_z, forms the non-linear wake (min n ~0.4 after 300 steps).
+PRELUDE_STEPS = 300
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fluid_kernel_traffic.json")
 KERNEL_SOURCES = ["paper_2201_05473_gb300/csrc/fluid.cu", "paper_2201_05473_gb300/csrc/fluid_node.cuh",
                   "paper_2201_05473_gb300/csrc/lbm_node.cuh", "paper_2201_05473_gb300/csrc/lbm_device.cuh"]
@@ -154,7 +165,8 @@ def dist_env():
 def workload_config(w, storage: str) -> dict:
     """The keys naming the workload, shared by both arms' JSON lines."""
     return {"workload": w.name, "grid_zyx": [w.nz, w.ny, w.nx], "dx": w.dx, "dt": w.dt, "tau": w.tau,
-            "driver": {"nb_over_n0": w.alpha, "sigma_r": w.sigma_r, "sigma_z": w.sigma_z}, "storage": storage}
+            "driver": {"nb_over_n0": w.alpha, "sigma_r": w.sigma_r, "sigma_z": w.sigma_z, "z0": w.z0},
+            "storage": storage}
 
 
 def oracle_rate(target_seconds: float, shape=(128, 64, 64)):
@@ -164,7 +176,7 @@ def oracle_rate(target_seconds: float, shape=(128, 64, 64)):
     import oracle
     oracle.build()
     nz, ny, nx = shape
-    w = W.production().replace(nx=nx, ny=ny, nz=nz, z0=-1.0)
+    w = W.production_timing().replace(nx=nx, ny=ny, nz=nz)
     o = oracle.Oracle(w.nx, w.ny, w.nz, w.dx, w.dt, w.tau, collision=w.collision, alpha=w.alpha,
                       sigma_r=w.sigma_r, sigma_z=w.sigma_z, z0=w.z0)
     o.step(1)
@@ -225,7 +237,7 @@ def run_reference(args):
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     import oracle
     oracle.build()
-    w = W.production().replace(nx=64, ny=64, nz=128, z0=-1.0)
+    w = W.production_timing().replace(nx=64, ny=64, nz=128)
     o = oracle.Oracle(w.nx, w.ny, w.nz, w.dx, w.dt, w.tau, collision=w.collision, alpha=w.alpha,
                       sigma_r=w.sigma_r, sigma_z=w.sigma_z, z0=w.z0)
     o.step(args.warmup)
@@ -237,7 +249,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {**workload_config(W.production(), "f32"),
+            "config": {**workload_config(W.production_timing(), "f32"),
                        "sample": f"{w.nz}x{w.ny}x{w.nx} sub-box per step", "parallelism": "host cores"},
             "cpu_baseline": {"value": val, "unit": "GLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
                              "kind": "oracle", "sample": f"{w.nz}x{w.ny}x{w.nx} sub-box of the "
@@ -260,7 +272,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     lbm.load()
-    w = W.production()
+    w = W.production_timing()
     if args.grid:
         nz, ny, nx = (int(v) for v in args.grid.lower().split("x"))
         w = w.replace(nx=nx, ny=ny, nz=nz, name=f"lbm-pwfa {nz}x{ny}x{nx} dx0.05 regularized")
@@ -276,6 +288,7 @@ def run_ours(args):
 
     with torch.cuda.stream(stream):
         sim = lbm.Simulation(w, stream=stream)
+        sim.step(args.prelude)
         sim.step(args.warmup)
         if args.launch:
             # fixed shape, no autotuner trial launches (profiling captures)
@@ -326,7 +339,7 @@ def run_ours(args):
             autotune, K steps under CUDA events, then K profiled steps."""
             torch.cuda.empty_cache()
             sim = lbm.Simulation(w2, stream=stream)
-            sim.step(args.warmup)
+            sim.step(args.prelude + args.warmup)
             sim.autotune(3)
             sim.kernel_times()
             barrier()
@@ -356,7 +369,7 @@ def run_ours(args):
                     "value": glups, "unit": "GLUPS", "vs_f32": glups / glups_main,
                     "ms_per_step": ms2 / args.steps, "bytes_per_node_step": STEP_BYTES[st],
                     "pct_hbm_step": glups * 1e9 * STEP_BYTES[st] / (hbm_peak()[0] * 1e9),
-                    "fluid_kernel_GBs": (76 * 2 * 2 + 48) * N / (kpl["fluid"] * 1e-3) / 1e9,
+                    "fluid_kernel_GBs": FLUID_BYTES[st] * N / (kpl["fluid"] * 1e-3) / 1e9,
                     "kernel_ms_per_step": kpl, "finite": bool(d2[7] == 0)}
         # ---- the same production step with the BGK collision (Eq. 7)
         bgk_line = None
@@ -367,7 +380,7 @@ def run_ours(args):
                 "value": glups, "unit": "GLUPS", "vs_regularized": glups / glups_main,
                 "ms_per_step": ms2 / args.steps,
                 "pct_hbm_step": glups * 1e9 * STEP_BYTES[w.storage] / (hbm_peak()[0] * 1e9),
-                "fluid_kernel_GBs": STEP_BYTES[w.storage] * N / (kpl["fluid"] * 1e-3) / 1e9,
+                "fluid_kernel_GBs": FLUID_BYTES[w.storage] * N / (kpl["fluid"] * 1e-3) / 1e9,
                 "kernel_ms_per_step": kpl, "finite": bool(d2[7] == 0)}
         # ---- moving window: the same workload with the box following the
         # driver from the first step (one plane every dx / dt = 5.67 steps)
@@ -473,55 +486,79 @@ def run_ours(args):
             sim.record(Ta, 0)
             stream.synchronize()
             t_rec = time.perf_counter() - t0
-            k, mask = W.witness_slab(wa, Ta)
-            seed = torch.zeros((3, wa.nz, wa.ny, wa.nx), dtype=torch.float32, device="cuda")
-            seed[2, k][torch.from_numpy(mask).cuda()] = -1.0 / float(mask.sum())
+            L = sim.witness_loss()
+            sim.kernel_times()
             t0 = time.perf_counter()
-            g = sim.adjoint_step(seed)
+            g = sim.adjoint_step(None)  # the built-in witness loss over the recorded run
             t_adj = time.perf_counter() - t0
+            _, la = sim.kernel_times()
+            # the same sweep with an event pair around every launch
+            sim.profile(True)
+            sim.adjoint_step(None)
+            ka, la2 = sim.kernel_times()
+            sim.profile(False)
             sim.close()
-            adjoint_line = {"value": wa.nodes * Ta / t_adj / 1e9, "unit": "GLUPS",
-                            "note": "reverse sweep incl. segment recompute; node-steps of the adjoint / wall time",
+            adj_glups = wa.nodes * Ta / t_adj / 1e9
+            adjoint_line = {"value": adj_glups, "unit": "GLUPS",
+                            "note": "reverse sweep incl. segment recompute, wall time of pwfa_lbm_adjoint_step "
+                                    "(NULL seed: the built-in witness loss); node-steps of the adjoint / time",
+                            "bytes_per_node_step": ADJOINT_BYTES,
+                            "pct_hbm": adj_glups * 1e9 * ADJOINT_BYTES / (hbm_peak()[0] * 1e9),
                             "record_glups": wa.nodes * Ta / t_rec / 1e9, "grid_zyx": [wa.nz, wa.ny, wa.nx],
                             "steps": Ta, "ckpt_every": int(__import__("math").ceil(Ta ** 0.5)),
+                            "witness_loss": L,
+                            "kernel_ms_per_reversed_step": {k: ka[k] / Ta for k in ka if la2[k]},
+                            "launches_per_reversed_step": {k: la[k] / Ta for k in la if la[k]},
                             "grad_alpha_sigr_sigz": [float(v) for v in g[:3]]}
-        # ---- batched form: 64 instances of uneven size in one persistent,
-        # graph-replayed launch per phase, against the same instances stepped
-        # one after another
+        # ---- batched form: 64 instances of uneven size, one launch per phase
+        # for all of them, two steps per graph replay, against the same
+        # instances stepped one after another; then a scan of 256 small
+        # instances, where one instance alone cannot fill the GPU
         batch_line = None
         if not args.no_extra and args.only in ("", "batched"):
-            torch.cuda.empty_cache()
-            ws = W.batched_scan(args.batch_instances, seed=0)
-            tot = sum(x.nodes for x in ws)
-            sb = lbm.Simulation(ws, stream=stream)
-            sb.step(args.warmup + (args.warmup % 2))
-            sb.autotune(2)
-            sb.step(2)
-            sb.kernel_times()
+            def time_batch(ws, K):
+                torch.cuda.empty_cache()
+                tot = sum(x.nodes for x in ws)
+                sb = lbm.Simulation(ws, stream=stream)
+                sb.step(args.warmup + (args.warmup % 2))
+                sb.autotune(2)
+                sb.step(2)
+                sb.kernel_times()
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sb.step(K)
+                e1.record(stream)
+                stream.synchronize()
+                msb = e0.elapsed_time(e1)
+                _, lb = sb.kernel_times()
+                # per-phase device times of the same batched steps
+                sb.profile(True)
+                sb.step(K)
+                kb, lk = sb.kernel_times()
+                sb.profile(False)
+                sb.set_batching(False)
+                sb.step(2)
+                e0.record(stream)
+                sb.step(K)
+                e1.record(stream)
+                stream.synchronize()
+                msu = e0.elapsed_time(e1)
+                db = [sb.diag(i, check=False)[7] for i in range(len(ws))]
+                sb.close()
+                return {"value": tot * K / (msb * 1e-3) / 1e9, "unit": "GLUPS", "instances": len(ws),
+                        "nodes_total": tot, "steps": K, "ms_per_step": msb / K,
+                        "launches_per_step": sum(lb.values()) / K,
+                        "kernel_ms_per_step": {k: kb[k] / K for k in kb if lk[k]},
+                        "unbatched_glups": tot * K / (msu * 1e-3) / 1e9, "speedup_vs_unbatched": msu / msb,
+                        "nonfinite_instances": int(sum(1 for v in db if v > 0))}
             Kb = args.steps - args.steps % 2
-            barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sb.step(Kb)
-            e1.record(stream)
-            stream.synchronize()
-            msb = e0.elapsed_time(e1)
-            _, lb = sb.kernel_times()
-            sb.set_batching(False)
-            sb.step(2)
-            e0.record(stream)
-            sb.step(Kb)
-            e1.record(stream)
-            stream.synchronize()
-            msu = e0.elapsed_time(e1)
-            db = [sb.diag(i, check=False)[7] for i in range(len(ws))]
-            sb.close()
-            batch_line = {"value": tot * Kb / (msb * 1e-3) / 1e9, "unit": "GLUPS", "instances": len(ws),
-                          "nodes_total": tot, "steps": Kb,
-                          "grids_zyx": sorted({(x.nz, x.ny, x.nx) for x in ws}),
-                          "launches_per_step": sum(lb.values()) / Kb,
-                          "unbatched_glups": tot * Kb / (msu * 1e-3) / 1e9, "speedup_vs_unbatched": msu / msb,
-                          "nonfinite_instances": int(sum(1 for v in db if v > 0))}
+            ws = W.batched_scan(args.batch_instances, seed=0)
+            batch_line = time_batch(ws, Kb)
+            batch_line["grids_zyx"] = sorted({(x.nz, x.ny, x.nx) for x in ws})
+            batch_line["vs_single_instance_bgk"] = (batch_line["value"] / bgk_line["value"]) if bgk_line else None
+            batch_line["small_instances"] = time_batch(W.small_scan(256, seed=0), max(Kb, 20))
+            batch_line["small_instances"]["grid_zyx"] = [32, 16, 16]
     value, e2e_val, ms_max = aggregate_over_ranks(ms, e2e_s, world, N, args.steps, dist, "cuda")
     if rank != 0:
         if dist is not None:
@@ -530,24 +567,28 @@ def run_ours(args):
 
     peak, peak_kind = hbm_peak()
     fluid_ms = kms["fluid"] / max(kl["fluid"], 1)
-    fluid_bytes = (FLUID_BYTES_F32 if w.storage == W.F32 else 76 * 2 * 2 + 48) * N
+    fluid_bytes = FLUID_BYTES[w.storage] * N
     achieved = fluid_bytes / (fluid_ms * 1e-3) / 1e9
     step_bytes = STEP_BYTES[w.storage]
+    step_achieved = value / world * step_bytes  # GB/s of one GPU over the whole step
     line = {
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {**workload_config(w, args.storage),
+                   "prelude_steps": args.prelude,
                    "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * 76 * (4 if w.storage == W.F32 else 2) * N / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "fluid_block": list(launch_shape), "fluid_variant": fluid_variant},
-        "pct_hbm_step": {"of_" + peak_kind: value * 1e9 * step_bytes / (peak * 1e9),
-                         "of_nominal_8000": value * 1e9 * step_bytes / (NOMINAL_HBM_GBS * 1e9),
+        "pct_hbm_step": {"of_" + peak_kind: value / world * 1e9 * step_bytes / (peak * 1e9),
+                         "of_nominal_8000": value / world * 1e9 * step_bytes / (NOMINAL_HBM_GBS * 1e9),
                          "bytes_per_node_step": step_bytes},
         "roofline": {"bound": "hbm", "kernel": "fluid", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": ncu_traffic(N), "algorithmic_bytes_per_launch": fluid_bytes,
-                     "avg_launch_ms": fluid_ms},
+                     "bytes_per_node": FLUID_BYTES[w.storage], "avg_launch_ms": fluid_ms,
+                     "step": {"bytes_per_node_step": step_bytes, "achieved": step_achieved,
+                              "frac": step_achieved / peak, "ms": ms_max / args.steps}},
         "kernel_ms_per_step": {k: kms[k] / max(kl[k], 1) for k in kms if kl[k]},
         "field_step": ("ampere fused with the next step's faraday (one launch)" if kl.get("faraday", 0) == 0
                        else "separate faraday and ampere launches"),
@@ -616,6 +657,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--prelude", type=int, default=PRELUDE_STEPS,
+                    help="untimed steps before the warm-up that form the wake")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -147,19 +147,39 @@ int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps);
  * and ~174 N floats of adjoint scratch; PWFA_ERR_ALLOC if it does not fit. */
 int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckpt_every);
 
-/* Gradient of L = sum(seed_E * E(t_{T+1/2})) over the raw Yee E after the
- * recorded T steps (seed_E: [3][z][y][x] FP32, host or device) with respect
- * to theta = (alpha, sigma_r, sigma_z, profile[0..n_profile-1]), written to
- * host_grad (n_grad >= 3 + n_profile doubles). Each segment is recomputed
- * from its checkpoint, then reversed: transposed Ampere (with the driver's
- * parameter derivatives), transposed fluid step (J = -n beta(p*), collision,
- * equilibrium, Lorentz source, beta(p), the n-floor branch, Eq. 14 boundary
- * nodes, transposed pull), transposed node averages and Faraday; the initial
- * populations give the profile derivative. Adjoint state is FP32, parameter
- * gradients are accumulated in FP64. n_profile <= 256. PWFA_ERR_STATE if
- * nothing was recorded. The instance ends at step T again. */
-int pwfa_lbm_adjoint_step(pwfa_lbm_t* h, int32_t instance, const float* seed_E, double* host_grad,
-                          int32_t n_grad);
+/* Gradient of an objective L of the raw Yee E after T recorded steps with
+ * respect to theta = (alpha, sigma_r, sigma_z, profile[0..n_profile-1]),
+ * written to host_grad (n_grad >= 3 + n_profile doubles, host).
+ *   seed_E  dL/dE, [3][z][y][x] FP32 (host or device) for
+ *           L = sum(seed_E * E(t_{T+1/2})); or NULL for the built-in witness
+ *           loss of pwfa_lbm_witness_loss after T steps (the library seeds
+ *           -1/count on its slab).
+ *   nsteps  T >= 1: run the forward with checkpoints first (as
+ *           pwfa_lbm_record(h, instance, nsteps, ckpt_every)) unless the
+ *           instance already holds a recording of T steps (with ckpt_every
+ *           checkpoints when ckpt_every > 0); 0: use the existing recording
+ *           (PWFA_ERR_STATE if there is none).
+ *   ckpt_every  checkpoint interval of a new recording; 0 selects
+ *           ceil(sqrt(T)).
+ * Each segment is recomputed from its checkpoint, then reversed: transposed
+ * Ampere (with the driver's parameter derivatives), transposed fluid step
+ * (J = -n beta(p*), collision, equilibrium, Lorentz source, beta(p), the
+ * n-floor branch, Eq. 14 boundary nodes, transposed pull), transposed node
+ * averages and Faraday; the initial populations give the profile
+ * derivative. Adjoint state is FP32, parameter gradients are accumulated in
+ * FP64. n_profile <= 256. The instance ends at step T. Synchronises. */
+int pwfa_lbm_adjoint_step(pwfa_lbm_t* h, int32_t instance, const float* seed_E, int32_t nsteps,
+                          int32_t ckpt_every, double* host_grad, int32_t n_grad);
+
+/* The built-in gradient objective at the instance's current step T (the
+ * witness loss of the differentiable form): host_loss receives
+ * L = -mean(E_z) over the witness slab, the layer of E_z edges
+ * z = (k + 1/2) dx nearest z_w = z0 + T dt - 3 pi (1.5 plasma wavelengths
+ * 2 pi c/omega_p behind the driver centre; k kept in 1..nz-2) over the
+ * transverse nodes off the walls with r <= 1 c/omega_p of the axis. The slab
+ * does not depend on the driver parameters. FP64 sum; synchronises.
+ * PWFA_ERR_PARAM if the slab holds no edge. */
+int pwfa_lbm_witness_loss(pwfa_lbm_t* h, int32_t instance, double* host_loss);
 
 /* Advance every instance by nsteps (>= 1) like pwfa_lbm_step and return the
  * FP64 diagnostics of the state entering the last step, fused into that
@@ -250,8 +270,10 @@ int pwfa_lbm_get_particles(pwfa_lbm_t* h, int32_t instance, float* out);
 #define PWFA_KERNEL_FARADAY 0 /* Yee B update */
 #define PWFA_KERNEL_FLUID 1   /* fused stream + moments + source + collide */
 #define PWFA_KERNEL_AMPERE 2  /* Yee E update with plasma and driver current */
-#define PWFA_KERNEL_AUX 3     /* step counters of the batched path, moving-window field moves */
-#define PWFA_KERNEL_KINDS 4
+#define PWFA_KERNEL_AUX 3     /* moving-window field moves, PIC push and deposit */
+#define PWFA_KERNEL_ADJ_FLUID 4 /* adjoint: transposed fluid step (boundary and interior nodes) */
+#define PWFA_KERNEL_ADJ_FIELD 5 /* adjoint: transposed Ampere, node averages and Faraday */
+#define PWFA_KERNEL_KINDS 6
 
 /* Per-kernel device timing, off by default. While enabled, each step records
  * a CUDA event pair around every kernel it launches on the handle's stream
@@ -288,14 +310,18 @@ int pwfa_lbm_get_fluid_variant(pwfa_lbm_t* h, int32_t instance, int32_t* variant
  * so the simulation state is unchanged. Synchronises the stream. */
 int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps);
 
-/* Batched path, on by default. A handle with 2..96 instances that share
- * storage, collision, boundary and coupling advances them together: one
- * persistent launch per phase (Faraday, fluid, Ampere) strides over a work
- * list of 128-node tiles of every instance, and two steps at a time are
- * replayed from a captured CUDA graph (an odd remainder step runs per
+/* Batched path, on by default. A handle with 2..65535 instances that share
+ * storage, collision, boundary and coupling and use the rigid driver in a
+ * fixed box advances them together: each phase of a step is one launch over
+ * the tiles of every instance (the fluid step on 128-node tiles, then Ampere
+ * fused with the next step's Faraday on z-marching field tiles; with
+ * PWFA_FUSION_OFF, Faraday, fluid and Ampere), and two steps at a time are
+ * replayed from a captured CUDA graph whose field launches advance the
+ * driver's step counters themselves (an odd remainder step runs per
  * instance). The instance table and graph are rebuilt lazily after any call
- * that changes an instance's state or launch shape. enable = 0 advances the
- * instances one after another with ordinary launches. */
+ * that changes an instance's state, launch shape or the field-fusion mode.
+ * enable = 0 advances the instances one after another with ordinary
+ * launches. */
 int pwfa_lbm_set_batching(pwfa_lbm_t* h, int32_t enable);
 
 /* Field-step fusion. For a coupled instance with the rigid driver and a
@@ -304,7 +330,8 @@ int pwfa_lbm_set_batching(pwfa_lbm_t* h, int32_t enable);
  * n+1 starts without its Faraday launch. Results are those of the separate
  * kernels, bit for bit. The kernel-time kind PWFA_KERNEL_AMPERE then covers
  * the fused kernel. Modes: OFF (separate launches), AUTO (the default: fused
- * on grids of 4 Mi nodes or more, where it is faster), ON (always);
+ * on grids of 4 Mi nodes or more, where it is faster, and in the batched
+ * path, whose field launch spans every instance), ON (always);
  * PWFA_ERR_PARAM for another value. */
 #define PWFA_FUSION_OFF 0
 #define PWFA_FUSION_AUTO 1
@@ -326,7 +353,8 @@ int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream);
  *   dev_out 8 doubles, device memory, the same quantities as the host_diag
  *           of pwfa_lbm_fields: sum n, sum n p_k (3), field energy
  *           1/2 sum(E^2 + B^2) dx^3, min n, max |beta|, non-finite count
- *   n_floor density floor of p = A / max(n, n_floor); <= 0 selects 1e-6
+ *   n_floor density floor of p = A / max(n, n_floor); 0 selects 1e-6, a
+ *           negative or NaN value is rejected with PWFA_ERR_PARAM
  * Work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default
  * stream) and not synchronised. Scratch is a fixed 1 MiB array inside the
  * library that every GPU which loads it holds until exit; grids of more than

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kBX * kBY) adj_ampere_kernel(const AdjArgs a) 
             const float yr = ((float)j - 0.5f * (float)(g.ny - 1)) * a.f.dx;
             const float zeta = ((float)k + 0.5f) * a.f.dx - a.f.zc;
             const float r2 = xr * xr + yr * yr;
-            const float ga = expf(-r2 * a.f.inv2sr2 - zeta * zeta * a.f.inv2sz2);
+            const float ga = expf(-r2 * a.f.inv2sr2) * expf(-zeta * zeta * a.f.inv2sz2);
             const float w = dt * ez * ga;
             g3[0] = w;
             g3[1] = w * a.csr * r2;
@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_ke
         for (int q = 0; q < kQ; ++q) {
             const int sx = x - xi_x(q), sy = y - xi_y(q), sz = z - xi_z(q);
             if (!in_grid(g, sx, sy, sz)) continue;
-            const uint32_t so = ((uint32_t)sz * (uint32_t)g.ny + (uint32_t)sy) * (uint32_t)g.nx + (uint32_t)sx;
+            const uint32_t so = PWFA_CHECK(
+                s.dbg, ((uint32_t)sz * (uint32_t)g.ny + (uint32_t)sy) * (uint32_t)g.nx + (uint32_t)sx, 0, g.Np, 7u);
             Sout[pop_off(q, so)] = 0.0f;
         }
     }
@@ -302,13 +303,14 @@ __global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_ke
             uint32_t src;
             if (PER) src = (uint32_t)src_index<true>(g, xs, ys, zs, q);
             else src = nodec - (uint32_t)(xi_x(q) + xi_y(q) * g.nx) - (uint32_t)xi_z(q) * sxy;
+            src = PWFA_CHECK(s.dbg, src, 0, g.Np, 7u);
             Al += Codec<ST>::load(fin + pop_elem<ST>(l, pop_off(q, src), LS), l, q, s.n0);
             S[q] = __ldg(Sin + pop_off(q, node));
         }
         float v[3] = {0.0f, 0.0f, 0.0f};
-        if (l == 0) { if (forced) node_E<PER>(g, s.E, x, y, z, v); }
-        else if (l == 1) { if (forced) node_B_sum<PER>(g, s.Bc, x, y, z, v); }
-        else if (l == 2) { if (forced) node_B_sum<PER>(g, s.Bn, x, y, z, v); }
+        if (l == 0) { if (forced) node_E<PER>(g, s.E, x, y, z, v, s.dbg); }
+        else if (l == 1) { if (forced) node_B_sum<PER>(g, s.Bc, x, y, z, v, s.dbg); }
+        else if (l == 2) { if (forced) node_B_sum<PER>(g, s.Bn, x, y, z, v, s.dbg); }
         else { v[0] = a.Jbar[0][node]; v[1] = a.Jbar[1][node]; v[2] = a.Jbar[2][node]; }
 #pragma unroll
         for (int c = 0; c < 3; ++c) sN[l][c][lane] = v[c];
@@ -501,6 +503,7 @@ __global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_ke
         uint32_t src;
         if (PER) src = (uint32_t)src_index<true>(g, xs, ys, zs, q);
         else src = nodec - (uint32_t)(xi_x(q) + xi_y(q) * g.nx) - (uint32_t)xi_z(q) * sxy;
+        src = PWFA_CHECK(s.dbg, src, 0, g.Np, 7u);
         float fb = Ab;
         if (COLL == 0) fb += (1.0f - om) * S[q];
         else if (COLL == 2) fb += S[q];
@@ -690,15 +693,19 @@ cudaError_t launch_adjoint_grad_finish(const double* gslots, double* grad, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_step(const AdjArgs& a0, int storage, int collision, cudaStream_t s) {
+static AdjArgs with_driver_factors(const AdjArgs& a0) {
     AdjArgs a = a0;
     a.csr = a.f.alpha / (a.sr * a.sr * a.sr);
     a.csz = a.f.alpha / (a.sz * a.sz * a.sz);
+    return a;
+}
+
+cudaError_t launch_adjoint_ampere(const AdjArgs& a0, cudaStream_t s) {
+    const AdjArgs a = with_driver_factors(a0);
     const Grid& g = a.f.g;
     const dim3 grid = grid_of(g, kBX, kBY), block(kBX, kBY, 1);
-    const bool per = g.periodic;
     if (a.f.couple) {
-        if (per) adj_ampere_kernel<true><<<grid, block, 0, s>>>(a);
+        if (g.periodic) adj_ampere_kernel<true><<<grid, block, 0, s>>>(a);
         else adj_ampere_kernel<false><<<grid, block, 0, s>>>(a);
     } else {
         // no Maxwell update: B, E pass through; J is not used
@@ -707,22 +714,39 @@ cudaError_t launch_adjoint_step(const AdjArgs& a0, int storage, int collision, c
         if (e == cudaSuccess) e = cudaMemsetAsync(a.Jbar[2], 0, sizeof(float) * g.N, s);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_fluid(const AdjArgs& a0, int storage, int collision, cudaStream_t s) {
+    const AdjArgs a = with_driver_factors(a0);
     switch (storage) {
-        case 0: e = launch_adj_fluid_s<0>(a, collision, s); break;
-        case 1: e = launch_adj_fluid_s<1>(a, collision, s); break;
-        case 2: e = launch_adj_fluid_s<2>(a, collision, s); break;
-        default: return cudaErrorInvalidValue;
+        case 0: return launch_adj_fluid_s<0>(a, collision, s);
+        case 1: return launch_adj_fluid_s<1>(a, collision, s);
+        case 2: return launch_adj_fluid_s<2>(a, collision, s);
     }
-    if (e != cudaSuccess || !a.f.couple) return e;
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adjoint_fields(const AdjArgs& a0, cudaStream_t s) {
+    const AdjArgs a = with_driver_factors(a0);
+    if (!a.f.couple) return cudaSuccess;
+    const Grid& g = a.f.g;
+    const dim3 grid = grid_of(g, kBX, kBY), block(kBX, kBY, 1);
+    const bool per = g.periodic;
     if (per) adj_faces_kernel<true><<<grid, block, 0, s>>>(a);
     else adj_faces_kernel<false><<<grid, block, 0, s>>>(a);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (per) adj_edges_kernel<true><<<grid, block, 0, s>>>(a);
     else adj_edges_kernel<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_step(const AdjArgs& a, int storage, int collision, cudaStream_t s) {
+    cudaError_t e = launch_adjoint_ampere(a, s);
+    if (e == cudaSuccess) e = launch_adjoint_fluid(a, storage, collision, s);
+    if (e == cudaSuccess) e = launch_adjoint_fields(a, s);
+    return e;
 }
 
 cudaError_t launch_adjoint_profile(const Grid& g, const float* Sbar, float n0, int n_profile, double rmax,

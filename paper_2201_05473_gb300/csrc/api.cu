@@ -1,12 +1,18 @@
 // Host runtime of the C ABI declared in include/pwfa_lbm.h: parameter
 // validation, one device arena per instance, the per-step launch sequence
 // (Faraday -> fused fluid -> Ampere), state exchange and diagnostics.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
+
+#include <atomic>
+#include <cstdlib>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pwfa_lbm.h"
 #include "lbm_adjoint.h"
@@ -28,6 +34,14 @@ int cuda_fail(cudaError_t e, const char* where) {
     return fail(PWFA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// NVTX range over a public call (named in profiler timelines).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 #define PWFA_CUDA(call, where)                          \
     do {                                                \
         cudaError_t e_ = (call);                        \
@@ -35,6 +49,7 @@ int cuda_fail(cudaError_t e, const char* where) {
     } while (0)
 
 size_t storage_bytes(int st) { return st == PWFA_F32 ? 4 : 2; }
+
 
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -60,6 +75,9 @@ struct Instance {
     int bcur = 0;
     float* J[3] = {nullptr, nullptr, nullptr};
     double* d_profile = nullptr;
+    int* d_wrows = nullptr;     // witness slab: x range of each row (2 ny ints)
+    double* d_wout = nullptr;   // witness slab: FP64 sum of E_z
+    unsigned* d_dbg = nullptr;  // debug builds: index-error word (site, index, count)
     int64_t steps = 0;
     int bx = 64, by = 2;  // fluid kernel block shape (pwfa_lbm_autotune refines it)
     int variant = PWFA_FLUID_DIRECT;  // fluid kernel variant
@@ -83,6 +101,25 @@ namespace pwfa {
 // Record the calling thread's error message for pwfa_lbm_last_error (used by
 // entry points defined in other translation units).
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+// Every device allocation of the library goes through here. Fault injection
+// for tests: with PWFA_FAIL_ALLOC_AT=n in the environment, the n-th
+// allocation of the process (counting from 1) fails as an out-of-memory
+// cudaMalloc would, so that each failure path can be exercised without
+// exhausting the device.
+namespace {
+std::atomic<long> g_alloc_count{0};
+}
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    const long k = ++g_alloc_count;
+    if (const char* v = std::getenv("PWFA_FAIL_ALLOC_AT")) {
+        if (std::atol(v) == k) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 }  // namespace pwfa
 
 struct pwfa_lbm {
@@ -96,16 +133,20 @@ struct pwfa_lbm {
     bool profiling = false;
     std::vector<cudaEvent_t> events;          // pool, used in start/stop pairs
     std::vector<int> pending_kind;            // kind of each recorded pair
-    double ms[PWFA_KERNEL_KINDS] = {0, 0, 0, 0};
-    int64_t launches[PWFA_KERNEL_KINDS] = {0, 0, 0, 0};
+    double ms[PWFA_KERNEL_KINDS] = {};
+    int64_t launches[PWFA_KERNEL_KINDS] = {};
     // Ampere fused with the next step's Faraday (rigid driver, no window):
     // PWFA_FUSION_OFF / _AUTO (grids of kFuseMinNodes and more) / _ON
     int field_fusion = PWFA_FUSION_AUTO;
-    // batched persistent path (several homogeneous instances)
+    // batched path (several homogeneous instances, one launch per phase)
     bool batching = true;
     bool batch_valid = false;
-    BatchEntry* d_entries = nullptr;
-    int64_t* d_steps = nullptr;
+    bool batch_fused = false;          // the table was built for the fused field step
+    BatchEntry* d_entries = nullptr;   // instance table (capacity: entries_cap)
+    int64_t* d_steps = nullptr;        // two driver step counters per instance
+    int entries_cap = 0;
+    uint16_t* d_tile_inst = nullptr;   // instance of each fluid tile, then of each fused-field tile
+    int64_t tile_inst_cap = 0;
     BatchLaunch blaunch{};
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph2 = nullptr;  // two steps (both parities)
@@ -204,6 +245,7 @@ StepArgs make_args(const Instance& in) {
     a.bx = in.bx;
     a.by = in.by;
     a.staged = in.variant == PWFA_FLUID_STAGED && in.bx * in.by == 128;
+    a.dbg = in.d_dbg;
     for (int c = 0; c < 3; ++c) a.Jb[c] = in.Jb[c];
     a.jbox = in.jbox ? in.jbox + 6 * (in.steps & 1) : nullptr;
     a.jbox_next = in.jbox ? in.jbox + 6 * ((in.steps + 1) & 1) : nullptr;
@@ -224,7 +266,7 @@ int ensure_staging(pwfa_lbm* h, size_t bytes) {
     if (h->staging) cudaFree(h->staging);
     h->staging = nullptr;
     h->staging_bytes = 0;
-    if (cudaMalloc(&h->staging, bytes) != cudaSuccess) {
+    if (dev_alloc((void**)&h->staging, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(PWFA_ERR_ALLOC, "cudaMalloc of the staging buffer failed");
     }
@@ -262,20 +304,29 @@ bool fusable(const pwfa_lbm_params& p) {
 // 256x128x128 (4.2 M nodes: 485 against 488 us; 512x256x256: 1.2 %).
 constexpr int64_t kFuseMinNodes = (int64_t)4 << 20;
 
+// Zero guard in front of every Yee/current array a step kernel reads: on an
+// open grid the node averages read the -1 neighbours in x, y and z without
+// bounds checks (one x-y plane, one row and one element before index 0 at
+// the lowest node), and every component on or outside the conducting walls
+// is kept at zero, so those reads see zeros and stay inside the array's own
+// allocation.
+size_t guard_bytes(const Grid& g) {
+    return align_up(((size_t)g.nx * g.ny + g.nx + 1) * sizeof(float));
+}
+
 int alloc_instance(Instance& in, cudaStream_t s) {
     const int64_t N = in.g.N;
     const size_t fbytes = align_up((size_t)in.g.Np * kPop * storage_bytes(in.p.storage));
-    // Each Yee/current array is preceded by one zero x-y plane: in open mode the
-    // node averages read index -1 / -nx / -nx*ny without bounds checks.
-    const size_t pad = align_up((size_t)in.g.nx * in.g.ny * sizeof(float));
+    const size_t pad = guard_bytes(in.g);
     const size_t vbytes = pad + align_up((size_t)N * sizeof(float));
     const size_t pbytes = align_up(sizeof(double) * (in.profile.empty() ? 1 : in.profile.size()));
+    const size_t wbytes = align_up(sizeof(int) * 2 * (size_t)in.g.ny) + align_up(sizeof(double)) + kAlign;
     // E 3, B 2x3, J 3 (+ a second E for the window move or the fused field
     // step, + the PIC driver's current)
     const bool ealt = in.p.moving_window || fusable(in.p);
     const int nvec = 12 + (ealt ? 3 : 0) + (in.p.driver == PWFA_DRIVER_PIC ? 3 : 0);
-    const size_t total = 2 * fbytes + nvec * vbytes + pbytes;
-    if (cudaMalloc(&in.arena, total) != cudaSuccess) {
+    const size_t total = 2 * fbytes + nvec * vbytes + pbytes + wbytes;
+    if (dev_alloc((void**)&in.arena, total) != cudaSuccess) {
         cudaGetLastError();
         in.arena = nullptr;
         char buf[160];
@@ -295,20 +346,25 @@ int alloc_instance(Instance& in, cudaStream_t s) {
     if (in.p.driver == PWFA_DRIVER_PIC)
         for (int c = 0; c < 3; ++c) { in.Jb[c] = (float*)(base + pad); base += vbytes; }
     in.d_profile = (double*)base;
+    base += pbytes;
+    in.d_wrows = (int*)base;
+    in.d_wout = (double*)(base + align_up(sizeof(int) * 2 * (size_t)in.g.ny));
+    in.d_dbg = (unsigned*)(base + align_up(sizeof(int) * 2 * (size_t)in.g.ny) + align_up(sizeof(double)));
     if (in.p.driver == PWFA_DRIVER_PIC) {
         // deposit boxes of both step parities, empty
         const int empty[12] = {0x7fffffff, 0x7fffffff, 0x7fffffff, -1, -1, -1,
                                0x7fffffff, 0x7fffffff, 0x7fffffff, -1, -1, -1};
-        if (cudaMalloc(&in.jbox, sizeof empty) != cudaSuccess) {
+        if (dev_alloc((void**)&in.jbox, sizeof empty) != cudaSuccess) {
             cudaGetLastError();
             return fail(PWFA_ERR_ALLOC, "cudaMalloc of the deposit boxes failed");
         }
         PWFA_CUDA(cudaMemcpy(in.jbox, empty, sizeof empty, cudaMemcpyHostToDevice), "cudaMemcpy");
     }
-    // Fields, currents, their guard planes and the second population buffer
+    // Fields, currents, their guards and the second population buffer
     // start at zero.
     PWFA_CUDA(cudaMemsetAsync(in.f[1], 0, fbytes, s), "cudaMemsetAsync");
     PWFA_CUDA(cudaMemsetAsync(fields, 0, nvec * vbytes, s), "cudaMemsetAsync");
+    PWFA_CUDA(cudaMemsetAsync(in.d_dbg, 0, kAlign, s), "cudaMemsetAsync");
     if (!in.profile.empty())
         PWFA_CUDA(cudaMemcpyAsync(in.d_profile, in.profile.data(), sizeof(double) * in.profile.size(),
                                   cudaMemcpyHostToDevice, s),
@@ -396,57 +452,104 @@ void batch_release(pwfa_lbm* h) {
 int batch_launch_all(pwfa_lbm* h, int parity, cudaStream_t s, bool timed);
 
 // Build the device instance table for the current ping-pong state and
-// capture a two-step graph (parity 0 then 1).
+// capture a two-step graph (parity 0 then 1). With the fused field step the
+// instances first get B(t_{n+1}) where it is not already computed.
 int batch_build(pwfa_lbm* h) {
     batch_release(h);
     const int n = (int)h->inst.size();
-    if (!h->d_entries) {
-        if (cudaMalloc(&h->d_entries, sizeof(BatchEntry) * n) != cudaSuccess ||
-            cudaMalloc(&h->d_steps, sizeof(int64_t) * (n + 2)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the batch table failed");
+    const auto& p0 = h->inst[0].p;
+    const bool fused = p0.couple && h->field_fusion != PWFA_FUSION_OFF;
+    if (fused) {
+        for (auto& in : h->inst) {
+            if (in.lookahead) continue;
+            StepArgs a = make_args(in);
+            int rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(a, h->stream); });
+            if (rc) return rc;
+            in.lookahead = true;
         }
     }
     std::vector<BatchEntry> ent(n);
-    std::vector<int64_t> steps(n);
-    int64_t items = 0;
+    std::vector<int64_t> steps(2 * (size_t)n);
+    int64_t ntiles = 0, nftiles = 0;
     for (int i = 0; i < n; ++i) {
         Instance& in = h->inst[i];
         if (in.bx * in.by != kBatchTile) { in.bx = 64; in.by = 2; }
         BatchEntry& e = ent[i];
-        e.args[0] = make_args(in);
-        in.fcur = 1 - in.fcur;
-        if (in.p.couple) in.bcur = 1 - in.bcur;
-        e.args[1] = make_args(in);
-        in.fcur = 1 - in.fcur;
-        if (in.p.couple) in.bcur = 1 - in.bcur;
+        for (int par = 0; par < 2; ++par) {
+            e.args[par] = make_args(in);
+            for (int c = 0; c < 3; ++c) {
+                e.out[par].E[c] = in.Ealt[c];
+                e.out[par].B[c] = in.B[in.bcur][c];
+            }
+            // the pointers of the next step
+            in.fcur = 1 - in.fcur;
+            if (in.p.couple) in.bcur = 1 - in.bcur;
+            if (fused) for (int c = 0; c < 3; ++c) std::swap(in.E[c], in.Ealt[c]);
+        }
         e.bx = in.bx;
         e.by = in.by;
         e.tiles_x = (in.g.nx + in.bx - 1) / in.bx;
         e.tiles_y = (in.g.ny + in.by - 1) / in.by;
-        e.item_begin = items;
-        items += (int64_t)e.tiles_x * e.tiles_y * in.g.nz;
+        e.ntiles = (int64_t)e.tiles_x * e.tiles_y * in.g.nz;
+        e.tile_begin = ntiles;
+        ntiles += (e.ntiles + kBatchGroup - 1) / kBatchGroup;
+        int fz = 0;
+        fused_field_tiles(in.g, &e.ftiles_x, &e.ftiles_y, &fz);
+        e.ftile_begin = nftiles;
+        nftiles += (int64_t)e.ftiles_x * e.ftiles_y * fz;
         e.z0 = in.p.z0;
         e.dt = in.p.dt;
-        e.step = h->d_steps + i;
-        steps[i] = in.steps;
+        e.step = h->d_steps;  // set below, once the counters exist
+        steps[2 * i] = in.steps;
+        steps[2 * i + 1] = in.steps + 1;
     }
-    if (items > INT32_MAX) return fail(PWFA_ERR_PARAM, "batched work list longer than 2^31 tiles");
+    if (ntiles > INT32_MAX || nftiles > INT32_MAX) return fail(PWFA_ERR_PARAM, "batched grid longer than 2^31 tiles");
+    if (n > h->entries_cap) {
+        if (h->d_entries) cudaFree(h->d_entries);
+        if (h->d_steps) cudaFree(h->d_steps);
+        h->d_entries = nullptr;
+        h->d_steps = nullptr;
+        h->entries_cap = 0;
+        if (dev_alloc((void**)&h->d_entries, sizeof(BatchEntry) * n) != cudaSuccess ||
+            dev_alloc((void**)&h->d_steps, sizeof(int64_t) * 2 * n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the batch table failed");
+        }
+        h->entries_cap = n;
+    }
+    if (ntiles + nftiles > h->tile_inst_cap) {
+        if (h->d_tile_inst) cudaFree(h->d_tile_inst);
+        h->d_tile_inst = nullptr;
+        h->tile_inst_cap = 0;
+        if (dev_alloc((void**)&h->d_tile_inst, sizeof(uint16_t) * (ntiles + nftiles)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the batch tile map failed");
+        }
+        h->tile_inst_cap = ntiles + nftiles;
+    }
+    std::vector<uint16_t> map((size_t)(ntiles + nftiles));
+    for (int i = 0; i < n; ++i) {
+        const int64_t t1 = i + 1 < n ? ent[i + 1].tile_begin : ntiles;
+        const int64_t f1 = i + 1 < n ? ent[i + 1].ftile_begin : nftiles;
+        std::fill(map.begin() + ent[i].tile_begin, map.begin() + t1, (uint16_t)i);
+        std::fill(map.begin() + ntiles + ent[i].ftile_begin, map.begin() + ntiles + f1, (uint16_t)i);
+        ent[i].step = h->d_steps + 2 * i;
+    }
     PWFA_CUDA(cudaMemcpyAsync(h->d_entries, ent.data(), sizeof(BatchEntry) * n, cudaMemcpyHostToDevice, h->stream),
               "batch table copy");
-    PWFA_CUDA(cudaMemcpyAsync(h->d_steps, steps.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream),
+    PWFA_CUDA(cudaMemcpyAsync(h->d_steps, steps.data(), sizeof(int64_t) * 2 * n, cudaMemcpyHostToDevice, h->stream),
               "batch counters copy");
-    PWFA_CUDA(batch_upload_table(ent.data(), n, h->stream), "batch table upload");
+    PWFA_CUDA(cudaMemcpyAsync(h->d_tile_inst, map.data(), sizeof(uint16_t) * map.size(), cudaMemcpyHostToDevice,
+                              h->stream),
+              "batch tile map copy");
     PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    const auto& p0 = h->inst[0].p;
     h->blaunch.entries = h->d_entries;
+    h->blaunch.tile_inst = h->d_tile_inst;
+    h->blaunch.ftile_inst = h->d_tile_inst + ntiles;
     h->blaunch.ninst = n;
-    h->blaunch.nitems = items;
-    // the work counters sit after the step counters
-    h->blaunch.counters = reinterpret_cast<int*>(h->d_steps + n);
-    PWFA_CUDA(cudaMemsetAsync(h->blaunch.counters, 0, sizeof(int) * kBatchCounters, h->stream), "cudaMemsetAsync");
-    PWFA_CUDA(batch_grid_size(p0.storage, p0.collision, p0.boundary == PWFA_PERIODIC, &h->blaunch.grid),
-              "batch occupancy");
+    h->blaunch.ntiles = ntiles;
+    h->blaunch.nftiles = nftiles;
+    h->batch_fused = fused;
     if (!h->capture_stream) PWFA_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     cudaGraph_t graph = nullptr;
     PWFA_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
@@ -464,13 +567,24 @@ int batch_build(pwfa_lbm* h) {
 
 int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag = nullptr);
 
-// One batched step of every instance with the given parity.
+// The launches of one batched step of every instance with the given parity:
+// fluid + fused field step, or Faraday + fluid + Ampere, or the fluid alone
+// (uncoupled).
+int batch_phases(const pwfa_lbm* h, int* phases) {
+    if (!h->inst[0].p.couple) { phases[0] = 1; return 1; }
+    if (h->batch_fused) { phases[0] = 1; phases[1] = 3; return 2; }
+    phases[0] = 0; phases[1] = 1; phases[2] = 2;
+    return 3;
+}
+
 int batch_launch_all(pwfa_lbm* h, int parity, cudaStream_t s, bool timed) {
     const auto& p0 = h->inst[0].p;
     const bool per = p0.boundary == PWFA_PERIODIC;
-    const int kinds[4] = {PWFA_KERNEL_FARADAY, PWFA_KERNEL_FLUID, PWFA_KERNEL_AMPERE, PWFA_KERNEL_AUX};
-    for (int phase = 0; phase < 4; ++phase) {
-        if ((phase == 0 || phase == 2) && !p0.couple) continue;
+    const int kinds[4] = {PWFA_KERNEL_FARADAY, PWFA_KERNEL_FLUID, PWFA_KERNEL_AMPERE, PWFA_KERNEL_AMPERE};
+    int phases[3];
+    const int np = batch_phases(h, phases);
+    for (int k = 0; k < np; ++k) {
+        const int phase = phases[k];
         if (timed) {
             cudaStream_t keep = h->stream;
             h->stream = s;
@@ -493,7 +607,9 @@ int batch_steps(pwfa_lbm* h, int32_t nsteps) {
             int rc = batch_build(h);
             if (rc) return rc;
         }
-        const int per_pair = h->inst[0].p.couple ? 4 : 2;
+        const int kinds[4] = {PWFA_KERNEL_FARADAY, PWFA_KERNEL_FLUID, PWFA_KERNEL_AMPERE, PWFA_KERNEL_AMPERE};
+        int phases[3];
+        const int np = batch_phases(h, phases);
         for (int32_t k = 0; k < pairs; ++k) {
             if (h->profiling) {
                 int rc = batch_launch_all(h, 0, h->stream, true);
@@ -501,15 +617,12 @@ int batch_steps(pwfa_lbm* h, int32_t nsteps) {
                 if (rc) return rc;
             } else {
                 PWFA_CUDA(cudaGraphLaunch(h->graph2, h->stream), "cudaGraphLaunch");
-                // launches inside the graph
-                h->launches[PWFA_KERNEL_FLUID] += 2;
-                h->launches[PWFA_KERNEL_AUX] += 2;
-                if (per_pair == 4) { h->launches[PWFA_KERNEL_FARADAY] += 2; h->launches[PWFA_KERNEL_AMPERE] += 2; }
+                for (int q = 0; q < np; ++q) h->launches[kinds[phases[q]]] += 2;  // launches inside the graph
             }
         }
         for (auto& in : h->inst) {
             in.steps += 2 * (int64_t)pairs;
-            in.lookahead = false;
+            in.lookahead = h->batch_fused;
         }
     }
     if (nsteps % 2) {
@@ -593,6 +706,9 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
 // ---------------------------------------------------------------- adjoint
 size_t fbytes_of(const Instance& in) { return align_up((size_t)in.g.Np * kPop * storage_bytes(in.p.storage)); }
 size_t vbytes_of(const Instance& in) { return align_up((size_t)in.g.N * sizeof(float)); }
+// one field array with its zero guard in front (the recorded segment states
+// that the recomputed forward steps read)
+size_t gvbytes_of(const Instance& in) { return guard_bytes(in.g) + vbytes_of(in); }
 
 struct StateRef {  // one stored state inside a recording buffer
     void* f;
@@ -631,6 +747,46 @@ int copy_state(const Instance& in, const StateRef& dst, bool to_rec, cudaStream_
     return PWFA_OK;
 }
 
+// The built-in objective of the gradient calls (the witness loss): L =
+// -mean(E_z) over the witness slab after T steps. The slab is the layer of
+// E_z edges (z = (k + 1/2) dx) nearest z_w = z0 + T dt - 3 pi, i.e. 1.5
+// plasma wavelengths 2 pi c / omega_p behind the driver centre (in box
+// coordinates when the window has moved), over the transverse nodes that are
+// not on the walls and lie within r <= 1 c/omega_p of the axis; k is kept in
+// 1..nz-2. The mask depends on the grid alone, not on the driver parameters.
+// rows receives the x range [lo, hi) of each row j; returns the edge count.
+int64_t witness_slab(const Instance& in, int64_t T, int* k_out, std::vector<int>& rows) {
+    const pwfa_lbm_params& p = in.p;
+    const double zw = p.z0 + (double)T * p.dt - 3.0 * M_PI - (double)window_planes_at(p, T) * p.dx;
+    int k = (int)std::nearbyint(zw / p.dx - 0.5);  // half-way cases to even
+    k = std::min(std::max(k, 1), in.g.nz - 2);
+    *k_out = k;
+    rows.assign(2 * (size_t)in.g.ny, 0);
+    int64_t count = 0;
+    const double r2max = 1.0;
+    for (int j = 1; j < in.g.ny - 1; ++j) {
+        // squares kept in memory apart from the sum: no fused multiply-add
+        volatile double yy = ((double)j - 0.5 * (in.g.ny - 1)) * p.dx;
+        volatile double y2 = yy * yy;
+        int lo = -1, hi = -1;
+        for (int i = 1; i < in.g.nx - 1; ++i) {
+            volatile double xx = ((double)i - 0.5 * (in.g.nx - 1)) * p.dx;
+            volatile double x2 = xx * xx;
+            volatile double r2 = x2 + y2;
+            if (r2 <= r2max) {
+                if (lo < 0) lo = i;
+                hi = i + 1;
+            }
+        }
+        if (lo >= 0) {
+            rows[2 * j] = lo;
+            rows[2 * j + 1] = hi;
+            count += hi - lo;
+        }
+    }
+    return count;
+}
+
 int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_every) {
     cudaStream_t s = h->stream;
     if (in.p.moving_window) return fail(PWFA_ERR_PARAM, "the adjoint does not support the moving window");
@@ -641,21 +797,24 @@ int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_ever
     r.K = ckpt_every > 0 ? ckpt_every : (int)std::ceil(std::sqrt((double)nsteps));
     if (r.K > nsteps) r.K = nsteps;
     r.ncp = (int)((nsteps + r.K - 1) / r.K);
-    const size_t fb = fbytes_of(in), vb = vbytes_of(in);
+    const size_t fb = fbytes_of(in), vb = vbytes_of(in), gvb = gvbytes_of(in);
     r.cp_stride = fb + 6 * vb;
-    r.seg_stride = fb + 6 * vb;  // per step: populations, E, B (plus one trailing B)
+    r.seg_stride = fb + 6 * gvb;  // per step: populations, E, B (plus one trailing B)
     const size_t adj_bytes = 2 * align_up((size_t)in.g.Np * kPop * sizeof(float)) + 22 * vb +
                              align_up(sizeof(double) * (260 + 3 * kGradSlots));
-    if (cudaMalloc(&r.cp, r.cp_stride * (r.ncp + 1)) != cudaSuccess ||
-        cudaMalloc(&r.seg, r.seg_stride * r.K + 3 * vb) != cudaSuccess ||
-        cudaMalloc(&r.adj, adj_bytes) != cudaSuccess) {
+    if (dev_alloc((void**)&r.cp, r.cp_stride * (r.ncp + 1)) != cudaSuccess ||
+        dev_alloc((void**)&r.seg, r.seg_stride * r.K + 3 * gvb) != cudaSuccess ||
+        dev_alloc((void**)&r.adj, adj_bytes) != cudaSuccess) {
         cudaGetLastError();
         char buf[200];
         std::snprintf(buf, sizeof buf, "recording needs %.2f GB (%d checkpoints + %d segment states)",
-                      (r.cp_stride * (r.ncp + 1) + r.seg_stride * r.K + adj_bytes) / 1e9, r.ncp + 1, r.K);
+                      (r.cp_stride * (r.ncp + 1) + r.seg_stride * r.K + 3 * gvb + adj_bytes) / 1e9, r.ncp + 1,
+                      r.K);
         free_recording(in);
         return fail(PWFA_ERR_ALLOC, buf);
     }
+    // the guards in front of the segment's field slots stay zero
+    PWFA_CUDA(cudaMemsetAsync(r.seg, 0, r.seg_stride * r.K + 3 * gvb, s), "cudaMemsetAsync");
     int rc = reset_instance(in, s);
     if (rc) return rc;
     for (int32_t n = 0; n < nsteps; ++n) {
@@ -672,10 +831,16 @@ int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_ever
     return PWFA_OK;
 }
 
-int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* host_grad, int32_t n_grad) {
+int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, int32_t nsteps, int32_t ckpt_every,
+                     double* host_grad, int32_t n_grad) {
     cudaStream_t s = h->stream;
     auto& r = in.rec;
-    if (!r.valid) return fail(PWFA_ERR_STATE, "no recording: call pwfa_lbm_record first");
+    if (nsteps > 0 && (!r.valid || r.T != nsteps || (ckpt_every > 0 && r.K != std::min(ckpt_every, nsteps)))) {
+        // no recording of this run yet: record it now
+        int rc = record_instance(h, in, nsteps, ckpt_every);
+        if (rc) return rc;
+    }
+    if (!r.valid) return fail(PWFA_ERR_STATE, "no recording: pass nsteps >= 1 or call pwfa_lbm_record first");
     const int np = (int)in.profile.size();
     if (n_grad < 3 + np) return fail(PWFA_ERR_PARAM, "n_grad must be >= 3 + n_profile");
     if (np > 256) return fail(PWFA_ERR_PARAM, "the adjoint supports at most 256 profile points");
@@ -703,8 +868,22 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
     a.sz = (float)in.p.sigma_z;
     PWFA_CUDA(cudaMemsetAsync(r.adj, 0, (size_t)(p - (char*)r.adj) + sizeof(double) * (260 + 3 * kGradSlots), s),
               "cudaMemsetAsync");
-    for (int c = 0; c < 3; ++c)
-        PWFA_CUDA(cudaMemcpyAsync(Ebar[c], seed_E + c * N, sizeof(float) * N, cudaMemcpyDefault, s), "seed copy");
+    if (seed_E) {
+        for (int c = 0; c < 3; ++c)
+            PWFA_CUDA(cudaMemcpyAsync(Ebar[c], seed_E + c * N, sizeof(float) * N, cudaMemcpyDefault, s), "seed copy");
+    } else {
+        // the witness loss: dL/dE_z = -1/count on the slab, zero elsewhere
+        int k = 0;
+        std::vector<int> rows;
+        const int64_t count = witness_slab(in, r.T, &k, rows);
+        if (count == 0) return fail(PWFA_ERR_PARAM, "the witness slab holds no edge (grid narrower than r <= 1)");
+        PWFA_CUDA(cudaMemcpyAsync(in.d_wrows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, s),
+                  "witness rows copy");
+        PWFA_CUDA(launch_witness_seed(in.g, Ebar[2], k, in.d_wrows, (float)(-1.0 / (double)count), s),
+                  "witness seed kernel");
+        // the rows are read by the kernel before this call returns
+        PWFA_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    }
     if (!in.g.periodic) {
         // the adjoint keeps E_bar zero at the components the conducting walls
         // hold at zero; the seed's values there never enter the forward
@@ -723,9 +902,10 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
         const size_t fbs = fbytes_of(in);
         char* segp = static_cast<char*>(r.seg);
         auto f_slot = [&](int64_t j) -> void* { return segp + fbs * j; };
-        auto E_slot = [&](int64_t j, int c) -> float* { return (float*)(segp + fbs * r.K + vb * (3 * j + c)); };
+        const size_t gvb = gvbytes_of(in), gb = guard_bytes(in.g);
+        auto E_slot = [&](int64_t j, int c) -> float* { return (float*)(segp + fbs * r.K + gvb * (3 * j + c) + gb); };
         auto B_slot = [&](int64_t j, int c) -> float* {
-            return (float*)(segp + fbs * r.K + vb * 3 * r.K + vb * (3 * j + c));
+            return (float*)(segp + fbs * r.K + gvb * 3 * r.K + gvb * (3 * j + c) + gb);
         };
         // restore the checkpoint into state 0 of the segment
         {
@@ -793,7 +973,15 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, double* hos
             a.f = f;
             a.Sbar_in = Sbar[cur];
             a.Sbar_out = Sbar[1 - cur];
-            PWFA_CUDA(launch_adjoint_step(a, in.p.storage, in.p.collision, s), "adjoint step");
+            int rc = timed_launch(h, PWFA_KERNEL_ADJ_FIELD, "adjoint ampere kernel",
+                                  [&] { return launch_adjoint_ampere(a, s); });
+            if (rc) return rc;
+            rc = timed_launch(h, PWFA_KERNEL_ADJ_FLUID, "adjoint fluid kernel",
+                              [&] { return launch_adjoint_fluid(a, in.p.storage, in.p.collision, s); });
+            if (rc) return rc;
+            rc = timed_launch(h, PWFA_KERNEL_ADJ_FIELD, "adjoint field kernels",
+                              [&] { return launch_adjoint_fields(a, s); });
+            if (rc) return rc;
             cur = 1 - cur;
         }
     }
@@ -819,8 +1007,8 @@ int ensure_step_diag(pwfa_lbm* h) {
         need_e = std::max(need_e, faraday_energy_records(in.g));
     }
     if (!h->d_step_diag) {
-        if (cudaMalloc(&h->d_step_diag, sizeof(double) * 8 * h->inst.size()) != cudaSuccess ||
-            cudaMalloc(&h->d_step_scratch, sizeof(double) * 8 * kDiagBlocks) != cudaSuccess) {
+        if (dev_alloc((void**)&h->d_step_diag, sizeof(double) * 8 * h->inst.size()) != cudaSuccess ||
+            dev_alloc((void**)&h->d_step_scratch, sizeof(double) * 8 * kDiagBlocks) != cudaSuccess) {
             cudaGetLastError();
             return fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics results failed");
         }
@@ -829,7 +1017,7 @@ int ensure_step_diag(pwfa_lbm* h) {
         if (h->d_step_records) cudaFree(h->d_step_records);
         h->d_step_records = nullptr;
         h->step_records_cap = h->step_energy_cap = 0;
-        if (cudaMalloc(&h->d_step_records, sizeof(float) * (8 * need + need_e)) != cudaSuccess) {
+        if (dev_alloc((void**)&h->d_step_records, sizeof(float) * (8 * need + need_e)) != cudaSuccess) {
             cudaGetLastError();
             return fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics records failed");
         }
@@ -839,13 +1027,39 @@ int ensure_step_diag(pwfa_lbm* h) {
     return PWFA_OK;
 }
 
+// Debug builds: after a call that ran kernels, fail it with PWFA_ERR_STATE
+// if a kernel recorded an index outside its array (the word stays set).
+// Release builds return rc unchanged without touching the device.
+int debug_after(pwfa_lbm* h, int rc) {
+#ifdef PWFA_DEBUG
+    if (!h) return rc;
+    for (size_t i = 0; i < h->inst.size(); ++i) {
+        unsigned w[3] = {0, 0, 0};
+        if (cudaMemcpyAsync(w, h->inst[i].d_dbg, sizeof w, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "debug word copy");
+        if (w[0]) {
+            char buf[200];
+            std::snprintf(buf, sizeof buf,
+                          "debug build: instance %d, index %d out of range at site %u (%u accesses)", (int)i,
+                          (int)w[1], w[0], w[2]);
+            return fail(PWFA_ERR_STATE, buf);
+        }
+    }
+#else
+    (void)h;
+#endif
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char* pwfa_lbm_last_error(void) { return g_err.c_str(); }
 
-int pwfa_lbm_step_diag(pwfa_lbm_t* h, int32_t nsteps, double* host_diag) {
+static int step_diag_impl(pwfa_lbm_t* h, int32_t nsteps, double* host_diag) {
+    NvtxRange nvtx_("pwfa_lbm_step_diag");
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
     if (nsteps < 1 || !host_diag) return fail(PWFA_ERR_PARAM, "nsteps must be >= 1 and host_diag not NULL");
     int rc = pwfa_lbm_step(h, nsteps - 1);
@@ -881,7 +1095,12 @@ int pwfa_lbm_step_diag(pwfa_lbm_t* h, int32_t nsteps, double* host_diag) {
     return PWFA_OK;
 }
 
-int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckpt_every) {
+int pwfa_lbm_step_diag(pwfa_lbm_t* h, int32_t nsteps, double* host_diag) {
+    return debug_after(h, step_diag_impl(h, nsteps, host_diag));
+}
+
+static int record_impl(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckpt_every) {
+    NvtxRange nvtx_("pwfa_lbm_record");
     int rc = check_instance(h, instance);
     if (rc) return rc;
     if (nsteps < 1 || ckpt_every < 0) return fail(PWFA_ERR_PARAM, "nsteps must be >= 1 and ckpt_every >= 0");
@@ -889,15 +1108,47 @@ int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckp
     return record_instance(h, h->inst[instance], nsteps, ckpt_every);
 }
 
-int pwfa_lbm_adjoint_step(pwfa_lbm_t* h, int32_t instance, const float* seed_E, double* host_grad, int32_t n_grad) {
+int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckpt_every) {
+    return debug_after(h, record_impl(h, instance, nsteps, ckpt_every));
+}
+
+static int adjoint_impl(pwfa_lbm_t* h, int32_t instance, const float* seed_E, int32_t nsteps, int32_t ckpt_every,
+                        double* host_grad, int32_t n_grad) {
+    NvtxRange nvtx_("pwfa_lbm_adjoint_step");
     int rc = check_instance(h, instance);
     if (rc) return rc;
-    if (!seed_E || !host_grad) return fail(PWFA_ERR_PARAM, "seed_E and host_grad must not be NULL");
+    if (!host_grad) return fail(PWFA_ERR_PARAM, "host_grad must not be NULL");
+    if (nsteps < 0 || ckpt_every < 0) return fail(PWFA_ERR_PARAM, "nsteps and ckpt_every must be >= 0");
     h->batch_valid = false;
-    return adjoint_instance(h, h->inst[instance], seed_E, host_grad, n_grad);
+    return adjoint_instance(h, h->inst[instance], seed_E, nsteps, ckpt_every, host_grad, n_grad);
+}
+
+int pwfa_lbm_adjoint_step(pwfa_lbm_t* h, int32_t instance, const float* seed_E, int32_t nsteps, int32_t ckpt_every,
+                          double* host_grad, int32_t n_grad) {
+    return debug_after(h, adjoint_impl(h, instance, seed_E, nsteps, ckpt_every, host_grad, n_grad));
+}
+
+int pwfa_lbm_witness_loss(pwfa_lbm_t* h, int32_t instance, double* host_loss) {
+    int rc = check_instance(h, instance);
+    if (rc) return rc;
+    if (!host_loss) return fail(PWFA_ERR_PARAM, "host_loss must not be NULL");
+    Instance& in = h->inst[instance];
+    int k = 0;
+    std::vector<int> rows;
+    const int64_t count = witness_slab(in, in.steps, &k, rows);
+    if (count == 0) return fail(PWFA_ERR_PARAM, "the witness slab holds no edge (grid narrower than r <= 1)");
+    PWFA_CUDA(cudaMemcpyAsync(in.d_wrows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, h->stream),
+              "witness rows copy");
+    PWFA_CUDA(launch_witness_sum(in.g, in.E[2], k, in.d_wrows, in.d_wout, h->stream), "witness sum kernel");
+    double sum = 0.0;
+    PWFA_CUDA(cudaMemcpyAsync(&sum, in.d_wout, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync");
+    PWFA_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    *host_loss = -sum / (double)count;
+    return PWFA_OK;
 }
 
 int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances, void* cuda_stream, pwfa_lbm_t** out) {
+    NvtxRange nvtx_("pwfa_lbm_create");
     if (!out) return fail(PWFA_ERR_PARAM, "out is NULL");
     *out = nullptr;
     if (!params || n_instances < 1) return fail(PWFA_ERR_PARAM, "params is NULL or n_instances < 1");
@@ -925,7 +1176,7 @@ int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances, void* cu
         rc = alloc_instance(in, h->stream);
     }
     if (rc == PWFA_OK) {
-        if (cudaMalloc(&h->d_partials, sizeof(double) * 8 * (kDiagBlocks + 1)) != cudaSuccess) {
+        if (dev_alloc((void**)&h->d_partials, sizeof(double) * 8 * (kDiagBlocks + 1)) != cudaSuccess) {
             cudaGetLastError();
             rc = fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics buffer failed");
         } else {
@@ -946,7 +1197,8 @@ int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances, void* cu
     return PWFA_OK;
 }
 
-int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps) {
+static int step_impl(pwfa_lbm_t* h, int32_t nsteps) {
+    NvtxRange nvtx_("pwfa_lbm_step");
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
     if (nsteps < 0) return fail(PWFA_ERR_PARAM, "nsteps must be >= 0");
     if (batch_eligible(h)) return batch_steps(h, nsteps);
@@ -958,7 +1210,9 @@ int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps) {
     return PWFA_OK;
 }
 
-int pwfa_lbm_fields(pwfa_lbm_t* h, int32_t instance, uint32_t mask, float* out, int64_t out_elems,
+int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps) { return debug_after(h, step_impl(h, nsteps)); }
+
+static int fields_impl(pwfa_lbm_t* h, int32_t instance, uint32_t mask, float* out, int64_t out_elems,
                     double* host_diag) {
     int rc = check_instance(h, instance);
     if (rc) return rc;
@@ -998,6 +1252,11 @@ int pwfa_lbm_fields(pwfa_lbm_t* h, int32_t instance, uint32_t mask, float* out, 
         }
     }
     return PWFA_OK;
+}
+
+int pwfa_lbm_fields(pwfa_lbm_t* h, int32_t instance, uint32_t mask, float* out, int64_t out_elems,
+                    double* host_diag) {
+    return debug_after(h, fields_impl(h, instance, mask, out, out_elems, host_diag));
 }
 
 int pwfa_lbm_linecut(pwfa_lbm_t* h, int32_t instance, double r, double n_star, float* out, int64_t out_elems,
@@ -1108,7 +1367,7 @@ int pwfa_lbm_set_particles(pwfa_lbm_t* h, int32_t instance, int64_t n, const flo
     in.particles = nullptr;
     in.np = 0;
     if (n > 0) {
-        if (cudaMalloc(&in.particles, sizeof(float) * 6 * (size_t)n) != cudaSuccess) {
+        if (dev_alloc((void**)&in.particles, sizeof(float) * 6 * (size_t)n) != cudaSuccess) {
             cudaGetLastError();
             return fail(PWFA_ERR_ALLOC, "cudaMalloc of the particle array failed");
         }
@@ -1255,6 +1514,7 @@ int pwfa_lbm_set_field_fusion(pwfa_lbm_t* h, int32_t mode) {
     if (mode != PWFA_FUSION_OFF && mode != PWFA_FUSION_AUTO && mode != PWFA_FUSION_ON)
         return fail(PWFA_ERR_PARAM, "unknown field-fusion mode");
     h->field_fusion = mode;
+    h->batch_valid = false;  // the batched graph holds the field step's form
     return PWFA_OK;
 }
 
@@ -1282,6 +1542,7 @@ int pwfa_lbm_destroy(pwfa_lbm_t* h) {
     batch_release(h);
     if (h->d_entries) cudaFree(h->d_entries);
     if (h->d_steps) cudaFree(h->d_steps);
+    if (h->d_tile_inst) cudaFree(h->d_tile_inst);
     if (h->d_step_records) cudaFree(h->d_step_records);
     if (h->d_step_diag) cudaFree(h->d_step_diag);
     if (h->d_step_scratch) cudaFree(h->d_step_scratch);

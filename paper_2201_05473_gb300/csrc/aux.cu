@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kBX * kBY) export_f_kernel(const StepArgs a, f
     const int64_t node = ((int64_t)z * g.ny + y) * g.nx + x;
     float f[kL][kQ];
     bool bnd;
-    gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+    gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, 0u, a.dbg);
     if (!PER && bnd) {
         float A[kL], inn, beta[3], phi[kQ];
         node_moments(f, a.n_floor, A, inn, beta);
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kBX * kBY) export_fields_kernel(const StepArgs
     if (mask & 0xE00Fu) {
         float f[kL][kQ];
         bool bnd;
-        gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+        gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, 0u, a.dbg);
         float A[kL], inn, beta[3];
         node_moments(f, a.n_floor, A, inn, beta);
         vals[0] = A[0];
@@ -130,11 +130,11 @@ __global__ void __launch_bounds__(kBX * kBY) export_fields_kernel(const StepArgs
     const bool raw = (mask >> 31) & 1u;
     if (mask & 0x70u) {
         if (raw) { for (int c = 0; c < 3; ++c) vals[4 + c] = a.E[c][node]; }
-        else { float e[3]; node_E<PER>(g, a.E, x, y, z, e); for (int c = 0; c < 3; ++c) vals[4 + c] = e[c]; }
+        else { float e[3]; node_E<PER>(g, a.E, x, y, z, e, a.dbg); for (int c = 0; c < 3; ++c) vals[4 + c] = e[c]; }
     }
     if (mask & 0x380u) {
         if (raw) { for (int c = 0; c < 3; ++c) vals[7 + c] = a.Bc[c][node]; }
-        else { float b[3]; node_B_sum<PER>(g, a.Bc, x, y, z, b); for (int c = 0; c < 3; ++c) vals[7 + c] = 0.25f * b[c]; }
+        else { float b[3]; node_B_sum<PER>(g, a.Bc, x, y, z, b, a.dbg); for (int c = 0; c < 3; ++c) vals[7 + c] = 0.25f * b[c]; }
     }
     if (mask & 0x1C00u) { for (int c = 0; c < 3; ++c) vals[10 + c] = a.J[c][node]; }
     int slot = 0;
@@ -163,11 +163,11 @@ __global__ void linecut_kernel(const StepArgs a, double xr, float* out) {
         const float wgt = ((c & 1) ? fx : 1.0f - fx) * ((c >> 1) ? fy : 1.0f - fy);
         float f[kL][kQ];
         bool bnd;
-        gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+        gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, 0u, a.dbg);
         float A[kL], inn, beta[3];
         node_moments(f, a.n_floor, A, inn, beta);
         float e[3];
-        node_E<PER>(g, a.E, x, y, z, e);
+        node_E<PER>(g, a.E, x, y, z, e, a.dbg);
         nsum += wgt * A[0];
         esum += wgt * e[2];
     }
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_kernel(const StepArgs a, do
         node_xyz(g, node, x, y, z);
         float f[kL][kQ];
         bool bnd;
-        gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd);
+        gather<ST, PER>(g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, 0u, a.dbg);
         float A[kL], inn, beta[3];
         node_moments(f, a.n_floor, A, inn, beta);
         const bool fin = isfinite(A[0]) && isfinite(A[1]) && isfinite(A[2]) && isfinite(A[3]);
@@ -278,7 +278,48 @@ __global__ void __launch_bounds__(kDiagThreads) diag_chunk_kernel(const float* r
 
 dim3 node_grid(const Grid& g) { return dim3((g.nx + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz); }
 
+// Witness slab: the x range [rows[2 j], rows[2 j + 1]) of each row j in plane
+// k. One block sums E_z over it in FP64 (the slab holds at most a few
+// thousand edges).
+constexpr int kWitnessThreads = 256;
+__global__ void __launch_bounds__(kWitnessThreads) witness_sum_kernel(Grid g, const float* Ez, int k,
+                                                                      const int* rows, double* out) {
+    double s = 0.0;
+    const int64_t plane = (int64_t)k * g.nx * g.ny;
+    for (int j = 0; j < g.ny; ++j) {
+        const int lo = rows[2 * j], hi = rows[2 * j + 1];
+        for (int i = lo + (int)threadIdx.x; i < hi; i += kWitnessThreads) s += Ez[plane + (int64_t)j * g.nx + i];
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    __shared__ double sh[kWitnessThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kWitnessThreads / 32; ++w) t += sh[w];
+        *out = t;
+    }
+}
+
+// Ez_bar := value on the witness slab (the rest of the array is untouched).
+__global__ void witness_seed_kernel(Grid g, float* Ezbar, int k, const int* rows, float value) {
+    const int j = blockIdx.x;
+    const int lo = rows[2 * j], hi = rows[2 * j + 1];
+    const int64_t row = ((int64_t)k * g.ny + j) * g.nx;
+    for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) Ezbar[row + i] = value;
+}
+
 }  // namespace
+
+cudaError_t launch_witness_sum(const Grid& g, const float* Ez, int k, const int* rows, double* out, cudaStream_t s) {
+    witness_sum_kernel<<<1, kWitnessThreads, 0, s>>>(g, Ez, k, rows, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_witness_seed(const Grid& g, float* Ezbar, int k, const int* rows, float value, cudaStream_t s) {
+    witness_seed_kernel<<<g.ny, 128, 0, s>>>(g, Ezbar, k, rows, value);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_diag_finish_step(const DiagOut& d, int64_t nrec, cudaStream_t s) {
     int64_t chunks = (nrec + 1023) / 1024;

@@ -13,6 +13,7 @@
 
 namespace pwfa {
 int set_error(int code, const std::string& msg);  // api.cu
+cudaError_t dev_alloc(void** p, size_t bytes);    // api.cu
 }
 
 using pwfa::set_error;
@@ -166,7 +167,7 @@ int pwfa_axi_create(const pwfa_axi_params* params, void* cuda_stream, pwfa_axi_t
     const size_t fbytes = align_up(sizeof(float) * 27 * (size_t)h->Np);
     const size_t vb = align_up(sizeof(float) * (size_t)h->N);
     const size_t total = 2 * fbytes + 3 * vb + 6 * vb + 6 * vb;  // f x2, moments, E 2 + B 2 + J 2, staging
-    if (cudaMalloc(&h->arena, total) != cudaSuccess) {
+    if (pwfa::dev_alloc((void**)&h->arena, total) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return set_error(PWFA_ERR_ALLOC, "cudaMalloc of the axisymmetric state failed");

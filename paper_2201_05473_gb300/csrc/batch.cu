@@ -1,105 +1,106 @@
-// Batched form: many independent instances of uneven grid sizes advanced by
-// one persistent launch per phase (Faraday, fused fluid, Ampere) over a
-// flattened work list of (instance, tile) items, replayed from a captured
-// CUDA graph. Each tile is 128 nodes of one z-plane in the instance's
-// autotuned shape (bx x by, bx * by = 128). No inter-CTA waits.
+// Batched form: many independent instances of uneven grid sizes advanced
+// together, one launch per phase for all of them, two steps replayed from a
+// captured CUDA graph. Each phase is one grid over the concatenated tiles of
+// every instance (per-node phases: groups of 128-node tiles of one z-plane
+// in the instance's autotuned shape; fused field step: the z-marching tiles
+// of fields_fused.cuh); a 16-bit table maps each block to its instance. The hardware block
+// scheduler hands the tiles out in order, so the tiles in flight form one
+// short window of the list and the z +- 1 planes a pull reads are still in
+// L2. No block waits on another.
 #include "lbm_batch.h"
-#include "lbm_kernels.h"
-#include "fields_node.cuh"
+#include "fields_fused.cuh"
 #include "fluid_node.cuh"
 
 namespace pwfa {
 
 namespace {
 
-constexpr int kThreads = kBatchTile;
+static_assert(sizeof(StepArgs) % 4 == 0 && sizeof(StepArgs) / 4 <= kBatchTile, "StepArgs copy");
+static_assert(sizeof(FieldPair) % 4 == 0 && sizeof(FieldPair) / 4 <= kBatchTile, "FieldPair copy");
 
-// The instance table lives in constant memory: every thread of a CTA reads
-// the same entry (broadcast), so no shared-memory copy and no barrier is
-// needed anywhere in the kernel.
-__constant__ BatchEntry c_entries[kMaxBatch];
-static_assert(sizeof(BatchEntry) * kMaxBatch <= 60 * 1024, "instance table exceeds constant memory");
+// The block's instance arguments, copied once into shared memory (every
+// thread reads them).
+template <int NT>
+__device__ __forceinline__ void copy_words(void* dst, const void* src, int bytes, int tid) {
+    for (int w = tid; w < bytes / 4; w += NT) static_cast<int*>(dst)[w] = __ldg(static_cast<const int*>(src) + w);
+}
 
-// Resident blocks per SM: the fluid phase as the single-instance fluid
-// kernel (FluidOcc: 96 or 128 registers); the light field phases run 8
-// blocks (64 registers).
-template <int PHASE, int COLL>
-struct PhaseOcc {
-    static constexpr int blocks = PHASE == 1 ? FluidOcc<COLL>::blocks : 8;
-};
+// Node (x, y, z) of thread tid in fluid tile `local` of an instance.
+__device__ __forceinline__ void tile_node(const BatchEntry& e, int64_t local, int tid, int& x, int& y, int& z) {
+    const int per_plane = e.tiles_x * e.tiles_y;
+    z = (int)(local / per_plane);
+    const int r = (int)(local - (int64_t)z * per_plane);
+    const int ty = r / e.tiles_x;
+    x = (r - ty * e.tiles_x) * e.bx + tid % e.bx;
+    y = ty * e.by + tid / e.bx;
+}
 
-// Work items are handed out in order by a global counter (one atomic per
-// grab, prefetched one grab ahead), so the items in flight always form one
-// short window of the work list, as with a hardware-scheduled grid: the
-// planes pulled across (z - 1, z + 1) are still in L2 when their neighbours
-// run, however unevenly the CTAs progress. Items only grow within a CTA, so
-// each CTA walks the instance table forward. The fluid phase grabs one item
-// at a time; the light field phases grab kFieldGrab consecutive items.
-constexpr int kFieldGrab = 4;
+// Driver time of the instance's Ampere launch of this parity, and the
+// counter of the other parity advanced by the instance's first tile.
+__device__ __forceinline__ float driver_centre(const BatchEntry& e, int parity, bool first) {
+    const int64_t n = e.step[parity];
+    if (first) e.step[parity ^ 1] = n + 1;
+    return (float)(e.z0 + (double)(n + 1) * e.dt);
+}
 
+// Phases 0-2 on the fluid tiles: Faraday, the fluid step, Ampere. A block
+// takes kBatchGroup consecutive tiles of one instance.
 template <int ST, int COLL, bool PER, int PHASE>
-__global__ void __launch_bounds__(kThreads, PhaseOcc<PHASE, COLL>::blocks) batch_kernel(int ninst, int nitems,
-                                                                                  int parity, int* counter) {
-    constexpr int grab = PHASE == 1 ? 1 : kFieldGrab;
-    __shared__ int s_next[2];
-    if (threadIdx.x == 0) s_next[0] = atomicAdd(counter, grab);
+__global__ void __launch_bounds__(kBatchTile, PHASE == 1 ? FluidOcc<COLL>::blocks : 8)
+    batch_node_kernel(const BatchEntry* __restrict__ ent, const uint16_t* __restrict__ tile_inst, int parity) {
+    __shared__ StepArgs sa;
+    __shared__ float s_zc;
+    const int tid = threadIdx.x;
+    const int inst = __ldg(tile_inst + blockIdx.x);
+    const BatchEntry& e = ent[inst];
+    copy_words<kBatchTile>(&sa, &e.args[parity], sizeof(StepArgs), tid);
+    const int64_t t0 = ((int64_t)blockIdx.x - e.tile_begin) * kBatchGroup;
+    if (PHASE == 2 && tid == 0) s_zc = driver_centre(e, parity, t0 == 0);
     __syncthreads();
-    // only the instance range is carried between items; the tile shape is
-    // re-read from the (broadcast) constant table to keep registers free
-    int inst = -1, begin = 0, end = 0;
-    float zc = 0.0f;
-    for (int buf = 0;; buf ^= 1) {
-        const int first = s_next[buf];
-        if (first >= nitems) break;
-        if (threadIdx.x == 0) s_next[buf ^ 1] = atomicAdd(counter, grab);
-        const int last = first + grab < nitems ? first + grab : nitems;
-        for (int item = first; item < last; ++item) {
-            if (item >= end) {
-                do {
-                    ++inst;
-                    begin = (int)c_entries[inst].item_begin;
-                    end = inst + 1 < ninst ? (int)c_entries[inst + 1].item_begin : nitems;
-                } while (item >= end);
-                if (PHASE == 2)
-                    zc = (float)(c_entries[inst].z0 + (double)(*c_entries[inst].step + 1) * c_entries[inst].dt);
-            }
-            const BatchEntry& e = c_entries[inst];
-            const int local = item - begin;
-            const int per_plane = e.tiles_x * e.tiles_y;
-            const int z = local / per_plane;
-            const int r = local - z * per_plane;
-            const int ty = r / e.tiles_x;
-            const int bx = e.bx;
-            const int x = (r - ty * e.tiles_x) * bx + (int)threadIdx.x % bx;
-            const int y = ty * (kThreads / bx) + (int)threadIdx.x / bx;
-            const StepArgs& a = c_entries[inst].args[parity];
-            if (x < a.g.nx && y < a.g.ny) {
-                if (PHASE == 0) faraday_node<PER>(a, x, y, z);
-                else if (PHASE == 1) fluid_node<ST, COLL, PER>(a, x, y, z);
-                else ampere_node<PER>(a, x, y, z, zc);
-            }
-        }
-        // every thread has read s_next[buf]; the next grab is visible
-        __syncthreads();
+    const int64_t t1 = t0 + kBatchGroup < e.ntiles ? t0 + kBatchGroup : e.ntiles;
+    for (int64_t t = t0; t < t1; ++t) {
+        int x, y, z;
+        tile_node(e, t, tid, x, y, z);
+        if (x >= sa.g.nx || y >= sa.g.ny) continue;
+        if (PHASE == 0) faraday_node<PER>(sa, x, y, z);
+        else if (PHASE == 1) fluid_node<ST, COLL, PER>(sa, x, y, z);
+        else ampere_node<PER>(sa, x, y, z, s_zc);
     }
 }
 
-// Advance the step counters and re-arm the phases' work counters.
-__global__ void batch_advance_kernel(const BatchEntry* ent, int ninst, int* counters) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ninst) *ent[i].step += 1;
-    if (i < kBatchCounters) counters[i] = 0;
+// Phase 3 on the fused-field tiles: Ampere of this step with Faraday of the
+// next.
+template <bool PER>
+__global__ void __launch_bounds__(kAFX * kAFY, PWFA_AF_MIN_BLOCKS)
+    batch_fields_kernel(const BatchEntry* __restrict__ ent, const uint16_t* __restrict__ ftile_inst, int parity) {
+    __shared__ StepArgs sa;
+    __shared__ FieldPair so;
+    __shared__ float s_zc;
+    const int tid = threadIdx.y * kAFX + threadIdx.x;
+    const int inst = __ldg(ftile_inst + blockIdx.x);
+    const BatchEntry& e = ent[inst];
+    copy_words<kAFX * kAFY>(&sa, &e.args[parity], sizeof(StepArgs), tid);
+    copy_words<kAFX * kAFY>(&so, &e.out[parity], sizeof(FieldPair), tid);
+    const int64_t local = (int64_t)blockIdx.x - e.ftile_begin;
+    if (tid == 0) s_zc = driver_centre(e, parity, local == 0);
+    __syncthreads();
+    const int per_slab = e.ftiles_x * e.ftiles_y;
+    const int tbz = (int)(local / per_slab);
+    const int r = (int)(local - (int64_t)tbz * per_slab);
+    const int tby = r / e.ftiles_x;
+    ampere_faraday_tile<PER>(sa, so, r - tby * e.ftiles_x, tby, tbz, s_zc);
 }
 
 template <int ST, int COLL, bool PER>
 cudaError_t launch_phase(const BatchLaunch& b, int phase, int parity, cudaStream_t s) {
-    const int g1 = b.grid;                                     // fluid phase
-    const int gf = b.grid / PhaseOcc<1, COLL>::blocks * PhaseOcc<0, COLL>::blocks;  // field phases
+    const unsigned nt = (unsigned)b.ntiles;
     switch (phase) {
-        case 0: batch_kernel<ST, COLL, PER, 0><<<gf, kThreads, 0, s>>>(b.ninst, (int)b.nitems, parity, b.counters); break;
-        case 1: batch_kernel<ST, COLL, PER, 1><<<g1, kThreads, 0, s>>>(b.ninst, (int)b.nitems, parity, b.counters + 1); break;
-        case 2: batch_kernel<ST, COLL, PER, 2><<<gf, kThreads, 0, s>>>(b.ninst, (int)b.nitems, parity, b.counters + 2); break;
-        case 3: batch_advance_kernel<<<(b.ninst + 127) / 128, 128, 0, s>>>(b.entries, b.ninst, b.counters); break;
+        case 0: batch_node_kernel<ST, COLL, PER, 0><<<nt, kBatchTile, 0, s>>>(b.entries, b.tile_inst, parity); break;
+        case 1: batch_node_kernel<ST, COLL, PER, 1><<<nt, kBatchTile, 0, s>>>(b.entries, b.tile_inst, parity); break;
+        case 2: batch_node_kernel<ST, COLL, PER, 2><<<nt, kBatchTile, 0, s>>>(b.entries, b.tile_inst, parity); break;
+        case 3:
+            batch_fields_kernel<PER><<<(unsigned)b.nftiles, dim3(kAFX, kAFY, 1), 0, s>>>(b.entries, b.ftile_inst, parity);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -125,36 +126,13 @@ cudaError_t launch_phase_c(const BatchLaunch& b, int phase, int parity, int coll
 
 cudaError_t launch_batch_phase(const BatchLaunch& b, int phase, int parity, int storage, int collision,
                                bool periodic, cudaStream_t s) {
+    if (b.ntiles > INT32_MAX || b.nftiles > INT32_MAX) return cudaErrorInvalidConfiguration;
     switch (storage) {
         case 0: return launch_phase_c<0>(b, phase, parity, collision, periodic, s);
         case 1: return launch_phase_c<1>(b, phase, parity, collision, periodic, s);
         case 2: return launch_phase_c<2>(b, phase, parity, collision, periodic, s);
     }
     return cudaErrorInvalidValue;
-}
-
-cudaError_t batch_upload_table(const BatchEntry* host, int n, cudaStream_t s) {
-    if (n > kMaxBatch) return cudaErrorInvalidValue;
-    return cudaMemcpyToSymbolAsync(c_entries, host, sizeof(BatchEntry) * n, 0, cudaMemcpyHostToDevice, s);
-}
-
-cudaError_t batch_grid_size(int storage, int collision, bool periodic, int* grid) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    // occupancy of the heaviest phase (the fluid kernel) sets the persistent grid
-    const void* fn = nullptr;
-#define PWFA_BATCH_FN(ST_, C_)                                                          \
-    fn = periodic ? (const void*)batch_kernel<ST_, C_, true, 1> : (const void*)batch_kernel<ST_, C_, false, 1>
-    if (storage == 0) { if (collision == 0) PWFA_BATCH_FN(0, 0); else if (collision == 1) PWFA_BATCH_FN(0, 1); else PWFA_BATCH_FN(0, 2); }
-    else if (storage == 1) { if (collision == 0) PWFA_BATCH_FN(1, 0); else if (collision == 1) PWFA_BATCH_FN(1, 1); else PWFA_BATCH_FN(1, 2); }
-    else { if (collision == 0) PWFA_BATCH_FN(2, 0); else if (collision == 1) PWFA_BATCH_FN(2, 1); else PWFA_BATCH_FN(2, 2); }
-#undef PWFA_BATCH_FN
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0);
-    if (e != cudaSuccess) return e;
-    *grid = sms * (per_sm > 0 ? per_sm : 1);
-    return cudaSuccess;
 }
 
 }  // namespace pwfa

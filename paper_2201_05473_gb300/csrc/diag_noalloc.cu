@@ -149,12 +149,14 @@ extern "C" int pwfa_lbm_diag_noalloc(int32_t nx, int32_t ny, int32_t nz, double 
                                std::to_string((int64_t)kMaxBlocks * kNodesPerBlock) + " nodes");
     if (!dev_f || !dev_E || !dev_B || !dev_out) return pwfa::set_error(PWFA_ERR_PARAM, "null pointer argument");
     if (!(dx > 0)) return pwfa::set_error(PWFA_ERR_PARAM, "dx must be > 0");
+    // as pwfa_lbm_create: 0 selects the default floor, a negative or NaN one is an error
+    if (!(n_floor >= 0)) return pwfa::set_error(PWFA_ERR_PARAM, "n_floor must be >= 0");
     double* scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int nblocks = (int)((N + kNodesPerBlock - 1) / kNodesPerBlock);
-    const float floor_f = (float)(n_floor > 0 ? n_floor : 1e-6);
+    const float floor_f = (float)(n_floor == 0 ? 1e-6 : n_floor);
     diag_noalloc_kernel<<<nblocks, kThreads, 0, s>>>(N, dx * dx * dx, floor_f, dev_f, dev_E, dev_B, scratch);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {

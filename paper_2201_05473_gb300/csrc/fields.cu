@@ -3,7 +3,7 @@
 // Faraday, the moving window's field move and the wall-zeroing helper used
 // after a state import.
 #include "lbm_kernels.h"
-#include "fields_node.cuh"
+#include "fields_fused.cuh"
 
 namespace pwfa {
 
@@ -67,71 +67,10 @@ __global__ void __launch_bounds__(kBX * kBY) ampere_kernel(const StepArgs a) {
     ampere_node<PER>(a, i, j, blockIdx.z, a.zc);
 }
 
-// Ampere of step n fused with Faraday of step n+1 (rigid driver):
-// E_{n+3/2} = E_{n+1/2} + (dt/dx) curl_h B_{n+1} - dt (J + J_b) into out.E
-// (the other E buffer), then B_{n+2} = B_{n+1} - (dt/dx) curl_h E_{n+3/2}
-// into out.B (the buffer of B_n, which no later kernel reads). B_{n+1} is
-// read once for both, so the pair moves 60 B per node instead of 84. A
-// block of kAFX x kAFY threads owns a tile of (kAFX - 1) x (kAFY - 1) nodes
-// over kAFZ planes and marches up z: each thread evaluates E_{n+3/2} at its
-// position (the last row and column are the +x / +y neighbours the tile's
-// Faraday reads, evaluated again by their owner), two planes of it kept in
-// shared memory, and once plane k is there Faraday runs on plane k - 1.
-#ifndef PWFA_AF_Y
-#define PWFA_AF_Y 8
-#endif
-#ifndef PWFA_AF_Z
-#define PWFA_AF_Z 16
-#endif
-constexpr int kAFX = 32, kAFY = PWFA_AF_Y, kAFZ = PWFA_AF_Z;
-
 template <bool PER>
-__global__ void __launch_bounds__(kAFX * kAFY, 5) ampere_faraday_kernel(const StepArgs a, const FieldPair out) {
-    const Grid& g = a.g;
-    __shared__ float sE[2][3][kAFY][kAFX];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x = blockIdx.x * (kAFX - 1) + tx, y = blockIdx.y * (kAFY - 1) + ty;
-    const bool own = tx < kAFX - 1 && ty < kAFY - 1 && x < g.nx && y < g.ny;
-    // the evaluated position: wrapped on periodic grids; none outside an open one
-    const bool inxy = PER || (x < g.nx && y < g.ny);
-    const int xe = PER ? x % g.nx : x, ye = PER ? y % g.ny : y;
-    const int kz0 = blockIdx.z * kAFZ, kend = min(kz0 + kAFZ, g.nz);
-    const float jb0[3] = {0.0f, 0.0f, 0.0f};
-    float bprev[3] = {0.0f, 0.0f, 0.0f};  // B_{n+1} at the own index of the previous plane
-    for (int k = kz0; k <= kend; ++k) {
-        const int buf = (k - kz0) & 1;
-        float en[3] = {0.0f, 0.0f, 0.0f}, bo[3] = {0.0f, 0.0f, 0.0f};
-        if (inxy && (PER || k < g.nz)) {
-            const int ke = PER ? k % g.nz : k;
-            const AmpereIn v = ampere_loads<PER>(a, xe, ye, ke);
-            bool act[3];
-            ampere_compute<PER>(a, xe, ye, ke, a.zc, v, jb0, en, act);
-            bo[0] = v.bx;
-            bo[1] = v.by;
-            bo[2] = v.bz;
-            if (own && k < kend) {
-                const int64_t o = ((int64_t)k * g.ny + y) * g.nx + x;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) out.E[c][o] = en[c];
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) sE[buf][c][ty][tx] = en[c];
-        __syncthreads();
-        if (k > kz0 && own) {
-            const int pb = buf ^ 1;
-            float bn[3];
-            faraday_values<PER>(g, a.cdt, x, y, k - 1, bprev, sE[pb][0][ty][tx], sE[pb][1][ty][tx],
-                                sE[pb][2][ty][tx], sE[pb][2][ty + 1][tx], sE[buf][1][ty][tx], sE[buf][0][ty][tx],
-                                sE[pb][2][ty][tx + 1], sE[pb][1][ty][tx + 1], sE[pb][0][ty + 1][tx], bn);
-            const int64_t o = ((int64_t)(k - 1) * g.ny + y) * g.nx + x;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) out.B[c][o] = bn[c];
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) bprev[c] = bo[c];
-        __syncthreads();
-    }
+__global__ void __launch_bounds__(kAFX * kAFY, PWFA_AF_MIN_BLOCKS)
+    ampere_faraday_kernel(const StepArgs a, const FieldPair out) {
+    ampere_faraday_tile<PER>(a, out, blockIdx.x, blockIdx.y, blockIdx.z, a.zc);
 }
 
 __global__ void __launch_bounds__(kBX * kBY) zero_walls_kernel(const StepArgs a) {
@@ -225,6 +164,12 @@ cudaError_t launch_faraday(const StepArgs& a, cudaStream_t s, float* energy) {
     } else if (a.g.periodic) faraday_kernel<true><<<grid, block, 0, s>>>(a);
     else faraday_kernel<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+void fused_field_tiles(const Grid& g, int* tx, int* ty, int* tz) {
+    *tx = (g.nx + kAFX - 2) / (kAFX - 1);
+    *ty = (g.ny + kAFY - 2) / (kAFY - 1);
+    *tz = (g.nz + kAFZ - 1) / kAFZ;
 }
 
 cudaError_t launch_ampere_faraday(const StepArgs& a, const FieldPair& out, cudaStream_t s) {

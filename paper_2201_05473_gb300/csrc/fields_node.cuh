@@ -30,9 +30,22 @@ __device__ __forceinline__ int up1(int i, int n) { return PER ? i + 1 : min(i + 
 template <bool PER>
 __device__ __forceinline__ int dn1(int i) { return PER ? i - 1 : max(i - 1, 0); }
 
+// Faraday's arithmetic for the three B components stored at one index, given
+// the E values it reads (own index and the +1 neighbours), the old B and
+// which components are active: Bn = Bc - (dt/dx) curl_h E, zero on the walls.
+// Every Faraday kernel goes through it, so they agree bit for bit.
+__device__ __forceinline__ void faraday_arith(float c, const float (&b)[3], float ex, float ey, float ez, float ez_j,
+                                              float ey_k, float ex_k, float ez_i, float ey_i, float ex_j, bool cx,
+                                              bool cy, bool cz, float (&bn)[3]) {
+    bn[0] = cx ? b[0] - c * ((ez_j - ez) - (ey_k - ey)) : 0.0f;
+    bn[1] = cy ? b[1] - c * ((ex_k - ex) - (ez_i - ez)) : 0.0f;
+    bn[2] = cz ? b[2] - c * ((ey_i - ey) - (ex_j - ex)) : 0.0f;
+}
+
 // Faraday's update of the three B components stored at node (i, j, k) from
-// the E values it reads (own index and the +1 neighbours) and the old B:
-// Bn = Bc - (dt/dx) curl_h E on the active faces, zero on the walls.
+// the E values it reads and the old B; B_x is active on the faces with
+// 1 <= i <= nx-2, j <= ny-2, k <= nz-2 of an open grid (cyclically for B_y,
+// B_z), every face of a periodic one.
 template <bool PER>
 __device__ __forceinline__ void faraday_values(const Grid& g, float c, int i, int j, int k, const float (&b)[3],
                                                float ex, float ey, float ez, float ez_j, float ey_k, float ex_k,
@@ -41,16 +54,36 @@ __device__ __forceinline__ void faraday_values(const Grid& g, float c, int i, in
     const bool cx = PER || (i >= 1 && i <= nx - 2 && j <= ny - 2 && k <= nz - 2);
     const bool cy = PER || (i <= nx - 2 && j >= 1 && j <= ny - 2 && k <= nz - 2);
     const bool cz = PER || (i <= nx - 2 && j <= ny - 2 && k >= 1 && k <= nz - 2);
-    bn[0] = cx ? b[0] - c * ((ez_j - ez) - (ey_k - ey)) : 0.0f;
-    bn[1] = cy ? b[1] - c * ((ex_k - ex) - (ez_i - ez)) : 0.0f;
-    bn[2] = cz ? b[2] - c * ((ey_i - ey) - (ex_j - ex)) : 0.0f;
+    faraday_arith(c, b, ex, ey, ez, ez_j, ey_k, ex_k, ez_i, ey_i, ex_j, cx, cy, cz, bn);
+}
+
+// The rigid driver's density n_b = alpha exp(-r^2/(2 sigma_r^2))
+// exp(-(z - zc)^2/(2 sigma_z^2)) at the E_z edge (i, j, k + 1/2), as the
+// product of a transverse factor (alpha included) and a longitudinal one:
+// the fused field kernel takes the first once per (x, y) column and the
+// second once per plane, and every kernel that evaluates J_b = -n_b forms
+// the same product.
+__device__ __forceinline__ float driver_transverse(const StepArgs& a, int i, int j) {
+    const float xr = ((float)i - 0.5f * (float)(a.g.nx - 1)) * a.dx;
+    const float yr = ((float)j - 0.5f * (float)(a.g.ny - 1)) * a.dx;
+    return a.alpha * expf(-(xr * xr + yr * yr) * a.inv2sr2);
+}
+__device__ __forceinline__ float driver_longitudinal(const StepArgs& a, int k, float zc) {
+    const float zeta = ((float)k + 0.5f) * a.dx - zc;
+    return expf(-zeta * zeta * a.inv2sz2);
+}
+
+// Ampere's arithmetic for one E component: e + (dt/dx) (curl_h B) - dt j,
+// the curl given as its two differences.
+__device__ __forceinline__ float ampere_arith(float c, float dt, float e, float d1, float d2, float j) {
+    return e + c * (d1 - d2) - dt * j;
 }
 
 // Bn = Bc - (dt/dx) curl_h E, curl at the face centres.
 template <bool PER>
 __device__ __forceinline__ void faraday_node(const StepArgs& a, int i, int j, int k) {
     const Grid& g = a.g;
-    const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
+    const int64_t o = PWFA_CHECK(a.dbg, ((int64_t)k * g.ny + j) * g.nx + i, 0, g.N, 4u);
     const float *Ex = a.E[0], *Ey = a.E[1], *Ez = a.E[2];
     // +1 neighbours: wrapped (periodic) or clamped into the grid as offsets
     int64_t pi, pj, pk;
@@ -63,6 +96,11 @@ __device__ __forceinline__ void faraday_node(const StepArgs& a, int i, int j, in
         pj = j < g.ny - 1 ? (int64_t)g.nx : 0;
         pk = k < g.nz - 1 ? (int64_t)g.nx * g.ny : 0;
     }
+#ifdef PWFA_DEBUG
+    pi = PWFA_CHECK(a.dbg, o + pi, 0, g.N, 4u) - o;
+    pj = PWFA_CHECK(a.dbg, o + pj, 0, g.N, 4u) - o;
+    pk = PWFA_CHECK(a.dbg, o + pk, 0, g.N, 4u) - o;
+#endif
     const float ex = __ldg(Ex + o), ey = __ldg(Ey + o), ez = __ldg(Ez + o);
     const float ez_j = __ldg(Ez + o + pj), ey_k = __ldg(Ey + o + pk);
     const float ex_k = __ldg(Ex + o + pk), ez_i = __ldg(Ez + o + pi);
@@ -89,7 +127,7 @@ struct AmpereIn {
 template <bool PER>
 __device__ __forceinline__ AmpereIn ampere_loads(const StepArgs& a, int i, int j, int k) {
     const Grid& g = a.g;
-    const int64_t o = ((int64_t)k * g.ny + j) * g.nx + i;
+    const int64_t o = PWFA_CHECK(a.dbg, ((int64_t)k * g.ny + j) * g.nx + i, 0, g.N, 5u);
     const float *Bx = a.Bn[0], *By = a.Bn[1], *Bz = a.Bn[2];
     AmpereIn v;
     if (PER) {
@@ -107,8 +145,13 @@ __device__ __forceinline__ AmpereIn ampere_loads(const StepArgs& a, int i, int j
     } else {
         // neighbours clamped into the grid as index offsets from o
         const int64_t sx = g.nx, sxy = (int64_t)g.nx * g.ny;
-        const int64_t di = i > 0 ? 1 : 0, dj = j > 0 ? sx : 0, dk = k > 0 ? sxy : 0;
-        const int64_t ui = i < g.nx - 1 ? 1 : 0, uj = j < g.ny - 1 ? sx : 0, uk = k < g.nz - 1 ? sxy : 0;
+        int64_t di = i > 0 ? 1 : 0, dj = j > 0 ? sx : 0, dk = k > 0 ? sxy : 0;
+        int64_t ui = i < g.nx - 1 ? 1 : 0, uj = j < g.ny - 1 ? sx : 0, uk = k < g.nz - 1 ? sxy : 0;
+#ifdef PWFA_DEBUG
+        dk = o - PWFA_CHECK(a.dbg, o - dk, 0, g.N, 5u);
+        uk = PWFA_CHECK(a.dbg, o + uk, 0, g.N, 5u) - o;
+        (void)di; (void)dj; (void)ui; (void)uj;
+#endif
         v.bz_j = __ldg(Bz + o - dj);
         v.by_k = __ldg(By + o - dk);
         v.bx_k = __ldg(Bx + o - dk);
@@ -145,25 +188,19 @@ __device__ __forceinline__ void ampere_compute(const StepArgs& a, int i, int j, 
     if (act[0]) {
         float je = 0.5f * (v.j0 + v.j0_i);
         if (a.Jb[0]) je += jbv[0];
-        en[0] = v.e0 + c * ((v.bz - v.bz_j) - (v.by - v.by_k)) - dt * je;
+        en[0] = ampere_arith(c, dt, v.e0, v.bz - v.bz_j, v.by - v.by_k, je);
     }
     if (act[1]) {
         float je = 0.5f * (v.j1 + v.j1_j);
         if (a.Jb[1]) je += jbv[1];
-        en[1] = v.e1 + c * ((v.bx - v.bx_k) - (v.bz - v.bz_i)) - dt * je;
+        en[1] = ampere_arith(c, dt, v.e1, v.bx - v.bx_k, v.bz - v.bz_i, je);
     }
     if (act[2]) {
         const float je = 0.5f * (v.j2 + v.j2_k);
         float jb = 0.0f;
-        if (a.Jb[2]) {
-            jb = jbv[2];
-        } else if (a.alpha != 0.0f) {
-            const float xr = ((float)i - 0.5f * (float)(nx - 1)) * a.dx;
-            const float yr = ((float)j - 0.5f * (float)(ny - 1)) * a.dx;
-            const float zeta = ((float)k + 0.5f) * a.dx - zc;
-            jb = -a.alpha * expf(-(xr * xr + yr * yr) * a.inv2sr2 - zeta * zeta * a.inv2sz2);
-        }
-        en[2] = v.e2 + c * ((v.by - v.by_i) - (v.bx - v.bx_j)) - dt * (je + jb);
+        if (a.Jb[2]) jb = jbv[2];
+        else if (a.alpha != 0.0f) jb = -(driver_transverse(a, i, j) * driver_longitudinal(a, k, zc));
+        en[2] = ampere_arith(c, dt, v.e2, v.by - v.by_i, v.bx - v.bx_j, je + jb);
     }
 }
 

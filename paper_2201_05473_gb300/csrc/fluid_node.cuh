@@ -69,7 +69,8 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
     using T = typename Codec<ST>::T;
     constexpr bool RAWR = RAW && ST != 0 && COLL == 1;
     const Grid& g = a.g;
-    const uint32_t node = ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x;
+    const uint32_t node =
+        PWFA_CHECK(a.dbg, ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x, 0, g.N, 2u);
 
     float A[kL], inn, beta[3];
     // Regularized: the first moments m_l = sum_i xi_i f_l,i, taken here so
@@ -101,9 +102,9 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
     float F[3] = {0.0f, 0.0f, 0.0f};
     if (COLL != 2 && a.couple) {
         float e[3], bc[3], bn[3];
-        node_E<PER>(g, a.E, x, y, z, e);
-        node_B_sum<PER>(g, a.Bc, x, y, z, bc);
-        node_B_sum<PER>(g, a.Bn, x, y, z, bn);
+        node_E<PER>(g, a.E, x, y, z, e, a.dbg);
+        node_B_sum<PER>(g, a.Bc, x, y, z, bc, a.dbg);
+        node_B_sum<PER>(g, a.Bn, x, y, z, bn, a.dbg);
         const float b0 = 0.125f * (bc[0] + bn[0]);
         const float b1 = 0.125f * (bc[1] + bn[1]);
         const float b2 = 0.125f * (bc[2] + bn[2]);
@@ -225,7 +226,7 @@ __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int 
     bool bnd;
     // the 16-bit regularized form works in stored units (see fluid_compute)
     constexpr bool RAW = ST != 0 && COLL == 1;
-    gather<ST, PER, RAW>(a.g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, a.src_shift);
+    gather<ST, PER, RAW>(a.g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, a.src_shift, a.dbg);
     fluid_compute<ST, COLL, PER, DIAG, RAW>(a, x, y, z, f, bnd, nd);
 }
 

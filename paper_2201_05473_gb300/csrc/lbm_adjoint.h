@@ -26,10 +26,15 @@ struct AdjArgs {
     double* grad;         // d/d(alpha, sigma_r, sigma_z), then the profile gradient
     double* gslots;       // [kGradSlots][3] partial sums of d/d(alpha, sigma_r, sigma_z)
     float sr, sz;         // driver sigma_r, sigma_z
-    float csr, csz;       // alpha / sigma_r^3, alpha / sigma_z^3 (set by launch_adjoint_step)
+    float csr, csz;       // alpha / sigma_r^3, alpha / sigma_z^3 (set by the launchers)
 };
 
-// R1..R4 of one reversed step on stream s.
+// R1..R4 of one reversed step on stream s: R1 (launch_adjoint_ampere), R2a
+// and R2 (launch_adjoint_fluid), R3 and R4 (launch_adjoint_fields), in that
+// order.
+cudaError_t launch_adjoint_ampere(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_fluid(const AdjArgs& a, int storage, int collision, cudaStream_t s);
+cudaError_t launch_adjoint_fields(const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint_step(const AdjArgs& a, int storage, int collision, cudaStream_t s);
 
 // grad[0..2] = the sums of the driver-gradient slots.

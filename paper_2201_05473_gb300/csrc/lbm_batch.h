@@ -1,42 +1,50 @@
-// Batched persistent launch of many instances (internal; see batch.cu).
+// Batched launch of many instances (internal; see batch.cu).
 #pragma once
 
 #include "lbm_kernels.h"
 
 namespace pwfa {
 
-constexpr int kBatchTile = 128;  // nodes (threads) per work item
-constexpr int kMaxBatch = 96;    // instances per batched launch (constant-memory table)
-constexpr int kBatchCounters = 3; // work counters of the Faraday, fluid and Ampere phases
+constexpr int kBatchTile = 128;     // nodes (threads) per fluid work tile
+// consecutive fluid tiles of one instance per block of the per-node phases
+// (the block's set-up: its instance, the argument copy, is paid once per
+// group)
+#ifndef PWFA_BATCH_TILES
+#define PWFA_BATCH_TILES 4
+#endif
+constexpr int kBatchGroup = PWFA_BATCH_TILES;
+constexpr int kMaxBatch = 65535;    // instances per batched launch (16-bit block -> instance map)
 
 // One instance of the batch, in device memory.
 struct BatchEntry {
-    StepArgs args[2];    // step arguments for the two ping-pong parities
-    int64_t item_begin;  // index of the instance's first work item
-    int tiles_x, tiles_y;
-    int bx, by;          // tile shape, bx * by = kBatchTile
-    double z0, dt;       // driver centre at t = 0 and time step
-    int64_t* step;       // device step counter (driver time t_{n+1} = (step + 1) dt)
+    StepArgs args[2];     // step arguments for the two ping-pong parities
+    FieldPair out[2];     // the fused field step's outputs for the two parities
+    int64_t tile_begin;   // first block (group of kBatchGroup fluid tiles) of the instance
+    int64_t ntiles;       // fluid tiles of the instance
+    int64_t ftile_begin;  // first fused-field tile
+    int tiles_x, tiles_y; // fluid tiles per plane (bx x by nodes each)
+    int ftiles_x, ftiles_y;  // fused-field tiles per z-slab
+    int bx, by;           // fluid tile shape, bx * by = kBatchTile
+    double z0, dt;        // driver centre at t = 0 and time step
+    int64_t* step;        // two device step counters: the step index n of the
+                          // step that the launches of parity p take is
+                          // step[p]; each Ampere (or fused field) launch of
+                          // parity p writes step[p ^ 1] = step[p] + 1, so the
+                          // replayed graph advances its own driver time
 };
 
 struct BatchLaunch {
-    const BatchEntry* entries;
+    const BatchEntry* entries;         // device copy of the table
+    const uint16_t* tile_inst;         // instance of each block of fluid tiles
+    const uint16_t* ftile_inst;        // instance of each fused-field tile
     int ninst;
-    int64_t nitems;
-    int grid;            // persistent CTAs (SMs x resident blocks)
-    int* counters;       // kBatchCounters work counters, zero before each phase
-                         // (re-armed by the step-counter kernel)
+    int64_t ntiles, nftiles;           // blocks of the per-node phases, fused-field tiles
 };
 
-// One phase of a step of every instance: 0 Faraday, 1 fluid, 2 Ampere,
-// 3 advance the step counters and re-arm the work counters.
+// Phases of one batched step: 0 Faraday, 1 fluid, 2 Ampere (per-node, on
+// the fluid tiles), 3 Ampere fused with the next step's Faraday (on the
+// fused-field tiles), each one launch over every instance.
 cudaError_t launch_batch_phase(const BatchLaunch& b, int phase, int parity, int storage, int collision,
                                bool periodic, cudaStream_t s);
-
-// Copy the instance table into the kernels' constant-memory copy.
-cudaError_t batch_upload_table(const BatchEntry* host, int n, cudaStream_t s);
-
-// Persistent grid size for the given kernel variant.
-cudaError_t batch_grid_size(int storage, int collision, bool periodic, int* grid);
 
 }  // namespace pwfa

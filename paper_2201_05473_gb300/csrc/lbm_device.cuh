@@ -121,6 +121,35 @@ template <> struct Codec<2> {
     }
 };
 
+// ------------------------------------------------------------ debug builds
+// With PWFA_DEBUG defined, the step kernels check each element index they
+// compute against the extent of the array it addresses before the access.
+// An index outside [lo, hi) is recorded in the instance's debug word (dbg[0]:
+// site of the first failure, dbg[1]: its index, dbg[2]: failures counted) and
+// replaced by lo, so nothing outside the allocation is read or written; the
+// host then fails the call with PWFA_ERR_STATE. Release builds compile the
+// checks away. Sites: 1 pulled source node, 2 stored node, 3 node-average
+// field read, 4 Faraday, 5 Ampere, 6 fused field step, 7 adjoint scatter.
+#ifdef PWFA_DEBUG
+static __device__ __noinline__ void debug_record(unsigned* dbg, unsigned site, long long i) {
+    if (!dbg) return;
+    if (atomicCAS(dbg, 0u, site) == 0u) dbg[1] = (unsigned)i;
+    atomicAdd(dbg + 2, 1u);
+}
+template <class I>
+__device__ __forceinline__ I debug_index(unsigned* dbg, I i, long long lo, long long hi, unsigned site) {
+    const long long v = (long long)i;
+    if (v < lo || v >= hi) {
+        debug_record(dbg, site, v);
+        return (I)lo;
+    }
+    return i;
+}
+#define PWFA_CHECK(dbg, i, lo, hi, site) ::pwfa::debug_index((dbg), (i), (long long)(lo), (long long)(hi), (site))
+#else
+#define PWFA_CHECK(dbg, i, lo, hi, site) (i)
+#endif
+
 // ------------------------------------------------------------ kernel args
 struct Grid {
     int nx, ny, nz;
@@ -180,7 +209,14 @@ struct StepArgs {
                           // read one plane up), else 0
     int bx, by;           // fluid kernel block shape (autotuned per instance)
     int staged;           // 1: software-pipelined fluid kernel (FP32 storage), 128-thread tiles
+    unsigned* dbg;        // debug builds: the instance's index-error word (see PWFA_CHECK)
 };
+
+// Elements of the zero guard in front of every Yee/current array (one x-y
+// plane, one row and one element): the lowest index a node average reads.
+__host__ __device__ __forceinline__ int64_t guard_elems(const Grid& g) {
+    return (int64_t)g.nx * g.ny + g.nx + 1;
+}
 
 __device__ __forceinline__ int wrapi(int a, int n) {
     return a < 0 ? a + n : (a >= n ? a - n : a);

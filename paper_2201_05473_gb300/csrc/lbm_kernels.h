@@ -8,6 +8,10 @@
 
 namespace pwfa {
 
+// Device allocation of the library (cudaMalloc with the test hook
+// PWFA_FAIL_ALLOC_AT: the n-th allocation of the process fails).
+cudaError_t dev_alloc(void** p, size_t bytes);
+
 // Launch bounds of the fluid kernels: blocks of at most 128 threads; five
 // per SM (a 96-register budget) for the regularized form, four (128
 // registers) for BGK and stream-only. With its first moments taken right
@@ -74,6 +78,8 @@ struct FieldPair {
     float* B[3];
 };
 cudaError_t launch_ampere_faraday(const StepArgs& a, const FieldPair& out, cudaStream_t s);
+// Tiles of the fused field step over a grid: tx x ty per z-slab, tz slabs.
+void fused_field_tiles(const Grid& g, int* tx, int* ty, int* tz);
 
 // Open grids: zero the Yee components of E and B(t_n) that lie on or outside
 // the conducting walls (tangential E, normal B, components past the grid).
@@ -115,6 +121,12 @@ cudaError_t launch_export_fields(const StepArgs& a, int storage, unsigned mask, 
 // Line cut along z at offset r from the axis: out[0..nz) density,
 // out[nz..2nz) node-averaged E_z (bilinear in x, y).
 cudaError_t launch_linecut(const StepArgs& a, int storage, double r, float* out, cudaStream_t s);
+
+// The built-in gradient objective's slab (plane k, x range [rows[2 j],
+// rows[2 j + 1]) in row j): the FP64 sum of E_z over it into out[0], or
+// Ez_bar := value on it.
+cudaError_t launch_witness_sum(const Grid& g, const float* Ez, int k, const int* rows, double* out, cudaStream_t s);
+cudaError_t launch_witness_seed(const Grid& g, float* Ezbar, int k, const int* rows, float value, cudaStream_t s);
 
 // FP64 diagnostics: partial sums per block into partials (nblocks x 8), then
 // reduced into out[8] (device).

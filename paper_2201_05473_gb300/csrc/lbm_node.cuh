@@ -27,7 +27,7 @@ __device__ __forceinline__ int64_t src_index(const Grid& g, int x, int y, int z,
 template <int ST, bool PER, bool RAW = false>
 __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::T* __restrict__ fin,
                                        float n0, int x, int y, int z, float f[kL][kQ], bool& bnd,
-                                       uint32_t src_shift = 0) {
+                                       uint32_t src_shift = 0, unsigned* dbg = nullptr) {
     using T = typename Codec<ST>::T;
     int xs = x, ys = y, zs = z;
     bnd = false;
@@ -53,6 +53,7 @@ __device__ __forceinline__ void gather(const Grid& g, const typename Codec<ST>::
             const int d = xi_x(q) + xi_y(q) * g.nx;
             src = nodec - (uint32_t)d - (uint32_t)(xi_z(q)) * sxy;
         }
+        src = PWFA_CHECK(dbg, src, 0, g.Np, 1u);
         const uint32_t off = pop_off(q, src);
         if constexpr (ST == 0) {
 #pragma unroll
@@ -119,18 +120,23 @@ __device__ __forceinline__ float yat(const Grid& g, const float* a, int i, int j
     return __ldg(a + ((int64_t)k * g.ny + j) * g.nx + i);
 }
 
-// Open grids keep a zero plane in front of every Yee array and every
-// component outside the conducting box at zero, so the index just below the
-// grid (x-1, y-1 or z-1 wrapping into the previous row/plane) always reads 0.
+// Open grids keep a zero guard in front of every Yee array (one plane, one
+// row and one element) and every component outside the conducting box at
+// zero, so the indices just below the grid (x-1, y-1, z-1 and their
+// combinations, wrapping into the previous row/plane or the guard) read 0.
 template <bool PER>
-__device__ __forceinline__ void node_E(const Grid& g, const float* const E[3], int x, int y, int z, float e[3]) {
+__device__ __forceinline__ void node_E(const Grid& g, const float* const E[3], int x, int y, int z, float e[3],
+                                       unsigned* dbg = nullptr) {
     if (PER) {
         e[0] = 0.5f * (yat<PER>(g, E[0], x - 1, y, z) + yat<PER>(g, E[0], x, y, z));
         e[1] = 0.5f * (yat<PER>(g, E[1], x, y - 1, z) + yat<PER>(g, E[1], x, y, z));
         e[2] = 0.5f * (yat<PER>(g, E[2], x, y, z - 1) + yat<PER>(g, E[2], x, y, z));
     } else {
-        const int64_t o = ((int64_t)z * g.ny + y) * g.nx + x;
+        const int64_t o = PWFA_CHECK(dbg, ((int64_t)z * g.ny + y) * g.nx + x, 0, g.N, 3u);
         const int64_t sxy = (int64_t)g.nx * g.ny;
+#ifdef PWFA_DEBUG
+        PWFA_CHECK(dbg, o - sxy, -guard_elems(g), g.N, 3u);
+#endif
         e[0] = 0.5f * (__ldg(E[0] + o - 1) + __ldg(E[0] + o));
         e[1] = 0.5f * (__ldg(E[1] + o - g.nx) + __ldg(E[1] + o));
         e[2] = 0.5f * (__ldg(E[2] + o - sxy) + __ldg(E[2] + o));
@@ -139,7 +145,8 @@ __device__ __forceinline__ void node_E(const Grid& g, const float* const E[3], i
 
 // Sum over the four faces around the node for one B array.
 template <bool PER>
-__device__ __forceinline__ void node_B_sum(const Grid& g, const float* const B[3], int x, int y, int z, float b[3]) {
+__device__ __forceinline__ void node_B_sum(const Grid& g, const float* const B[3], int x, int y, int z, float b[3],
+                                           unsigned* dbg = nullptr) {
     if (PER) {
         b[0] = yat<PER>(g, B[0], x, y, z) + yat<PER>(g, B[0], x, y - 1, z) + yat<PER>(g, B[0], x, y, z - 1)
              + yat<PER>(g, B[0], x, y - 1, z - 1);
@@ -148,8 +155,12 @@ __device__ __forceinline__ void node_B_sum(const Grid& g, const float* const B[3
         b[2] = yat<PER>(g, B[2], x, y, z) + yat<PER>(g, B[2], x - 1, y, z) + yat<PER>(g, B[2], x, y - 1, z)
              + yat<PER>(g, B[2], x - 1, y - 1, z);
     } else {
-        const int64_t o = ((int64_t)z * g.ny + y) * g.nx + x;
+        const int64_t o = PWFA_CHECK(dbg, ((int64_t)z * g.ny + y) * g.nx + x, 0, g.N, 3u);
         const int64_t sx = g.nx, sxy = (int64_t)g.nx * g.ny;
+#ifdef PWFA_DEBUG
+        // the lowest index read: the -y, -z corner of B_x
+        PWFA_CHECK(dbg, o - sx - sxy, -guard_elems(g), g.N, 3u);
+#endif
         const float* b0 = B[0] + o;
         const float* b1 = B[1] + o;
         const float* b2 = B[2] + o;

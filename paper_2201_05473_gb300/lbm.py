@@ -73,7 +73,7 @@ EXPORTS = ("pwfa_lbm_create", "pwfa_lbm_step", "pwfa_lbm_fields", "pwfa_lbm_get_
            "pwfa_lbm_set_state", "pwfa_lbm_steps_done", "pwfa_lbm_set_stream",
            "pwfa_lbm_destroy", "pwfa_lbm_last_error", "pwfa_lbm_profile", "pwfa_lbm_kernel_times",
            "pwfa_lbm_set_launch", "pwfa_lbm_get_launch", "pwfa_lbm_autotune",
-           "pwfa_lbm_diag_noalloc", "pwfa_lbm_record", "pwfa_lbm_adjoint_step", "pwfa_lbm_set_batching",
+           "pwfa_lbm_diag_noalloc", "pwfa_lbm_record", "pwfa_lbm_adjoint_step", "pwfa_lbm_witness_loss", "pwfa_lbm_set_batching",
            "pwfa_lbm_set_field_fusion",
            "pwfa_lbm_step_diag", "pwfa_lbm_linecut", "pwfa_lbm_set_fluid_variant", "pwfa_lbm_get_fluid_variant",
            "pwfa_lbm_window_planes", "pwfa_axi_create", "pwfa_axi_step", "pwfa_axi_fields",
@@ -137,7 +137,9 @@ def load(build: bool = True):
         lib.pwfa_lbm_diag_noalloc.restype = ctypes.c_int
         lib.pwfa_lbm_record.argtypes = [vp, i32, i32, i32]
         lib.pwfa_lbm_record.restype = ctypes.c_int
-        lib.pwfa_lbm_adjoint_step.argtypes = [vp, i32, vp, dp, i32]
+        lib.pwfa_lbm_adjoint_step.argtypes = [vp, i32, vp, i32, i32, dp, i32]
+        lib.pwfa_lbm_witness_loss.argtypes = [vp, i32, dp]
+        lib.pwfa_lbm_witness_loss.restype = ctypes.c_int
         lib.pwfa_lbm_adjoint_step.restype = ctypes.c_int
         lib.pwfa_lbm_linecut.argtypes = [vp, i32, ctypes.c_double, ctypes.c_double, vp, i64, dp]
         lib.pwfa_lbm_linecut.restype = ctypes.c_int
@@ -348,24 +350,34 @@ class Simulation:
         """Reset to t = 0 and run nsteps keeping checkpoints for the adjoint."""
         _check(self._lib.pwfa_lbm_record(self._h, instance, int(nsteps), int(ckpt_every)))
 
-    def adjoint_step(self, seed_E, instance: int = 0) -> np.ndarray:
-        """Gradient of sum(seed_E * E) after the recorded steps with respect to
-        (alpha, sigma_r, sigma_z, profile...). seed_E: [3][z][y][x] float32."""
+    def adjoint_step(self, seed_E=None, nsteps: int = 0, ckpt_every: int = 0, instance: int = 0) -> np.ndarray:
+        """Gradient with respect to (alpha, sigma_r, sigma_z, profile...) of
+        sum(seed_E * E) (seed_E: [3][z][y][x] float32), or of the built-in
+        witness loss when seed_E is None, after the recorded steps; nsteps >= 1
+        records that many steps first unless they are already recorded."""
         torch = self._torch
-        if isinstance(seed_E, np.ndarray):
-            seed_E = torch.from_numpy(np.ascontiguousarray(seed_E, dtype=np.float32))
-        seed_E = seed_E.contiguous().to(torch.float32)
+        if seed_E is not None:
+            if isinstance(seed_E, np.ndarray):
+                seed_E = torch.from_numpy(np.ascontiguousarray(seed_E, dtype=np.float32))
+            seed_E = seed_E.contiguous().to(torch.float32)
         w = self.works[instance]
         ng = 3 + (0 if w.profile is None else len(w.profile))
         g = np.zeros(ng, dtype=np.float64)
-        _check(self._lib.pwfa_lbm_adjoint_step(self._h, instance, _ptr(seed_E),
+        _check(self._lib.pwfa_lbm_adjoint_step(self._h, instance, _ptr(seed_E), int(nsteps), int(ckpt_every),
                                                g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ng))
         return g
+
+    def witness_loss(self, instance: int = 0) -> float:
+        """The built-in gradient objective -mean(E_z over the witness slab)
+        at the current step, reduced in FP64 by the library."""
+        v = ctypes.c_double()
+        _check(self._lib.pwfa_lbm_witness_loss(self._h, instance, ctypes.byref(v)))
+        return v.value
 
     def profile(self, enable: bool = True):
         _check(self._lib.pwfa_lbm_profile(self._h, 1 if enable else 0))
 
-    KERNELS = ("faraday", "fluid", "ampere", "aux")
+    KERNELS = ("faraday", "fluid", "ampere", "aux", "adj_fluid", "adj_field")
 
     def set_batching(self, enable: bool = True):
         _check(self._lib.pwfa_lbm_set_batching(self._h, 1 if enable else 0))
@@ -379,8 +391,8 @@ class Simulation:
 
     def kernel_times(self):
         """(ms, launches) per kernel kind since the previous call."""
-        ms = np.zeros(4, dtype=np.float64)
-        n = np.zeros(4, dtype=np.int64)
+        ms = np.zeros(len(self.KERNELS), dtype=np.float64)
+        n = np.zeros(len(self.KERNELS), dtype=np.int64)
         _check(self._lib.pwfa_lbm_kernel_times(
             self._h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
             n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))

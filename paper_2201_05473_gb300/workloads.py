@@ -82,6 +82,14 @@ def production() -> Workload:
                     name="lbm-pwfa 512x256x256 dx0.05 regularized")
 
 
+def production_timing() -> Workload:
+    """The production workload as timed: the driver starts inside the box at
+    z0 = 4 sigma_z (a timing run may start there; the parity runs let it
+    enter through the z = 0 wall)."""
+    w = production()
+    return w.replace(z0=4.0 * w.sigma_z, name=w.name + " driver-in-box")
+
+
 def precision_form(storage: int = BF16) -> Workload:
     """Config-1 physics on 256x128x128 with reduced-precision storage, 1000 steps."""
     w = parity_small().replace(nx=128, ny=128, nz=256, steps=1000, storage=storage)
@@ -111,6 +119,14 @@ def batched_scan(n_instances: int = 64, seed: int = 0, steps: int = 500):
                             sigma_r=sr, sigma_z=sz, z0=-4.0 * sz, steps=steps,
                             name=f"scan{m}"))
     return out
+
+
+def small_scan(n_instances: int = 256, seed: int = 0, steps: int = 500):
+    """A scan of many small instances: the parameter draws of batched_scan
+    on 32x16x16 (z, y, x) grids each, too small for one instance to fill the
+    GPU."""
+    return [w.replace(nx=16, ny=16, nz=32, name=f"small{m}")
+            for m, w in enumerate(batched_scan(n_instances, seed=seed, steps=steps))]
 
 
 def random_populations(shape_zyx, seed: int = 1, base: float = 1.0, spread: float = 0.05):

@@ -115,3 +115,23 @@ def test_null_arguments(lib):
     assert lib.pwfa_lbm_set_field_fusion(None, 1) == -1
     assert lib.pwfa_lbm_set_batching(None, 1) == -1
     assert lib.pwfa_lbm_step_diag(None, 1, None) == -1
+    g = (ctypes.c_double * 3)()
+    assert lib.pwfa_lbm_adjoint_step(None, 0, None, 10, 0, g, 3) == -1
+    assert lib.pwfa_lbm_witness_loss(None, 0, g) == -1
+
+
+def test_noalloc_argument_checks(lib):
+    """pwfa_lbm_diag_noalloc rejects bad arguments with PWFA_ERR_PARAM before
+    any CUDA call (the pointers below are never dereferenced)."""
+    fake = ctypes.c_void_p(0x1000)
+
+    def call(nx=8, ny=8, nz=8, dx=0.2, n_floor=0.0, f=fake, E=fake, B=fake, out=fake):
+        return lib.pwfa_lbm_diag_noalloc(nx, ny, nz, dx, n_floor, f, E, B, out, None)
+
+    assert call(nx=1024, ny=1024, nz=128) == -1  # 134 M nodes, above the fixed scratch
+    assert "exceeds" in lib.pwfa_lbm_last_error().decode()
+    assert call(nx=0) == -1
+    assert call(f=None) == -1
+    assert call(dx=0.0) == -1
+    assert call(n_floor=-1.0) == -1 and "n_floor" in lib.pwfa_lbm_last_error().decode()
+    assert call(n_floor=float("nan")) == -1

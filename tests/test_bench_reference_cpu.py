@@ -25,7 +25,8 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["unit"] == "GLUPS" and line["higher_is_better"] is True and line["value"] > 0
     assert line["steps"] == 1 and line["warmup"] == 3 and line["n_gpus"] == 1
-    assert line["config"]["workload"] == "lbm-pwfa 512x256x256 dx0.05 regularized"
+    assert line["config"]["workload"] == "lbm-pwfa 512x256x256 dx0.05 regularized driver-in-box"
+    assert line["config"]["driver"]["z0"] == 2.0
     assert line["config"]["grid_zyx"] == [512, 256, 256]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]

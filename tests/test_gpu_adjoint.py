@@ -148,3 +148,31 @@ def test_adjoint_requires_recording():
     with lbm.Simulation(w) as sim:
         with pytest.raises(lbm.LBMError):
             sim.adjoint_step(np.zeros((3, w.nz, w.ny, w.nx), dtype=np.float32))
+
+
+def test_builtin_witness_loss_and_null_seed():
+    """The library's built-in objective: pwfa_lbm_witness_loss equals
+    -mean(E_z) over the witness slab of the exported fields, and the adjoint
+    with a NULL seed (the built-in loss) recording its own forward run
+    (nsteps given) equals record + adjoint with the explicit slab seed."""
+    w = W.parity_small().replace(nx=16, ny=16, nz=40, alpha=0.5, z0=-1.0, profile=np.ones(8),
+                                 profile_rmax=1.5)
+    steps = 120
+    k, mask = W.witness_slab(w, steps)
+    seed = np.zeros((3, w.nz, w.ny, w.nx), dtype=np.float32)
+    seed[2, k][mask] = -1.0 / mask.sum()
+    with lbm.Simulation(w) as sim:
+        sim.record(steps, 11)
+        ez = sim.fields(lbm.FIELD_EZ | lbm.RAW_YEE)[0, k].cpu().numpy().astype(np.float64)
+        L = sim.witness_loss()
+        assert abs(L - (-ez[mask].mean())) <= 1e-12 * max(abs(L), 1e-30) + 1e-15, (L, -ez[mask].mean())
+        g_seed = sim.adjoint_step(seed)
+    with lbm.Simulation(w) as sim:
+        g_null = sim.adjoint_step(None, nsteps=steps, ckpt_every=11)
+        assert sim.steps_done() == steps
+        # the recording is kept: a second call with nsteps = 0 reuses it
+        g_again = sim.adjoint_step(None)
+    # the same sweep; the FP64 atomic sums of the driver terms may add in
+    # another order
+    assert np.allclose(g_null, g_seed, rtol=1e-12, atol=1e-15), (g_null, g_seed)
+    assert np.allclose(g_again, g_seed, rtol=1e-12, atol=1e-15)

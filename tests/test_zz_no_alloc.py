@@ -61,12 +61,20 @@ def test_noalloc_diagnostics_match_handle_diagnostics():
             _check(out.cpu().numpy(), ref)
 
 
-def test_noalloc_rejects_oversized_grid():
+def test_noalloc_diagnostics_many_blocks():
+    """A grid of 1.57 M nodes: 384 first-pass blocks of 4096 nodes, so the
+    finishing kernel loops over more than its 256 threads' worth of block
+    records and the scratch records past the first 256 are used."""
     lib = lbm.load()
-    w = W.parity_small().replace(nx=1024, ny=1024, nz=128)  # 134 M nodes > limit
-    dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
-    rc = lib.pwfa_lbm_diag_noalloc(w.nx, w.ny, w.nz, w.dx, w.n_floor, ctypes.c_void_p(dummy.data_ptr()),
-                                   ctypes.c_void_p(dummy.data_ptr()), ctypes.c_void_p(dummy.data_ptr()),
-                                   ctypes.c_void_p(dummy.data_ptr()), None)
-    assert rc == -1
-    assert "exceeds" in lib.pwfa_lbm_last_error().decode()
+    w = W.parity_small().replace(nx=128, ny=128, nz=96, alpha=0.5, z0=-1.0)
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with lbm.Simulation(w, stream=stream) as sim:
+        for steps in (30, 10):
+            sim.step(steps)
+            ref = sim.diag()
+            f, E, B = sim.get_state()
+            rc = _noalloc(lib, w, f, E, B, out, stream)
+            assert rc == 0, lib.pwfa_lbm_last_error().decode()
+            torch.cuda.synchronize()
+            _check(out.cpu().numpy(), ref)
