@@ -143,8 +143,11 @@ int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps);
  * advances it nsteps, keeping a checkpoint of the full state every
  * ckpt_every steps (0 selects ceil(sqrt(nsteps))) plus the final state. The
  * instance is left at step nsteps. Device memory: (nsteps/ckpt_every + 1)
- * states of 76 N populations + 6 N field values, ckpt_every segment states
- * and ~174 N floats of adjoint scratch; PWFA_ERR_ALLOC if it does not fit. */
+ * states of 76 N populations + 6 N field values; one segment of K =
+ * ckpt_every recomputed steps (two population buffers, the E and B of its
+ * states, 6 (K + 1) N values, and the four lattice sums of each step, 4 K N:
+ * the reverse step needs nothing else of the populations); ~174 N floats of
+ * adjoint scratch; PWFA_ERR_ALLOC if it does not fit. */
 int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckpt_every);
 
 /* Gradient of an objective L of the raw Yee E after T recorded steps with

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_ke
     const bool row_in = y >= 1 && y <= g.ny - 2 && z >= 1 && z <= g.nz - 2;
     const bool xwall = !PER && !SHELL && live && row_in && (x == 0 || (x == g.nx - 1 && lane != 0));
     const int64_t LS = lattice_stride(g);
-    const T* __restrict__ fin = static_cast<const T*>(s.fin);
+    const float* __restrict__ mom = s.mom;
     const float* __restrict__ Sin = a.Sbar_in + l * LS;
     float* __restrict__ Sout = a.Sbar_out + l * LS;
     if (!SHELL && live && bnd) {
@@ -299,14 +299,10 @@ __global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_ke
     const bool forced = (COLL != 2) && s.couple;
     if (act) {
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            uint32_t src;
-            if (PER) src = (uint32_t)src_index<true>(g, xs, ys, zs, q);
-            else src = nodec - (uint32_t)(xi_x(q) + xi_y(q) * g.nx) - (uint32_t)xi_z(q) * sxy;
-            src = PWFA_CHECK(s.dbg, src, 0, g.Np, 7u);
-            Al += Codec<ST>::load(fin + pop_elem<ST>(l, pop_off(q, src), LS), l, q, s.n0);
-            S[q] = __ldg(Sin + pop_off(q, node));
-        }
+        for (int q = 0; q < kQ; ++q) S[q] = __ldg(Sin + pop_off(q, node));
+        // the lattice sum of the node's pulled populations, as the forward
+        // step formed it (for a boundary node: of its clamped node's)
+        Al = __ldg(mom + (int64_t)l * g.N + node);
         float v[3] = {0.0f, 0.0f, 0.0f};
         if (l == 0) { if (forced) node_E<PER>(g, s.E, x, y, z, v, s.dbg); }
         else if (l == 1) { if (forced) node_B_sum<PER>(g, s.Bc, x, y, z, v, s.dbg); }

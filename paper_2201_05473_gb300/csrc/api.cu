@@ -473,7 +473,6 @@ int batch_build(pwfa_lbm* h) {
     int64_t ntiles = 0, nftiles = 0;
     for (int i = 0; i < n; ++i) {
         Instance& in = h->inst[i];
-        if (in.bx * in.by != kBatchTile) { in.bx = 64; in.by = 2; }
         BatchEntry& e = ent[i];
         for (int par = 0; par < 2; ++par) {
             e.args[par] = make_args(in);
@@ -486,11 +485,7 @@ int batch_build(pwfa_lbm* h) {
             if (in.p.couple) in.bcur = 1 - in.bcur;
             if (fused) for (int c = 0; c < 3; ++c) std::swap(in.E[c], in.Ealt[c]);
         }
-        e.bx = in.bx;
-        e.by = in.by;
-        e.tiles_x = (in.g.nx + in.bx - 1) / in.bx;
-        e.tiles_y = (in.g.ny + in.by - 1) / in.by;
-        e.ntiles = (int64_t)e.tiles_x * e.tiles_y * in.g.nz;
+        e.ntiles = (in.g.N + kBatchTile - 1) / kBatchTile;
         e.tile_begin = ntiles;
         ntiles += (e.ntiles + kBatchGroup - 1) / kBatchGroup;
         int fz = 0;
@@ -704,11 +699,36 @@ int step_instance(pwfa_lbm* h, Instance& in, const DiagOut* diag) {
 }
 
 // ---------------------------------------------------------------- adjoint
+// One segment of a recording: the two population buffers the recomputed
+// forward steps ping-pong between, then E of each of its K states and B of
+// its K + 1 states (each field array behind a zero guard), and the lattice
+// sums A_l ([4][N]) that each recomputed step stores for the reverse step.
+struct SegLayout {
+    size_t fb, vb, gvb, gb;
+    int64_t K;
+    size_t pop(int b) const { return fb * (size_t)b; }
+    size_t E(int64_t j, int c) const { return 2 * fb + gvb * (size_t)(3 * j + c) + gb; }
+    size_t B(int64_t j, int c) const { return 2 * fb + gvb * (size_t)(3 * K + 3 * j + c) + gb; }
+    size_t mom(int64_t j) const { return 2 * fb + gvb * (size_t)(6 * K + 3) + 4 * vb * (size_t)j; }
+    size_t bytes() const { return mom(K); }
+};
+
 size_t fbytes_of(const Instance& in) { return align_up((size_t)in.g.Np * kPop * storage_bytes(in.p.storage)); }
 size_t vbytes_of(const Instance& in) { return align_up((size_t)in.g.N * sizeof(float)); }
 // one field array with its zero guard in front (the recorded segment states
 // that the recomputed forward steps read)
 size_t gvbytes_of(const Instance& in) { return guard_bytes(in.g) + vbytes_of(in); }
+
+SegLayout seg_layout(const Instance& in, int K) {
+    SegLayout L;
+    L.fb = fbytes_of(in);
+    L.vb = vbytes_of(in);
+    L.gvb = gvbytes_of(in);
+    L.gb = guard_bytes(in.g);
+    L.K = K;
+    return L;
+}
+
 
 struct StateRef {  // one stored state inside a recording buffer
     void* f;
@@ -797,24 +817,23 @@ int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_ever
     r.K = ckpt_every > 0 ? ckpt_every : (int)std::ceil(std::sqrt((double)nsteps));
     if (r.K > nsteps) r.K = nsteps;
     r.ncp = (int)((nsteps + r.K - 1) / r.K);
-    const size_t fb = fbytes_of(in), vb = vbytes_of(in), gvb = gvbytes_of(in);
+    const size_t fb = fbytes_of(in), vb = vbytes_of(in);
     r.cp_stride = fb + 6 * vb;
-    r.seg_stride = fb + 6 * gvb;  // per step: populations, E, B (plus one trailing B)
+    const size_t seg_bytes = seg_layout(in, r.K).bytes();
     const size_t adj_bytes = 2 * align_up((size_t)in.g.Np * kPop * sizeof(float)) + 22 * vb +
                              align_up(sizeof(double) * (260 + 3 * kGradSlots));
     if (dev_alloc((void**)&r.cp, r.cp_stride * (r.ncp + 1)) != cudaSuccess ||
-        dev_alloc((void**)&r.seg, r.seg_stride * r.K + 3 * gvb) != cudaSuccess ||
+        dev_alloc((void**)&r.seg, seg_bytes) != cudaSuccess ||
         dev_alloc((void**)&r.adj, adj_bytes) != cudaSuccess) {
         cudaGetLastError();
         char buf[200];
-        std::snprintf(buf, sizeof buf, "recording needs %.2f GB (%d checkpoints + %d segment states)",
-                      (r.cp_stride * (r.ncp + 1) + r.seg_stride * r.K + 3 * gvb + adj_bytes) / 1e9, r.ncp + 1,
-                      r.K);
+        std::snprintf(buf, sizeof buf, "recording needs %.2f GB (%d checkpoints + a segment of %d steps)",
+                      (r.cp_stride * (r.ncp + 1) + seg_bytes + adj_bytes) / 1e9, r.ncp + 1, r.K);
         free_recording(in);
         return fail(PWFA_ERR_ALLOC, buf);
     }
     // the guards in front of the segment's field slots stay zero
-    PWFA_CUDA(cudaMemsetAsync(r.seg, 0, r.seg_stride * r.K + 3 * gvb, s), "cudaMemsetAsync");
+    PWFA_CUDA(cudaMemsetAsync(r.seg, 0, seg_bytes, s), "cudaMemsetAsync");
     int rc = reset_instance(in, s);
     if (rc) return rc;
     for (int32_t n = 0; n < nsteps; ++n) {
@@ -897,21 +916,18 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, int32_t nst
     int cur = 0;
     for (int seg = r.ncp - 1; seg >= 0; --seg) {
         const int64_t s0 = (int64_t)seg * r.K, s1 = std::min<int64_t>(r.T, s0 + r.K);
-        // Segment storage: populations and E of each state j (K slots) and B
-        // of states 0..K (state j's B(t_{n+1}) is state j+1's B).
-        const size_t fbs = fbytes_of(in);
+        // segment storage (SegLayout)
+        const SegLayout L = seg_layout(in, r.K);
         char* segp = static_cast<char*>(r.seg);
-        auto f_slot = [&](int64_t j) -> void* { return segp + fbs * j; };
-        const size_t gvb = gvbytes_of(in), gb = guard_bytes(in.g);
-        auto E_slot = [&](int64_t j, int c) -> float* { return (float*)(segp + fbs * r.K + gvb * (3 * j + c) + gb); };
-        auto B_slot = [&](int64_t j, int c) -> float* {
-            return (float*)(segp + fbs * r.K + gvb * 3 * r.K + gvb * (3 * j + c) + gb);
-        };
+        auto pop_buf = [&](int64_t j) -> void* { return segp + L.pop((int)(j & 1)); };
+        auto E_slot = [&](int64_t j, int c) -> float* { return (float*)(segp + L.E(j, c)); };
+        auto B_slot = [&](int64_t j, int c) -> float* { return (float*)(segp + L.B(j, c)); };
+        auto mom_slot = [&](int64_t j) -> float* { return (float*)(segp + L.mom(j)); };
         // restore the checkpoint into state 0 of the segment
         {
             StateRef cp = state_at(in, (char*)r.cp + r.cp_stride * seg, false);
             const size_t fb = (size_t)in.g.Np * kPop * storage_bytes(in.p.storage);
-            PWFA_CUDA(cudaMemcpyAsync(f_slot(0), cp.f, fb, cudaMemcpyDeviceToDevice, s), "restore copy");
+            PWFA_CUDA(cudaMemcpyAsync(pop_buf(0), cp.f, fb, cudaMemcpyDeviceToDevice, s), "restore copy");
             for (int c = 0; c < 3; ++c) {
                 PWFA_CUDA(cudaMemcpyAsync(E_slot(0, c), cp.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
                           "restore copy");
@@ -919,16 +935,21 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, int32_t nst
                           "restore copy");
             }
         }
-        // recompute the segment's steps straight into the slots
+        // recompute the segment's steps: populations ping-pong, E and B of
+        // each state and the lattice sums of each step into their slots; Ampere
+        // of step j runs fused with Faraday of step j + 1 where that B slot
+        // exists
         const int64_t len = s1 - s0;
+        bool b_ahead = false;
         for (int64_t j = 0; j < len; ++j) {
             const int64_t keep_steps = in.steps;
             in.steps = s0 + j;
             StepArgs f = make_args(in);
             in.steps = keep_steps;
             const bool last = j + 1 == len;
-            f.fin = f_slot(j);
-            f.fout = last ? in.f[1 - in.fcur] : f_slot(j + 1);
+            f.fin = pop_buf(j);
+            f.fout = last ? in.f[1 - in.fcur] : pop_buf(j + 1);
+            f.mom = mom_slot(j);
             for (int c = 0; c < 3; ++c) {
                 f.E[c] = E_slot(j, c);
                 f.Bc[c] = B_slot(j, c);
@@ -936,8 +957,10 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, int32_t nst
                 f.Eout[c] = last ? in.E[c] : E_slot(j + 1, c);  // Ampere out of place writes every component
             }
             if (in.p.couple) {
-                int rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(f, s); });
-                if (rc) return rc;
+                if (!b_ahead) {
+                    int rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(f, s); });
+                    if (rc) return rc;
+                }
             } else {
                 // no Maxwell update: E and B pass through
                 for (int c = 0; c < 3; ++c) {
@@ -948,9 +971,21 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, int32_t nst
                 }
             }
             int rc = timed_launch(h, PWFA_KERNEL_FLUID, "fluid kernel",
-                                  [&] { return launch_fluid(f, in.p.storage, in.p.collision, s); });
+                                  [&] { return launch_fluid_mom(f, in.p.storage, in.p.collision, s); });
             if (rc) return rc;
-            if (in.p.couple) {
+            b_ahead = false;
+            if (in.p.couple && !last && fusable(in.p)) {
+                // B(t_{n+2}) of the next recomputed step into its slot
+                FieldPair out{};
+                for (int c = 0; c < 3; ++c) {
+                    out.E[c] = f.Eout[c];
+                    out.B[c] = B_slot(j + 2, c);
+                }
+                rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere-faraday kernel",
+                                  [&] { return launch_ampere_faraday(f, out, s); });
+                if (rc) return rc;
+                b_ahead = true;
+            } else if (in.p.couple) {
                 rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere kernel", [&] { return launch_ampere(f, s); });
                 if (rc) return rc;
             }
@@ -961,8 +996,9 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, int32_t nst
             in.steps = n;
             StepArgs f = make_args(in);
             in.steps = keep_steps;
-            f.fin = f_slot(j);
+            f.fin = nullptr;  // the reverse step reads the lattice sums instead
             f.fout = nullptr;
+            f.mom = mom_slot(j);
             for (int c = 0; c < 3; ++c) {
                 f.E[c] = E_slot(j, c);
                 f.Bc[c] = B_slot(j, c);
@@ -1465,13 +1501,11 @@ int pwfa_lbm_get_launch(pwfa_lbm_t* h, int32_t instance, int32_t* bx, int32_t* b
 int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
     if (reps < 1) return fail(PWFA_ERR_PARAM, "reps must be >= 1");
-    // {bx, by, variant}: direct shapes, then the staged kernel's 128-thread tiles
+    // {bx, by, variant}: direct shapes, then the staged kernel's 128-thread
+    // tiles (the batched path's per-node phases take tiles of consecutive
+    // nodes instead; the shapes serve the per-instance steps)
     static const int cand_all[][3] = {{32, 4, 0}, {64, 2, 0}, {128, 1, 0}, {32, 4, 1}, {64, 2, 1}, {128, 1, 1}};
-    // the batched kernels take tiles of kBatchTile nodes
-    static const int cand_batch[][3] = {{32, 4, 0}, {64, 2, 0}, {128, 1, 0}};
-    const bool batched = batch_eligible(h);
-    const int ncand = batched ? (int)(sizeof cand_batch / sizeof cand_batch[0])
-                              : (int)(sizeof cand_all / sizeof cand_all[0]);
+    const int ncand = (int)(sizeof cand_all / sizeof cand_all[0]);
     h->batch_valid = false;
     cudaEvent_t e0, e1;
     PWFA_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
@@ -1481,7 +1515,7 @@ int pwfa_lbm_autotune(pwfa_lbm_t* h, int32_t reps) {
         float best = 1e30f;
         int bb[3] = {in.bx, in.by, in.variant};
         for (int ci = 0; ci < ncand; ++ci) {
-            const int* c = batched ? cand_batch[ci] : cand_all[ci];
+            const int* c = cand_all[ci];
             if (c[0] > 2 * in.g.nx && c[0] > 32) continue;  // mostly idle lanes
             if (c[0] * c[1] > PWFA_FLUID_MAX_THREADS) continue;
             in.bx = c[0];

@@ -1,9 +1,9 @@
 // Batched form: many independent instances of uneven grid sizes advanced
 // together, one launch per phase for all of them, two steps replayed from a
 // captured CUDA graph. Each phase is one grid over the concatenated tiles of
-// every instance (per-node phases: groups of 128-node tiles of one z-plane
-// in the instance's autotuned shape; fused field step: the z-marching tiles
-// of fields_fused.cuh); a 16-bit table maps each block to its instance. The hardware block
+// every instance (per-node phases: groups of tiles of 128 consecutive nodes;
+// fused field step: the z-marching tiles of fields_fused.cuh); a 16-bit
+// table maps each block to its instance. The hardware block
 // scheduler hands the tiles out in order, so the tiles in flight form one
 // short window of the list and the z +- 1 planes a pull reads are still in
 // L2. No block waits on another.
@@ -25,14 +25,19 @@ __device__ __forceinline__ void copy_words(void* dst, const void* src, int bytes
     for (int w = tid; w < bytes / 4; w += NT) static_cast<int*>(dst)[w] = __ldg(static_cast<const int*>(src) + w);
 }
 
-// Node (x, y, z) of thread tid in fluid tile `local` of an instance.
-__device__ __forceinline__ void tile_node(const BatchEntry& e, int64_t local, int tid, int& x, int& y, int& z) {
-    const int per_plane = e.tiles_x * e.tiles_y;
-    z = (int)(local / per_plane);
-    const int r = (int)(local - (int64_t)z * per_plane);
-    const int ty = r / e.tiles_x;
-    x = (r - ty * e.tiles_x) * e.bx + tid % e.bx;
-    y = ty * e.by + tid / e.bx;
+// Node (x, y, z) of thread tid in fluid tile t of an instance: tiles are
+// 128 consecutive nodes of the instance's [z][y][x] order (four 32-node
+// chunks of the population layout), so no lane idles on a narrow grid; false
+// past the instance's last node.
+__device__ __forceinline__ bool tile_node(const Grid& g, int64_t t, int tid, int& x, int& y, int& z) {
+    const uint32_t node = (uint32_t)t * (uint32_t)kBatchTile + (uint32_t)tid;
+    if (node >= (uint32_t)g.N) return false;
+    const uint32_t nx = (uint32_t)g.nx, nxy = nx * (uint32_t)g.ny;
+    const uint32_t zz = node / nxy, r = node - zz * nxy, yy = r / nx;
+    z = (int)zz;
+    y = (int)yy;
+    x = (int)(r - yy * nx);
+    return true;
 }
 
 // Driver time of the instance's Ampere launch of this parity, and the
@@ -60,8 +65,7 @@ __global__ void __launch_bounds__(kBatchTile, PHASE == 1 ? FluidOcc<COLL>::block
     const int64_t t1 = t0 + kBatchGroup < e.ntiles ? t0 + kBatchGroup : e.ntiles;
     for (int64_t t = t0; t < t1; ++t) {
         int x, y, z;
-        tile_node(e, t, tid, x, y, z);
-        if (x >= sa.g.nx || y >= sa.g.ny) continue;
+        if (!tile_node(sa.g, t, tid, x, y, z)) continue;
         if (PHASE == 0) faraday_node<PER>(sa, x, y, z);
         else if (PHASE == 1) fluid_node<ST, COLL, PER>(sa, x, y, z);
         else ampere_node<PER>(sa, x, y, z, s_zc);

@@ -63,7 +63,7 @@ __device__ __forceinline__ void raw_moments(const float (&s)[kQ], float base, fl
 // RAW (16-bit storage, regularized collision) in stored units, and the
 // post-collision values are formed in stored units too, so that neither the
 // decode nor the encode of the deviations costs a per-value operation.
-template <int ST, int COLL, bool PER, bool DIAG = false, bool RAW = false>
+template <int ST, int COLL, bool PER, bool DIAG = false, bool RAW = false, bool MOM = false>
 __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, int z, float (&f)[kL][kQ], bool bnd,
                                               NodeDiag* nd = nullptr) {
     using T = typename Codec<ST>::T;
@@ -89,6 +89,12 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
         }
     }
     const float n = A[0];
+    if (MOM) {
+        // the adjoint's recompute keeps the lattice sums (the reverse step
+        // needs nothing else of the populations)
+#pragma unroll
+        for (int l = 0; l < kL; ++l) __stcs(a.mom + (int64_t)l * g.N + node, A[l]);
+    }
     if (DIAG) {
         nd->n = A[0];
         nd->a1 = A[1];
@@ -219,7 +225,7 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
     __stcs(a.J[2] + node, ngs * ps2);
 }
 
-template <int ST, int COLL, bool PER, bool DIAG = false>
+template <int ST, int COLL, bool PER, bool DIAG = false, bool MOM = false>
 __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int z, NodeDiag* nd = nullptr) {
     using T = typename Codec<ST>::T;
     float f[kL][kQ];
@@ -227,7 +233,7 @@ __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int 
     // the 16-bit regularized form works in stored units (see fluid_compute)
     constexpr bool RAW = ST != 0 && COLL == 1;
     gather<ST, PER, RAW>(a.g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, a.src_shift, a.dbg);
-    fluid_compute<ST, COLL, PER, DIAG, RAW>(a, x, y, z, f, bnd, nd);
+    fluid_compute<ST, COLL, PER, DIAG, RAW, MOM>(a, x, y, z, f, bnd, nd);
 }
 
 }  // namespace pwfa

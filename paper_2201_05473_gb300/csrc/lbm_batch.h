@@ -5,12 +5,12 @@
 
 namespace pwfa {
 
-constexpr int kBatchTile = 128;     // nodes (threads) per fluid work tile
+constexpr int kBatchTile = 128;     // consecutive nodes (threads) per fluid work tile
 // consecutive fluid tiles of one instance per block of the per-node phases
 // (the block's set-up: its instance, the argument copy, is paid once per
 // group)
 #ifndef PWFA_BATCH_TILES
-#define PWFA_BATCH_TILES 4
+#define PWFA_BATCH_TILES 2
 #endif
 constexpr int kBatchGroup = PWFA_BATCH_TILES;
 constexpr int kMaxBatch = 65535;    // instances per batched launch (16-bit block -> instance map)
@@ -22,9 +22,7 @@ struct BatchEntry {
     int64_t tile_begin;   // first block (group of kBatchGroup fluid tiles) of the instance
     int64_t ntiles;       // fluid tiles of the instance
     int64_t ftile_begin;  // first fused-field tile
-    int tiles_x, tiles_y; // fluid tiles per plane (bx x by nodes each)
     int ftiles_x, ftiles_y;  // fused-field tiles per z-slab
-    int bx, by;           // fluid tile shape, bx * by = kBatchTile
     double z0, dt;        // driver centre at t = 0 and time step
     int64_t* step;        // two device step counters: the step index n of the
                           // step that the launches of parity p take is

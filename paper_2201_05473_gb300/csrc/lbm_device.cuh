@@ -210,6 +210,8 @@ struct StepArgs {
     int bx, by;           // fluid kernel block shape (autotuned per instance)
     int staged;           // 1: software-pipelined fluid kernel (FP32 storage), 128-thread tiles
     unsigned* dbg;        // debug builds: the instance's index-error word (see PWFA_CHECK)
+    float* mom;           // adjoint recompute (launch_fluid_mom): each node's lattice
+                          // sums A_l are stored here too ([4][N]); unused otherwise
 };
 
 // Elements of the zero guard in front of every Yee/current array (one x-y

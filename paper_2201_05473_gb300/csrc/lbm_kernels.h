@@ -54,6 +54,11 @@ struct DiagOut {
 cudaError_t launch_fluid(const StepArgs& a, int storage, int collision, cudaStream_t s,
                          const DiagOut* d = nullptr);
 
+// The same fluid step that also stores each node's lattice sums A_l into
+// a.mom ([4][N] FP32): the adjoint's recomputed forward steps keep them for
+// the reverse step, which needs nothing else of the populations.
+cudaError_t launch_fluid_mom(const StepArgs& a, int storage, int collision, cudaStream_t s);
+
 // Reduce the nrec fluid records and d.nenergy energy records of a fused step
 // into d.out: up to kDiagBlocks blocks combine contiguous chunks into
 // d.scratch, one block combines those (a single block over the ~2.6e5
