@@ -10,7 +10,7 @@ namespace pwfa {
 namespace {
 
 template <int ST, int COLL, bool PER>
-__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, FluidOcc<COLL>::blocks) fluid_mom_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(PWFA_FLUID_MAX_THREADS, FluidOcc<ST, COLL>::blocks) fluid_mom_kernel(const StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.g.nx || y >= a.g.ny) return;

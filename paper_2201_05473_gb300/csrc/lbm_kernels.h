@@ -12,12 +12,13 @@ namespace pwfa {
 // PWFA_FAIL_ALLOC_AT: the n-th allocation of the process fails).
 cudaError_t dev_alloc(void** p, size_t bytes);
 
-// Launch bounds of the fluid kernels: blocks of at most 128 threads; five
-// per SM (a 96-register budget) for the regularized form, four (128
-// registers) for BGK and stream-only. With its first moments taken right
-// after the gather the regularized kernel fits 96 registers without spilling
-// and the extra warps hide the pull's latency (production grid: FP32 3.24 ->
-// 3.17 ms, BF16 2.05 -> 1.86 ms against 128 registers and four blocks). BGK
+// Launch bounds of the fluid kernels: blocks of at most 128 threads; for the
+// regularized form five per SM with FP32 storage (a 96-register budget) and
+// six with the 16-bit forms (80 registers; a few values spill to L1), four
+// (128 registers) for BGK and stream-only. With its first moments taken right after the gather the
+// regularized kernel fits those budgets and the extra warps hide the pull's
+// latency (production grid: FP32 3.24 -> 3.17 ms at five blocks against four;
+// BF16 2.05 -> 1.86 ms at five, 1.83 ms at six; FP32 at six: 3.46 ms). BGK
 // and stream-only carry every pulled value itself through the source
 // computation and would spill at 96.
 #ifndef PWFA_FLUID_MAX_THREADS
@@ -26,9 +27,12 @@ cudaError_t dev_alloc(void** p, size_t bytes);
 #ifndef PWFA_FLUID_MIN_BLOCKS
 #define PWFA_FLUID_MIN_BLOCKS 5
 #endif
-template <int COLL>
+#ifndef PWFA_FLUID_MIN_BLOCKS_16
+#define PWFA_FLUID_MIN_BLOCKS_16 6
+#endif
+template <int ST, int COLL>
 struct FluidOcc {
-    static constexpr int blocks = COLL == 1 ? PWFA_FLUID_MIN_BLOCKS : 4;
+    static constexpr int blocks = COLL == 1 ? (ST == 0 ? PWFA_FLUID_MIN_BLOCKS : PWFA_FLUID_MIN_BLOCKS_16) : 4;
 };
 
 // Where the fused diagnostics of a step go. The fluid launch writes one FP32
