@@ -316,14 +316,16 @@ def test_unstable_state_is_reported(defect):
         assert e.value.code == -3
 
 
-@pytest.mark.parametrize("boundary,collision", [(W.OPEN, W.REGULARIZED), (W.OPEN, W.BGK), (W.PERIODIC, W.BGK)])
-def test_fused_field_step(boundary, collision):
+@pytest.mark.parametrize("boundary,collision,nx", [(W.OPEN, W.REGULARIZED, 70), (W.OPEN, W.BGK, 70),
+                                                   (W.PERIODIC, W.BGK, 70), (W.OPEN, W.REGULARIZED, 72),
+                                                   (W.OPEN, W.BGK, 72)])
+def test_fused_field_step(boundary, collision, nx):
     """Ampere fused with the next step's Faraday (one kernel, tiles of 31 x 7
     nodes over 16 planes, E of the +1 neighbours evaluated twice) against the
     separate kernels on a grid that spans several tiles in every direction
     with ragged ends: the same arithmetic, so the same state bit for bit,
     also across a state import and through the fused step diagnostics."""
-    w = W.parity_small().replace(nx=70, ny=23, nz=37, boundary=boundary, collision=collision, alpha=0.5,
+    w = W.parity_small().replace(nx=nx, ny=23, nz=37, boundary=boundary, collision=collision, alpha=0.5,
                                  z0=-1.0, tau=0.6)
     with lbm.Simulation(w) as a, lbm.Simulation(w) as b:
         a.set_field_fusion(lbm.Simulation.FUSION_ON)
