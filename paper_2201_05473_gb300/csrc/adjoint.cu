@@ -71,6 +71,18 @@ __device__ __forceinline__ Nbr nbr_of(const Grid& g, int i, int j, int k) {
 }
 __device__ __forceinline__ float msk(bool ok, float v) { return ok ? v : 0.0f; }
 
+// R3's transposed average of one face component: b_bar at the node and its
+// three neighbours across the face (the node B is the mean of two time
+// levels, each the mean of four faces: 1/8 per face), each masked by its
+// in-grid flag. R4's update of one E_bar component: e the sum of the two
+// node-averaged E_bar of the edge, d the transposed Faraday curl of Bn_bar.
+// Both the separate and the fused kernels go through these, so they agree
+// bit for bit.
+__device__ __forceinline__ float r3_sum(float v0, float v1, float v2, float v3, bool m1, bool m2, bool m3) {
+    return 0.125f * (v0 + msk(m1, v1) + msk(m2, v2) + msk(m3, v3));
+}
+__device__ __forceinline__ float r4_arith(float c, float E, float e, float d) { return E + 0.5f * e + c * d; }
+
 // ------------------------------------------------------------------- R1
 // Every load of a node is issued before any is used; the driver-gradient
 // terms are formed and summed over the warp in FP32 (FP64 arithmetic is slow
@@ -522,20 +534,20 @@ __global__ void __launch_bounds__(kBX * kBY) adj_faces_kernel(const AdjArgs a) {
     const float* bz = a.bbar[2];
     float sx, sy, sz;
     if (PER) {
-        sx = 0.125f * (rd<true>(g, bx, i, j, k) + rd<true>(g, bx, i, j + 1, k) + rd<true>(g, bx, i, j, k + 1)
-                       + rd<true>(g, bx, i, j + 1, k + 1));
-        sy = 0.125f * (rd<true>(g, by, i, j, k) + rd<true>(g, by, i + 1, j, k) + rd<true>(g, by, i, j, k + 1)
-                       + rd<true>(g, by, i + 1, j, k + 1));
-        sz = 0.125f * (rd<true>(g, bz, i, j, k) + rd<true>(g, bz, i + 1, j, k) + rd<true>(g, bz, i, j + 1, k)
-                       + rd<true>(g, bz, i + 1, j + 1, k));
+        sx = r3_sum(rd<true>(g, bx, i, j, k), rd<true>(g, bx, i, j + 1, k), rd<true>(g, bx, i, j, k + 1),
+                    rd<true>(g, bx, i, j + 1, k + 1), true, true, true);
+        sy = r3_sum(rd<true>(g, by, i, j, k), rd<true>(g, by, i + 1, j, k), rd<true>(g, by, i, j, k + 1),
+                    rd<true>(g, by, i + 1, j, k + 1), true, true, true);
+        sz = r3_sum(rd<true>(g, bz, i, j, k), rd<true>(g, bz, i + 1, j, k), rd<true>(g, bz, i, j + 1, k),
+                    rd<true>(g, bz, i + 1, j + 1, k), true, true, true);
     } else {
         const Nbr n = nbr_of(g, i, j, k);
         const float x0 = bx[o], x1 = bx[o + n.pj], x2 = bx[o + n.pk], x3 = bx[o + n.pj + n.pk];
         const float y0 = by[o], y1 = by[o + n.pi], y2 = by[o + n.pk], y3 = by[o + n.pi + n.pk];
         const float z0 = bz[o], z1 = bz[o + n.pi], z2 = bz[o + n.pj], z3 = bz[o + n.pi + n.pj];
-        sx = 0.125f * (x0 + msk(n.jp, x1) + msk(n.kp, x2) + msk(n.jp && n.kp, x3));
-        sy = 0.125f * (y0 + msk(n.ip, y1) + msk(n.kp, y2) + msk(n.ip && n.kp, y3));
-        sz = 0.125f * (z0 + msk(n.ip, z1) + msk(n.jp, z2) + msk(n.ip && n.jp, z3));
+        sx = r3_sum(x0, x1, x2, x3, n.jp, n.kp, n.jp && n.kp);
+        sy = r3_sum(y0, y1, y2, y3, n.ip, n.kp, n.ip && n.kp);
+        sz = r3_sum(z0, z1, z2, z3, n.ip, n.jp, n.ip && n.jp);
     }
     const float s3[3] = {sx, sy, sz};
     const float bn[3] = {a.Bnp[0][o], a.Bnp[1][o], a.Bnp[2][o]};
@@ -599,9 +611,110 @@ __global__ void __launch_bounds__(kBX * kBY) adj_edges_kernel(const AdjArgs a) {
     const bool a0 = PER || act_E(g, 0, i, j, k);
     const bool a1 = PER || act_E(g, 1, i, j, k);
     const bool a2 = PER || act_E(g, 2, i, j, k);
-    a.Ebar[0][o] = a0 ? E0 + 0.5f * e0 + c * (by - by_k - bz + bz_j) : 0.0f;
-    a.Ebar[1][o] = a1 ? E1 + 0.5f * e1 + c * (-bx + bx_k + bz - bz_i) : 0.0f;
-    a.Ebar[2][o] = a2 ? E2 + 0.5f * e2 + c * (bx - bx_j - by + by_i) : 0.0f;
+    a.Ebar[0][o] = a0 ? r4_arith(c, E0, e0, by - by_k - bz + bz_j) : 0.0f;
+    a.Ebar[1][o] = a1 ? r4_arith(c, E1, e1, -bx + bx_k + bz - bz_i) : 0.0f;
+    a.Ebar[2][o] = a2 ? r4_arith(c, E2, e2, bx - bx_j - by + by_i) : 0.0f;
+}
+
+// ------------------------------------------------------------- R3 + R4
+// R3 and R4 in one kernel. A block of kRX x kRY threads owns (kRX - 1) x
+// (kRY - 1) columns and marches up kRZ planes, starting one plane below its
+// slab. Each thread forms R3 at its column (lane 0 and row 0 are the -x / -y
+// neighbour columns of the tile, evaluated again by their owners), so the
+// new Bn_bar stays on chip: R4 takes the -x neighbour's by a shuffle, the
+// -y neighbour's from shared memory (one barrier per plane, two buffers) and
+// the -z one from the thread's registers. Nothing reads Bn_bar after R4, so
+// it is not written back: 72 B per node against the separate kernels' 96.
+constexpr int kRX = 32, kRY = 8, kRZ = 16;
+
+template <bool PER>
+__global__ void __launch_bounds__(kRX * kRY, 4) adj_faces_edges_kernel(const AdjArgs a) {
+    const Grid& g = a.f.g;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
+    __shared__ float sBx[2][kRY][kRX], sBz[2][kRY][kRX];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = (int)blockIdx.x * (kRX - 1) + tx - 1, y = (int)blockIdx.y * (kRY - 1) + ty - 1;
+    const bool own = tx > 0 && ty > 0 && x < nx && y < ny;
+    // the evaluated column: wrapped (periodic) or clamped into the grid (an
+    // open grid's clamped -1 column is masked by R4's bound below)
+    const int xe = PER ? (x < 0 ? x + nx : x % nx) : min(max(x, 0), nx - 1);
+    const int ye = PER ? (y < 0 ? y + ny : y % ny) : min(max(y, 0), ny - 1);
+    // +1 neighbours (R3, R4's node averages) and -1 bounds (R4's curl)
+    const bool ip = PER || xe + 1 < nx, jp = PER || ye + 1 < ny;
+    const bool im = PER || x > 0, jm = PER || y > 0;
+    const int pi = xe + 1 < nx ? 1 : (PER ? 1 - nx : 0);
+    const int pj = ye + 1 < ny ? nx : (PER ? nx - nxy : 0);
+    const float c = a.f.cdt;
+    const float *bx = a.bbar[0], *by = a.bbar[1], *bz = a.bbar[2];
+
+    const int kz0 = (int)blockIdx.z * kRZ, kend = min(kz0 + kRZ, nz);
+    const int kfirst = PER || kz0 > 0 ? kz0 - 1 : kz0;
+    float pbx = 0.0f, pby = 0.0f;  // new Bn_bar (x, y) of the plane below
+    for (int k = kfirst; k < kend; ++k) {
+        const int kk = k < 0 ? k + nz : k;
+        const int buf = (k - kfirst) & 1;
+        int o = (kk * ny + ye) * nx + xe;
+#ifdef PWFA_DEBUG
+        o = (int)PWFA_CHECK(a.f.dbg, o, 0, g.N, 7u);
+#endif
+        const bool kp = PER || kk + 1 < nz, km = PER || kk > 0;
+        const int pk = kk + 1 < nz ? nxy : (PER ? nxy - nz * nxy : 0);
+        // R3 at (xe, ye, kk)
+        const float x0 = bx[o], x1 = bx[o + pj], x2 = bx[o + pk], x3 = bx[o + pj + pk];
+        const float y0 = by[o], y1 = by[o + pi], y2 = by[o + pk], y3 = by[o + pi + pk];
+        const float z0 = bz[o], z1 = bz[o + pi], z2 = bz[o + pj], z3 = bz[o + pi + pj];
+        const float bn0 = a.Bnp[0][o], bn1 = a.Bnp[1][o], bn2 = a.Bnp[2][o];
+        // R4's loads, issued with R3's (owned nodes of the slab only)
+        const bool slab = own && k >= kz0;
+        float ex0 = 0.0f, ex1 = 0.0f, ey0 = 0.0f, ey1 = 0.0f, ez0 = 0.0f, ez1 = 0.0f, E0 = 0.0f, E1 = 0.0f, E2 = 0.0f;
+        if (slab) {
+            const float* ex = a.ebar[0];
+            const float* ey = a.ebar[1];
+            const float* ez = a.ebar[2];
+            ex0 = ex[o];
+            ex1 = ex[o + pi];
+            ey0 = ey[o];
+            ey1 = ey[o + pj];
+            ez0 = ez[o];
+            ez1 = ez[o + pk];
+            E0 = a.Ebar[0][o];
+            E1 = a.Ebar[1][o];
+            E2 = a.Ebar[2][o];
+        }
+        const float s3[3] = {r3_sum(x0, x1, x2, x3, jp, kp, jp && kp), r3_sum(y0, y1, y2, y3, ip, kp, ip && kp),
+                             r3_sum(z0, z1, z2, z3, ip, jp, ip && jp)};
+        const float bn[3] = {bn0, bn1, bn2};
+        float bnew[3];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const bool on = PER || act_B(g, cc, xe, ye, kk);
+            const float bnt = bn[cc] + s3[cc];
+            bnew[cc] = on ? bnt : 0.0f;
+            if (slab) a.Bbar[cc][o] = on ? bnt + s3[cc] : 0.0f;
+        }
+        // R4 at (x, y, kk): the -x neighbour's Bn_bar from lane - 1, the -y
+        // neighbour's from row - 1, the -z one from the plane below
+        const float bz_i = __shfl_up_sync(0xffffffffu, bnew[2], 1);
+        const float by_i = __shfl_up_sync(0xffffffffu, bnew[1], 1);
+        sBx[buf][ty][tx] = bnew[0];
+        sBz[buf][ty][tx] = bnew[2];
+        __syncthreads();
+        if (slab) {
+            const float bx_j = msk(jm, sBx[buf][ty - 1][tx]), bz_j = msk(jm, sBz[buf][ty - 1][tx]);
+            const float bx_k = msk(km, pbx), by_k = msk(km, pby);
+            const float bz_im = msk(im, bz_i), by_im = msk(im, by_i);
+            const float e0 = ex0 + msk(ip, ex1), e1 = ey0 + msk(jp, ey1), e2 = ez0 + msk(kp, ez1);
+            const float bxn = bnew[0], byn = bnew[1], bzn = bnew[2];
+            const bool a0 = PER || act_E(g, 0, x, y, kk);
+            const bool a1 = PER || act_E(g, 1, x, y, kk);
+            const bool a2 = PER || act_E(g, 2, x, y, kk);
+            a.Ebar[0][o] = a0 ? r4_arith(c, E0, e0, byn - by_k - bzn + bz_j) : 0.0f;
+            a.Ebar[1][o] = a1 ? r4_arith(c, E1, e1, -bxn + bx_k + bzn - bz_im) : 0.0f;
+            a.Ebar[2][o] = a2 ? r4_arith(c, E2, e2, bxn - bx_j - byn + by_im) : 0.0f;
+        }
+        pbx = bnew[0];
+        pby = bnew[1];
+    }
 }
 
 // ------------------------------------------------------------- profile
@@ -723,12 +836,20 @@ cudaError_t launch_adjoint_fluid(const AdjArgs& a0, int storage, int collision, 
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_adjoint_fields(const AdjArgs& a0, cudaStream_t s) {
+cudaError_t launch_adjoint_fields(const AdjArgs& a0, bool fused, cudaStream_t s) {
     const AdjArgs a = with_driver_factors(a0);
     if (!a.f.couple) return cudaSuccess;
     const Grid& g = a.f.g;
-    const dim3 grid = grid_of(g, kBX, kBY), block(kBX, kBY, 1);
     const bool per = g.periodic;
+    if (fused) {
+        const dim3 tiles((unsigned)(g.nx + kRX - 2) / (kRX - 1), (unsigned)(g.ny + kRY - 2) / (kRY - 1),
+                         (unsigned)(g.nz + kRZ - 1) / kRZ);
+        const dim3 block(kRX, kRY, 1);
+        if (per) adj_faces_edges_kernel<true><<<tiles, block, 0, s>>>(a);
+        else adj_faces_edges_kernel<false><<<tiles, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    const dim3 grid = grid_of(g, kBX, kBY), block(kBX, kBY, 1);
     if (per) adj_faces_kernel<true><<<grid, block, 0, s>>>(a);
     else adj_faces_kernel<false><<<grid, block, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
@@ -741,7 +862,7 @@ cudaError_t launch_adjoint_fields(const AdjArgs& a0, cudaStream_t s) {
 cudaError_t launch_adjoint_step(const AdjArgs& a, int storage, int collision, cudaStream_t s) {
     cudaError_t e = launch_adjoint_ampere(a, s);
     if (e == cudaSuccess) e = launch_adjoint_fluid(a, storage, collision, s);
-    if (e == cudaSuccess) e = launch_adjoint_fields(a, s);
+    if (e == cudaSuccess) e = launch_adjoint_fields(a, true, s);
     return e;
 }
 

@@ -1015,8 +1015,9 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, int32_t nst
             rc = timed_launch(h, PWFA_KERNEL_ADJ_FLUID, "adjoint fluid kernel",
                               [&] { return launch_adjoint_fluid(a, in.p.storage, in.p.collision, s); });
             if (rc) return rc;
-            rc = timed_launch(h, PWFA_KERNEL_ADJ_FIELD, "adjoint field kernels",
-                              [&] { return launch_adjoint_fields(a, s); });
+            rc = timed_launch(h, PWFA_KERNEL_ADJ_FIELD, "adjoint field kernels", [&] {
+                return launch_adjoint_fields(a, h->field_fusion != PWFA_FUSION_OFF, s);
+            });
             if (rc) return rc;
             cur = 1 - cur;
         }

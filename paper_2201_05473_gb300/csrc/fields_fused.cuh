@@ -23,7 +23,9 @@ namespace pwfa {
 // march also keeps B_{n+1} of plane k - 1 (Ampere's -z neighbour) and J_z of
 // plane k + 1 (the next plane's own value) in registers, and the column's
 // neighbour offsets, wall masks and the driver's transverse factor are
-// computed once: per plane a thread loads 15 values. Open-grid neighbours
+// computed once: per plane a thread loads 15 values. The driver's
+// longitudinal factor of plane kz0 + l is evaluated once per warp, by lane l,
+// and each plane takes it by a shuffle. Open-grid neighbours
 // below index 0 read the zero guard in front of each array; +1 neighbours
 // are clamped into the grid (the conducting walls discard what they feed).
 #ifndef PWFA_AF_Y
@@ -35,7 +37,12 @@ namespace pwfa {
 #ifndef PWFA_AF_MIN_BLOCKS
 #define PWFA_AF_MIN_BLOCKS 4
 #endif
-constexpr int kAFX = 32, kAFY = PWFA_AF_Y, kAFZ = PWFA_AF_Z;
+#ifndef PWFA_AF_UNROLL
+#define PWFA_AF_UNROLL 1
+#endif
+constexpr int kAFX = 32, kAFY = PWFA_AF_Y, kAFZ = PWFA_AF_Z, kAFUnroll = PWFA_AF_UNROLL;
+// one lane per plane of a slab, the plane above it included
+static_assert(kAFZ < kAFX, "the driver's per-plane factors are held one per lane");
 
 // The 15 values a thread loads for one plane of its column.
 struct AFPlane {
@@ -104,6 +111,9 @@ __device__ __forceinline__ void ampere_faraday_tile(const StepArgs& a, const Fie
     const float c = a.cdt, dt = a.dt;
 
     const int kz0 = tbz * kAFZ, kend = min(kz0 + kAFZ, nz);
+    // lane l holds the longitudinal factor of plane kz0 + l (same function,
+    // same arguments as everywhere else: the same value)
+    const float glane = a.alpha != 0.0f && tx <= kAFZ ? driver_longitudinal(a, kz0 + tx, zc) : 0.0f;
     // plane offsets: o of plane k (wrapped on a periodic grid), zp its +z
     // neighbour offset (clamped on an open grid)
     auto plane_o = [&](int k) { return ((PER && k >= nz ? k - nz : k) * ny + ye) * nx + xe; };
@@ -127,18 +137,22 @@ __device__ __forceinline__ void ampere_faraday_tile(const StepArgs& a, const Fie
     AFPlane nxt;
     af_load<PER>(a, o, plane_zp(kz0), xm, ym, xp, yp, nxt);
     int oprev = o;
+#pragma unroll kAFUnroll
     for (int k = kz0; k <= kend; ++k) {
         const int buf = (k - kz0) & 1;
         const bool valid = PER || k < nz;
         const AFPlane v = nxt;
-        if (k < kend && (PER || k + 1 < nz)) af_load<PER>(a, plane_o(k + 1), plane_zp(k + 1), xm, ym, xp, yp, nxt);
+        // plane_o(k + 1), one plane up from o (wrapped on a periodic grid)
+        const int onext = PER && k + 1 >= nz ? o + nxy - nz * nxy : o + nxy;
+        if (k < kend && (PER || k + 1 < nz)) af_load<PER>(a, onext, plane_zp(k + 1), xm, ym, xp, yp, nxt);
         float e0 = valid ? v.e0 : 0.0f, e1 = valid ? v.e1 : 0.0f, e2 = valid ? v.e2 : 0.0f;
+        const float gl = __shfl_sync(0xffffffffu, glane, k - kz0);
         if (valid) {
             const bool kin = PER || (k >= 1 && k <= nz - 2), klo = PER || k <= nz - 2;
             if (mEx && kin) e0 = ampere_arith(c, dt, e0, v.bz - v.bz_j, v.by - bp1, 0.5f * (v.j0 + v.j0_i));
             if (mEy && kin) e1 = ampere_arith(c, dt, e1, v.bx - bp0, v.bz - v.bz_i, 0.5f * (v.j1 + v.j1_j));
             if (mEz && klo) {
-                const float jb = a.alpha != 0.0f ? -(gT * driver_longitudinal(a, k, zc)) : 0.0f;
+                const float jb = a.alpha != 0.0f ? -(gT * gl) : 0.0f;
                 e2 = ampere_arith(c, dt, e2, v.by - v.by_i, v.bx - v.bx_j, 0.5f * (j2n + v.j2k) + jb);
             }
             if (own && k < kend) {
@@ -184,7 +198,7 @@ __device__ __forceinline__ void ampere_faraday_tile(const StepArgs& a, const Fie
         bp2 = v.bz;
         j2n = v.j2k;
         oprev = o;
-        o = plane_o(k + 1);
+        o = onext;
     }
 }
 

@@ -30,11 +30,12 @@ struct AdjArgs {
 };
 
 // R1..R4 of one reversed step on stream s: R1 (launch_adjoint_ampere), R2a
-// and R2 (launch_adjoint_fluid), R3 and R4 (launch_adjoint_fields), in that
-// order.
+// and R2 (launch_adjoint_fluid), R3 and R4 (launch_adjoint_fields: one fused
+// kernel, or two separate ones when fused is false; the same results bit
+// for bit), in that order.
 cudaError_t launch_adjoint_ampere(const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint_fluid(const AdjArgs& a, int storage, int collision, cudaStream_t s);
-cudaError_t launch_adjoint_fields(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_fields(const AdjArgs& a, bool fused, cudaStream_t s);
 cudaError_t launch_adjoint_step(const AdjArgs& a, int storage, int collision, cudaStream_t s);
 
 // grad[0..2] = the sums of the driver-gradient slots.
