@@ -147,7 +147,11 @@ int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps);
  * ckpt_every recomputed steps (two population buffers, the E and B of its
  * states, 6 (K + 1) N values, and the four lattice sums of each step, 4 K N:
  * the reverse step needs nothing else of the populations); ~174 N floats of
- * adjoint scratch; PWFA_ERR_ALLOC if it does not fit. */
+ * adjoint scratch; PWFA_ERR_ALLOC if it does not fit. The last segment
+ * runs as the reverse sweep would recompute it, into the segment storage,
+ * so the next pwfa_lbm_adjoint_step reverses it without recomputing it; with
+ * ckpt_every >= nsteps (one segment of nsteps steps, when memory allows)
+ * that sweep recomputes nothing. */
 int pwfa_lbm_record(pwfa_lbm_t* h, int32_t instance, int32_t nsteps, int32_t ckpt_every);
 
 /* Gradient of an objective L of the raw Yee E after T recorded steps with
@@ -335,7 +339,9 @@ int pwfa_lbm_set_batching(pwfa_lbm_t* h, int32_t enable);
  * the fused kernel. Modes: OFF (separate launches), AUTO (the default: fused
  * on grids of 4 Mi nodes or more, where it is faster, and in the batched
  * path, whose field launch spans every instance), ON (always);
- * PWFA_ERR_PARAM for another value. */
+ * PWFA_ERR_PARAM for another value. In the adjoint sweep the transposed
+ * node averages and Faraday update run as one kernel unless the mode is
+ * OFF (the same results, bit for bit). */
 #define PWFA_FUSION_OFF 0
 #define PWFA_FUSION_AUTO 1
 #define PWFA_FUSION_ON 2

@@ -92,6 +92,7 @@ struct Instance {
         void* seg = nullptr;
         size_t seg_stride = 0;
         void* adj = nullptr;
+        int filled = -1;  // segment whose per-step slots already hold its steps
     } rec;
 };
 
@@ -807,6 +808,99 @@ int64_t witness_slab(const Instance& in, int64_t T, int* k_out, std::vector<int>
     return count;
 }
 
+// The slots of one segment of a recording (SegLayout): the population
+// buffers its steps ping-pong between, E and B of each state, the lattice
+// sums of each step.
+struct SegSlots {
+    SegLayout L;
+    char* p;
+    void* pop(int64_t j) const { return p + L.pop((int)(j & 1)); }
+    float* E(int64_t j, int c) const { return (float*)(p + L.E(j, c)); }
+    float* B(int64_t j, int c) const { return (float*)(p + L.B(j, c)); }
+    float* mom(int64_t j) const { return (float*)(p + L.mom(j)); }
+};
+SegSlots seg_slots(const Instance& in) { return SegSlots{seg_layout(in, in.rec.K), static_cast<char*>(in.rec.seg)}; }
+
+// Run segment seg of the recording (steps s0 = seg K .. s1) from its
+// checkpoint into the segment slots. Its last step leaves the populations
+// at s1 in in.f[1 - in.fcur], E(t_s1) in in.E and B(t_s1) in slot B(s1 - s0);
+// J in in.J.
+int fill_segment(pwfa_lbm* h, Instance& in, int seg) {
+    cudaStream_t s = h->stream;
+    const auto& r = in.rec;
+    const int64_t N = in.g.N;
+    const int64_t s0 = (int64_t)seg * r.K, s1 = std::min<int64_t>(r.T, s0 + r.K);
+    const SegSlots S = seg_slots(in);
+    // restore the checkpoint into state 0 of the segment
+    {
+        StateRef cp = state_at(in, (char*)r.cp + r.cp_stride * seg, false);
+        const size_t fb = (size_t)in.g.Np * kPop * storage_bytes(in.p.storage);
+        PWFA_CUDA(cudaMemcpyAsync(S.pop(0), cp.f, fb, cudaMemcpyDeviceToDevice, s), "restore copy");
+        for (int c = 0; c < 3; ++c) {
+            PWFA_CUDA(cudaMemcpyAsync(S.E(0, c), cp.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                      "restore copy");
+            PWFA_CUDA(cudaMemcpyAsync(S.B(0, c), cp.B[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                      "restore copy");
+        }
+    }
+    // recompute the segment's steps: populations ping-pong, E and B of
+    // each state and the lattice sums of each step into their slots; Ampere
+    // of step j runs fused with Faraday of step j + 1 where that B slot
+    // exists
+    const int64_t len = s1 - s0;
+    bool b_ahead = false;
+    for (int64_t j = 0; j < len; ++j) {
+        const int64_t keep_steps = in.steps;
+        in.steps = s0 + j;
+        StepArgs f = make_args(in);
+        in.steps = keep_steps;
+        const bool last = j + 1 == len;
+        f.fin = S.pop(j);
+        f.fout = last ? in.f[1 - in.fcur] : S.pop(j + 1);
+        f.mom = S.mom(j);
+        for (int c = 0; c < 3; ++c) {
+            f.E[c] = S.E(j, c);
+            f.Bc[c] = S.B(j, c);
+            f.Bn[c] = S.B(j + 1, c);
+            f.Eout[c] = last ? in.E[c] : S.E(j + 1, c);  // Ampere out of place writes every component
+        }
+        if (in.p.couple) {
+            if (!b_ahead) {
+                int rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(f, s); });
+                if (rc) return rc;
+            }
+        } else {
+            // no Maxwell update: E and B pass through
+            for (int c = 0; c < 3; ++c) {
+                PWFA_CUDA(cudaMemcpyAsync(f.Bn[c], f.Bc[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                          "B copy");
+                PWFA_CUDA(cudaMemcpyAsync(f.Eout[c], f.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
+                          "E copy");
+            }
+        }
+        int rc = timed_launch(h, PWFA_KERNEL_FLUID, "fluid kernel",
+                              [&] { return launch_fluid_mom(f, in.p.storage, in.p.collision, s); });
+        if (rc) return rc;
+        b_ahead = false;
+        if (in.p.couple && !last && fusable(in.p)) {
+            // B(t_{n+2}) of the next recomputed step into its slot
+            FieldPair out{};
+            for (int c = 0; c < 3; ++c) {
+                out.E[c] = f.Eout[c];
+                out.B[c] = S.B(j + 2, c);
+            }
+            rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere-faraday kernel",
+                              [&] { return launch_ampere_faraday(f, out, s); });
+            if (rc) return rc;
+            b_ahead = true;
+        } else if (in.p.couple) {
+            rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere kernel", [&] { return launch_ampere(f, s); });
+            if (rc) return rc;
+        }
+    }
+    return PWFA_OK;
+}
+
 int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_every) {
     cudaStream_t s = h->stream;
     if (in.p.moving_window) return fail(PWFA_ERR_PARAM, "the adjoint does not support the moving window");
@@ -836,7 +930,10 @@ int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_ever
     PWFA_CUDA(cudaMemsetAsync(r.seg, 0, seg_bytes, s), "cudaMemsetAsync");
     int rc = reset_instance(in, s);
     if (rc) return rc;
-    for (int32_t n = 0; n < nsteps; ++n) {
+    // the segments before the last one: ordinary steps with a checkpoint at
+    // the start of each
+    const int64_t s_last = (int64_t)(r.ncp - 1) * r.K;
+    for (int64_t n = 0; n < s_last; ++n) {
         if (n % r.K == 0) {
             rc = copy_state(in, state_at(in, (char*)r.cp + r.cp_stride * (n / r.K), false), true, s);
             if (rc) return rc;
@@ -844,8 +941,30 @@ int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_ever
         rc = step_instance(h, in);
         if (rc) return rc;
     }
+    rc = copy_state(in, state_at(in, (char*)r.cp + r.cp_stride * (r.ncp - 1), false), true, s);
+    if (rc) return rc;
+    // the last segment runs as the reverse sweep would recompute it, into
+    // the segment slots, which the sweep then reverses first without a
+    // recomputation (with one segment, ckpt_every >= nsteps, nothing is
+    // recomputed at all)
+    rc = fill_segment(h, in, r.ncp - 1);
+    if (rc) return rc;
+    // the state at T: populations and E where the last step left them, B
+    // from the segment's last slot
+    in.fcur = 1 - in.fcur;
+    {
+        const SegSlots S = seg_slots(in);
+        for (int c = 0; c < 3; ++c)
+            PWFA_CUDA(cudaMemcpyAsync(in.B[in.bcur][c], S.B(r.T - s_last, c), sizeof(float) * (size_t)in.g.N,
+                                      cudaMemcpyDeviceToDevice, s),
+                      "B copy");
+    }
+    in.lookahead = false;
+    in.steps = r.T;
+    h->batch_valid = false;  // the batch table holds the population pointers
     rc = copy_state(in, state_at(in, (char*)r.cp + r.cp_stride * r.ncp, false), true, s);
     if (rc) return rc;
+    r.filled = r.ncp - 1;
     r.valid = true;
     return PWFA_OK;
 }
@@ -916,79 +1035,15 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, int32_t nst
     int cur = 0;
     for (int seg = r.ncp - 1; seg >= 0; --seg) {
         const int64_t s0 = (int64_t)seg * r.K, s1 = std::min<int64_t>(r.T, s0 + r.K);
-        // segment storage (SegLayout)
-        const SegLayout L = seg_layout(in, r.K);
-        char* segp = static_cast<char*>(r.seg);
-        auto pop_buf = [&](int64_t j) -> void* { return segp + L.pop((int)(j & 1)); };
-        auto E_slot = [&](int64_t j, int c) -> float* { return (float*)(segp + L.E(j, c)); };
-        auto B_slot = [&](int64_t j, int c) -> float* { return (float*)(segp + L.B(j, c)); };
-        auto mom_slot = [&](int64_t j) -> float* { return (float*)(segp + L.mom(j)); };
-        // restore the checkpoint into state 0 of the segment
-        {
-            StateRef cp = state_at(in, (char*)r.cp + r.cp_stride * seg, false);
-            const size_t fb = (size_t)in.g.Np * kPop * storage_bytes(in.p.storage);
-            PWFA_CUDA(cudaMemcpyAsync(pop_buf(0), cp.f, fb, cudaMemcpyDeviceToDevice, s), "restore copy");
-            for (int c = 0; c < 3; ++c) {
-                PWFA_CUDA(cudaMemcpyAsync(E_slot(0, c), cp.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
-                          "restore copy");
-                PWFA_CUDA(cudaMemcpyAsync(B_slot(0, c), cp.B[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
-                          "restore copy");
-            }
-        }
-        // recompute the segment's steps: populations ping-pong, E and B of
-        // each state and the lattice sums of each step into their slots; Ampere
-        // of step j runs fused with Faraday of step j + 1 where that B slot
-        // exists
-        const int64_t len = s1 - s0;
-        bool b_ahead = false;
-        for (int64_t j = 0; j < len; ++j) {
-            const int64_t keep_steps = in.steps;
-            in.steps = s0 + j;
-            StepArgs f = make_args(in);
-            in.steps = keep_steps;
-            const bool last = j + 1 == len;
-            f.fin = pop_buf(j);
-            f.fout = last ? in.f[1 - in.fcur] : pop_buf(j + 1);
-            f.mom = mom_slot(j);
-            for (int c = 0; c < 3; ++c) {
-                f.E[c] = E_slot(j, c);
-                f.Bc[c] = B_slot(j, c);
-                f.Bn[c] = B_slot(j + 1, c);
-                f.Eout[c] = last ? in.E[c] : E_slot(j + 1, c);  // Ampere out of place writes every component
-            }
-            if (in.p.couple) {
-                if (!b_ahead) {
-                    int rc = timed_launch(h, PWFA_KERNEL_FARADAY, "faraday kernel", [&] { return launch_faraday(f, s); });
-                    if (rc) return rc;
-                }
-            } else {
-                // no Maxwell update: E and B pass through
-                for (int c = 0; c < 3; ++c) {
-                    PWFA_CUDA(cudaMemcpyAsync(f.Bn[c], f.Bc[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
-                              "B copy");
-                    PWFA_CUDA(cudaMemcpyAsync(f.Eout[c], f.E[c], sizeof(float) * N, cudaMemcpyDeviceToDevice, s),
-                              "E copy");
-                }
-            }
-            int rc = timed_launch(h, PWFA_KERNEL_FLUID, "fluid kernel",
-                                  [&] { return launch_fluid_mom(f, in.p.storage, in.p.collision, s); });
+        const SegSlots S = seg_slots(in);
+        // the recording leaves its last segment's steps in the slots; every
+        // other segment is recomputed from its checkpoint (which overwrites
+        // them)
+        const bool have = r.filled == seg;
+        r.filled = -1;
+        if (!have) {
+            int rc = fill_segment(h, in, seg);
             if (rc) return rc;
-            b_ahead = false;
-            if (in.p.couple && !last && fusable(in.p)) {
-                // B(t_{n+2}) of the next recomputed step into its slot
-                FieldPair out{};
-                for (int c = 0; c < 3; ++c) {
-                    out.E[c] = f.Eout[c];
-                    out.B[c] = B_slot(j + 2, c);
-                }
-                rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere-faraday kernel",
-                                  [&] { return launch_ampere_faraday(f, out, s); });
-                if (rc) return rc;
-                b_ahead = true;
-            } else if (in.p.couple) {
-                rc = timed_launch(h, PWFA_KERNEL_AMPERE, "ampere kernel", [&] { return launch_ampere(f, s); });
-                if (rc) return rc;
-            }
         }
         for (int64_t n = s1 - 1; n >= s0; --n) {
             const int64_t j = n - s0;
@@ -998,11 +1053,11 @@ int adjoint_instance(pwfa_lbm* h, Instance& in, const float* seed_E, int32_t nst
             in.steps = keep_steps;
             f.fin = nullptr;  // the reverse step reads the lattice sums instead
             f.fout = nullptr;
-            f.mom = mom_slot(j);
+            f.mom = S.mom(j);
             for (int c = 0; c < 3; ++c) {
-                f.E[c] = E_slot(j, c);
-                f.Bc[c] = B_slot(j, c);
-                f.Bn[c] = B_slot(j + 1, c);
+                f.E[c] = S.E(j, c);
+                f.Bc[c] = S.B(j, c);
+                f.Bn[c] = S.B(j + 1, c);
                 f.Eout[c] = nullptr;
                 f.J[c] = nullptr;
             }

@@ -197,3 +197,37 @@ def test_fused_faces_edges_equal_separate(boundary, collision):
             grads.append(sim.adjoint_step(seed))
     assert np.all(np.isfinite(grads[0])) and np.any(grads[0] != 0.0)
     assert np.allclose(grads[0], grads[1], rtol=1e-12, atol=1e-15), (grads[0], grads[1])
+
+
+def test_record_keeps_last_segment_and_single_segment():
+    """The recording runs its last segment into the segment slots, so the
+    sweep reverses that segment without recomputing it; with one segment
+    (ckpt_every >= nsteps) the sweep recomputes nothing. The gradient, and
+    the state the instance ends in, must not depend on it: the same as a
+    sweep that recomputes every segment (the second call on a recording)
+    and as a recording with several segments, up to the order of the FP64
+    atomic sums."""
+    w = W.parity_small().replace(nx=20, ny=16, nz=40, alpha=0.5, z0=-1.0, tau=0.6, collision=W.REGULARIZED,
+                                 profile=np.linspace(1.0, 0.7, 8), profile_rmax=2.0)
+    steps = 60
+    seed = random_seed(w, np.random.default_rng(9)).astype(np.float32)
+    mask = lbm.FIELD_N | lbm.FIELD_EZ | lbm.FIELD_BX
+    out = {}
+    for ck in (7, steps):
+        with lbm.Simulation(w) as sim:
+            sim.record(steps, ck)
+            after_record = sim.fields(mask).cpu().numpy()
+            g_first = sim.adjoint_step(seed)  # last segment taken from the recording
+            after_adjoint = sim.fields(mask).cpu().numpy()
+            g_again = sim.adjoint_step(seed)  # every segment recomputed
+            assert sim.steps_done() == steps
+        assert np.array_equal(after_record, after_adjoint)
+        assert np.allclose(g_first, g_again, rtol=1e-12, atol=1e-15), (g_first, g_again)
+        out[ck] = (after_record, g_first)
+    # the recording's end state does not depend on where its checkpoints are
+    assert np.array_equal(out[7][0], out[steps][0])
+    assert np.allclose(out[7][1], out[steps][1], rtol=1e-12, atol=1e-15), (out[7][1], out[steps][1])
+    # and equals plain stepping
+    with lbm.Simulation(w) as sim:
+        sim.step(steps)
+        assert np.array_equal(sim.fields(mask).cpu().numpy(), out[7][0])
