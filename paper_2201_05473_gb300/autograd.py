@@ -4,7 +4,9 @@
 L = -mean(E_z over the witness slab after ``steps`` steps) as a differentiable
 scalar of theta = (n_b/n0, sigma_r, sigma_z) and of the radial density profile.
 The forward pass records the run with sqrt(steps) checkpointing through the C
-ABI (pwfa_lbm_record) and evaluates the loss in the library
+ABI (pwfa_lbm_record; ckpt_every = steps keeps the whole run as one segment
+where device memory allows, and the backward pass then recomputes no
+forward step) and evaluates the loss in the library
 (pwfa_lbm_witness_loss); the backward pass calls the adjoint with the
 built-in witness seed (pwfa_lbm_adjoint_step with a NULL seed). All
 arithmetic runs in the CUDA library; this module only marshals arguments.
