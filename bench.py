@@ -314,6 +314,21 @@ def run_ours(args):
         sim.step(args.steps)
         kms, kl = sim.kernel_times()
         sim.profile(False)
+        # ---- repeatability: five timed runs of 200 steps each (the driver
+        # stays in the box), clocks sampled throughout
+        repeat = None
+        if not args.no_extra:
+            per = []
+            with ClockSampler(dev) as rclk:
+                for _ in range(5):
+                    ev0.record(stream)
+                    sim.step(200)
+                    ev1.record(stream)
+                    stream.synchronize()
+                    per.append(ev0.elapsed_time(ev1) / 200)
+            med = statistics.median(per)
+            repeat = {"reps": 5, "steps_each": 200, "median_ms_per_step": med, "min_ms_per_step": min(per),
+                      "max_ms_per_step": max(per), "glups_median": N / med / 1e6, "clocks": rclk.summary()}
         diag = sim.diag(check=False)
         sim.close()
         del sim
@@ -334,6 +349,19 @@ def run_ours(args):
             sim.close()
             stream.synchronize()
             e2e_s = time.perf_counter() - t0
+        # the same path over 200 steps (the creation spread over more steps)
+        e2e_200 = None
+        if not args.no_e2e and not args.no_extra:
+            torch.cuda.empty_cache()
+            barrier()
+            t0 = time.perf_counter()
+            sim = lbm.Simulation(w, stream=stream)
+            hd = host_diag.numpy()
+            for _ in range(200):
+                sim.step_diag(1, out=hd)
+            sim.close()
+            stream.synchronize()
+            e2e_200 = {"value": world * N * 200 / (time.perf_counter() - t0) / 1e9, "unit": "GLUPS", "steps": 200}
         def time_variant(w2):
             """The production timing of another form of the workload: warm-up,
             autotune, K steps under CUDA events, then K profiled steps."""
@@ -627,7 +655,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": lbm.ctypes.sizeof(lbm.Params) / args.steps,
                 "d2h_bytes_per_step": 64,
                 "note": "create from host params, then per step pwfa_lbm_step_diag (step + fused FP64 "
-                        "diagnostics, D2H into pinned host memory), destroy"},
+                        "diagnostics, D2H into pinned host memory), destroy",
+                "steps_200": e2e_200},
         "storage_forms": storage_lines or None,
         "bgk": bgk_line,
         "adjoint": adjoint_line,
@@ -636,6 +665,7 @@ def run_ours(args):
         "axisymmetric": axi_line,
         "pic_driver": pic_line,
         "clocks": clk.summary(),
+        "repeat": repeat,
         "diag_after": {"sum_n": diag[0], "min_n": diag[5], "max_beta": diag[6], "nonfinite": diag[7]},
     }
     if not args.no_cpu_baseline:

@@ -116,8 +116,10 @@ __device__ __forceinline__ void ampere_faraday_tile(const StepArgs& a, const Fie
     const float glane = a.alpha != 0.0f && tx <= kAFZ ? driver_longitudinal(a, kz0 + tx, zc) : 0.0f;
     // plane offsets: o of plane k (wrapped on a periodic grid), zp its +z
     // neighbour offset (clamped on an open grid)
-    auto plane_o = [&](int k) { return ((PER && k >= nz ? k - nz : k) * ny + ye) * nx + xe; };
-    auto plane_zp = [&](int k) { return k < nz - 1 ? nxy : (PER ? -(nz - 1) * nxy : 0); };
+    // (k runs to kend <= nz: on a periodic grid plane nz is plane 0 again)
+    auto wrapk = [&](int k) { return PER && k >= nz ? k - nz : k; };
+    auto plane_o = [&](int k) { return (wrapk(k) * ny + ye) * nx + xe; };
+    auto plane_zp = [&](int k) { return wrapk(k) < nz - 1 ? nxy : (PER ? -(nz - 1) * nxy : 0); };
     // carried from plane k - 1: own E_{n+3/2}, the +x and +y neighbours' E,
     // own B_{n+1}; J_z of plane k
     float ep0 = 0.0f, ep1 = 0.0f, ep2 = 0.0f, ezx = 0.0f, eyx = 0.0f, ezy = 0.0f, exy = 0.0f;
@@ -143,7 +145,7 @@ __device__ __forceinline__ void ampere_faraday_tile(const StepArgs& a, const Fie
         const bool valid = PER || k < nz;
         const AFPlane v = nxt;
         // plane_o(k + 1), one plane up from o (wrapped on a periodic grid)
-        const int onext = PER && k + 1 >= nz ? o + nxy - nz * nxy : o + nxy;
+        const int onext = PER && wrapk(k) + 1 >= nz ? o + nxy - nz * nxy : o + nxy;
         if (k < kend && (PER || k + 1 < nz)) af_load<PER>(a, onext, plane_zp(k + 1), xm, ym, xp, yp, nxt);
         float e0 = valid ? v.e0 : 0.0f, e1 = valid ? v.e1 : 0.0f, e2 = valid ? v.e2 : 0.0f;
         const float gl = __shfl_sync(0xffffffffu, glane, k - kz0);

@@ -6,7 +6,8 @@ its array's extent and records a bad one in the instance's debug word
 with PWFA_ERR_STATE. Here it runs the step paths on 8x8x8 and 16x8x8 grids
 (open and periodic, BGK and regularized, the three storage forms, the fused
 field step, the batched path, the moving window, the PIC driver, recording
-and the adjoint with its built-in loss) in a child process: every call must
+and the adjoint with its built-in loss, also from a one-segment recording)
+in a child process: every call must
 succeed, and the states must equal those of the release build.
 """
 import json
@@ -41,6 +42,8 @@ def cases():
         ("window", [long.replace(moving_window=1, window_z=0.2)], dict(steps=20)),
         ("pic", [long.replace(driver=1)], dict(steps=12, particles=400)),
         ("adjoint", [long.replace(profile=np.ones(4), profile_rmax=0.8)], dict(adjoint=12)),
+        ("adjoint_one_segment_periodic", [long.replace(boundary=W.PERIODIC, collision=W.REGULARIZED)],
+         dict(adjoint=10, ckpt=10)),
     ]
 
 
@@ -57,7 +60,7 @@ def run_cases(lbm):
                                            w.dx)
                 sim.set_particles(xp, wt)
             if "adjoint" in opt:
-                g = sim.adjoint_step(None, nsteps=opt["adjoint"], ckpt_every=5)
+                g = sim.adjoint_step(None, nsteps=opt["adjoint"], ckpt_every=opt.get("ckpt", 5))
                 out[name + "/grad"] = g
             else:
                 sim.step(opt["steps"])
