@@ -4,11 +4,12 @@ The debug build checks every element index the step kernels compute against
 its array's extent and records a bad one in the instance's debug word
 (without touching memory outside the array); the next public call then fails
 with PWFA_ERR_STATE. Here it runs the step paths on 8x8x8 and 16x8x8 grids
-(open and periodic, BGK and regularized, the three storage forms, the fused
-field step, the batched path, the moving window, the PIC driver, recording
-and the adjoint with its built-in loss, also from a one-segment recording)
-in a child process: every call must
-succeed, and the states must equal those of the release build.
+(open and periodic, BGK and regularized, the three storage forms, the staged
+fluid kernel, the fused field step, the batched path, the moving window, the
+PIC driver, recording and the adjoint with its built-in loss, from a
+one-segment recording and with the separate transposed field kernels) in a
+child process: every call must succeed, and the states must equal those of
+the release build.
 """
 import json
 import os
@@ -44,6 +45,11 @@ def cases():
         ("adjoint", [long.replace(profile=np.ones(4), profile_rmax=0.8)], dict(adjoint=12)),
         ("adjoint_one_segment_periodic", [long.replace(boundary=W.PERIODIC, collision=W.REGULARIZED)],
          dict(adjoint=10, ckpt=10)),
+        ("adjoint_fusion_off", [long.replace(profile=np.ones(4), profile_rmax=0.8)], dict(adjoint=12, fusion=0)),
+        ("fused_fields_periodic", [long.replace(boundary=W.PERIODIC)], dict(steps=25, fusion=2)),
+        ("batched_periodic", [base.replace(boundary=W.PERIODIC), long.replace(boundary=W.PERIODIC)],
+         dict(steps=10)),
+        ("staged_fluid", [long.replace(collision=W.REGULARIZED, storage=W.BF16)], dict(steps=12, variant=1)),
     ]
 
 
@@ -54,6 +60,9 @@ def run_cases(lbm):
         with lbm.Simulation(works) as sim:
             if "fusion" in opt:
                 sim.set_field_fusion(opt["fusion"])
+            if "variant" in opt:
+                for i in range(len(works)):
+                    sim.set_fluid_variant(opt["variant"], i)
             if "particles" in opt:
                 w = works[0]
                 xp, wt = W.bunch_particles(opt["particles"], w.alpha, w.sigma_r, w.sigma_z, w.z0, w.dt, w.nx, w.ny,
