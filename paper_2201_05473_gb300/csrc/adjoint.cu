@@ -152,13 +152,20 @@ __global__ void __launch_bounds__(kBX * kBY) adj_ampere_kernel(const AdjArgs a) 
             const float yr = ((float)j - 0.5f * (float)(g.ny - 1)) * a.f.dx;
             const float zeta = ((float)k + 0.5f) * a.f.dx - a.f.zc;
             const float r2 = xr * xr + yr * yr;
-            const float ga = expf(-r2 * a.f.inv2sr2) * expf(-zeta * zeta * a.f.inv2sz2);
-            const float w = dt * ez * ga;
-            g3[0] = w;
-            g3[1] = w * a.csr * r2;
-            g3[2] = w * a.csz * (zeta * zeta);
+            const float er = -r2 * a.f.inv2sr2, ez2 = -zeta * zeta * a.f.inv2sz2;
+            // below -104 a factor's exp (< 7e-46) rounds to zero in FP32: the
+            // term is dropped
+            if (er >= -104.0f && ez2 >= -104.0f) {
+                const float ga = expf(er) * expf(ez2);
+                const float w = dt * ez * ga;
+                g3[0] = w;
+                g3[1] = w * a.csr * r2;
+                g3[2] = w * a.csz * (zeta * zeta);
+            }
         }
     }
+    // most warps lie where the driver density is zero: no sums to form
+    if (!__any_sync(0xffffffffu, g3[0] != 0.0f || g3[1] != 0.0f || g3[2] != 0.0f)) return;
     for (int c3 = 0; c3 < 3; ++c3)
         for (int off = 16; off > 0; off >>= 1) g3[c3] += __shfl_down_sync(0xffffffffu, g3[c3], off);
     const int t = threadIdx.y * kBX + threadIdx.x;
@@ -625,10 +632,57 @@ __global__ void __launch_bounds__(kBX * kBY) adj_edges_kernel(const AdjArgs a) {
 // -y neighbour's from shared memory (one barrier per plane, two buffers) and
 // the -z one from the thread's registers. Nothing reads Bn_bar after R4, so
 // it is not written back: 72 B per node against the separate kernels' 96.
+// The plane above's b_bar_x, b_bar_y and e_bar_z that a plane reads are the
+// next plane's own values (kept in registers), and each iteration issues the
+// next plane's loads before it works on its own.
 constexpr int kRX = 32, kRY = 8, kRZ = 16;
+#ifndef PWFA_ADJ_FE_MIN_BLOCKS
+#define PWFA_ADJ_FE_MIN_BLOCKS 4
+#endif
+
+// The loads of one plane of a column (o its index; pi, pj, pk its +1
+// neighbour offsets): R3's b_bar_x, b_bar_y one plane up, b_bar_z and Bn_bar
+// of the plane; R4's node-averaged E_bar (e_bar_z one plane up) and E_bar,
+// for an owned node of the slab (e_bar_z one plane up for any owned node: the
+// next plane takes it as its own).
+struct AdjFEPlane {
+    float x2, x3, y2, y3, z0, z1, z2, z3, bn0, bn1, bn2, ex0, ex1, ey0, ey1, ez1, E0, E1, E2;
+};
+
+__device__ __forceinline__ void adj_fe_load(const AdjArgs& a, int o, int pi, int pj, int pk, bool own, bool slab,
+                                            AdjFEPlane& v) {
+#ifdef PWFA_DEBUG
+    o = (int)PWFA_CHECK(a.f.dbg, o, 0, a.f.g.N, 7u);
+    pk = (int)PWFA_CHECK(a.f.dbg, o + pi + pj + pk, 0, a.f.g.N, 7u) - o - pi - pj;
+#endif
+    const float *bx = a.bbar[0], *by = a.bbar[1], *bz = a.bbar[2];
+    v.x2 = __ldg(bx + o + pk);
+    v.x3 = __ldg(bx + o + pj + pk);
+    v.y2 = __ldg(by + o + pk);
+    v.y3 = __ldg(by + o + pi + pk);
+    v.z0 = __ldg(bz + o);
+    v.z1 = __ldg(bz + o + pi);
+    v.z2 = __ldg(bz + o + pj);
+    v.z3 = __ldg(bz + o + pi + pj);
+    v.bn0 = __ldg(a.Bnp[0] + o);
+    v.bn1 = __ldg(a.Bnp[1] + o);
+    v.bn2 = __ldg(a.Bnp[2] + o);
+    v.ez1 = own ? __ldg(a.ebar[2] + o + pk) : 0.0f;
+    if (slab) {
+        v.ex0 = __ldg(a.ebar[0] + o);
+        v.ex1 = __ldg(a.ebar[0] + o + pi);
+        v.ey0 = __ldg(a.ebar[1] + o);
+        v.ey1 = __ldg(a.ebar[1] + o + pj);
+        v.E0 = a.Ebar[0][o];
+        v.E1 = a.Ebar[1][o];
+        v.E2 = a.Ebar[2][o];
+    } else {
+        v.ex0 = v.ex1 = v.ey0 = v.ey1 = v.E0 = v.E1 = v.E2 = 0.0f;
+    }
+}
 
 template <bool PER>
-__global__ void __launch_bounds__(kRX * kRY, 4) adj_faces_edges_kernel(const AdjArgs a) {
+__global__ void __launch_bounds__(kRX * kRY, PWFA_ADJ_FE_MIN_BLOCKS) adj_faces_edges_kernel(const AdjArgs a) {
     const Grid& g = a.f.g;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = nx * ny;
     __shared__ float sBx[2][kRY][kRX], sBz[2][kRY][kRX];
@@ -645,52 +699,54 @@ __global__ void __launch_bounds__(kRX * kRY, 4) adj_faces_edges_kernel(const Adj
     const int pi = xe + 1 < nx ? 1 : (PER ? 1 - nx : 0);
     const int pj = ye + 1 < ny ? nx : (PER ? nx - nxy : 0);
     const float c = a.f.cdt;
-    const float *bx = a.bbar[0], *by = a.bbar[1], *bz = a.bbar[2];
+    // the +z offset of plane kk (wrapped on a periodic grid, clamped on an
+    // open one)
+    auto zoff = [&](int kk) { return kk + 1 < nz ? nxy : (PER ? nxy - nz * nxy : 0); };
 
     const int kz0 = (int)blockIdx.z * kRZ, kend = min(kz0 + kRZ, nz);
     const int kfirst = PER || kz0 > 0 ? kz0 - 1 : kz0;
+    int kk = kfirst < 0 ? kfirst + nz : kfirst;
+    int o = (kk * ny + ye) * nx + xe;
+    int pk = zoff(kk);
+    // the first plane: b_bar_x, b_bar_y at the plane and e_bar_z (its
+    // neighbours one plane up come with the plane's loads)
+    float x0, x1, y0, y1, ez0;
+    {
+        int oc = o;
+#ifdef PWFA_DEBUG
+        oc = (int)PWFA_CHECK(a.f.dbg, oc + pi + pj, 0, g.N, 7u) - pi - pj;
+#endif
+        x0 = __ldg(a.bbar[0] + oc);
+        x1 = __ldg(a.bbar[0] + oc + pj);
+        y0 = __ldg(a.bbar[1] + oc);
+        y1 = __ldg(a.bbar[1] + oc + pi);
+        ez0 = own && kfirst >= kz0 ? __ldg(a.ebar[2] + oc) : 0.0f;
+    }
+    AdjFEPlane nxt;
+    adj_fe_load(a, o, pi, pj, pk, own, own && kfirst >= kz0, nxt);
     float pbx = 0.0f, pby = 0.0f;  // new Bn_bar (x, y) of the plane below
     for (int k = kfirst; k < kend; ++k) {
-        const int kk = k < 0 ? k + nz : k;
         const int buf = (k - kfirst) & 1;
-        int o = (kk * ny + ye) * nx + xe;
-#ifdef PWFA_DEBUG
-        o = (int)PWFA_CHECK(a.f.dbg, o, 0, g.N, 7u);
-#endif
-        const bool kp = PER || kk + 1 < nz, km = PER || kk > 0;
-        const int pk = kk + 1 < nz ? nxy : (PER ? nxy - nz * nxy : 0);
-        // R3 at (xe, ye, kk)
-        const float x0 = bx[o], x1 = bx[o + pj], x2 = bx[o + pk], x3 = bx[o + pj + pk];
-        const float y0 = by[o], y1 = by[o + pi], y2 = by[o + pk], y3 = by[o + pi + pk];
-        const float z0 = bz[o], z1 = bz[o + pi], z2 = bz[o + pj], z3 = bz[o + pi + pj];
-        const float bn0 = a.Bnp[0][o], bn1 = a.Bnp[1][o], bn2 = a.Bnp[2][o];
-        // R4's loads, issued with R3's (owned nodes of the slab only)
+        const AdjFEPlane v = nxt;
         const bool slab = own && k >= kz0;
-        float ex0 = 0.0f, ex1 = 0.0f, ey0 = 0.0f, ey1 = 0.0f, ez0 = 0.0f, ez1 = 0.0f, E0 = 0.0f, E1 = 0.0f, E2 = 0.0f;
-        if (slab) {
-            const float* ex = a.ebar[0];
-            const float* ey = a.ebar[1];
-            const float* ez = a.ebar[2];
-            ex0 = ex[o];
-            ex1 = ex[o + pi];
-            ey0 = ey[o];
-            ey1 = ey[o + pj];
-            ez0 = ez[o];
-            ez1 = ez[o + pk];
-            E0 = a.Ebar[0][o];
-            E1 = a.Ebar[1][o];
-            E2 = a.Ebar[2][o];
-        }
-        const float s3[3] = {r3_sum(x0, x1, x2, x3, jp, kp, jp && kp), r3_sum(y0, y1, y2, y3, ip, kp, ip && kp),
-                             r3_sum(z0, z1, z2, z3, ip, jp, ip && jp)};
-        const float bn[3] = {bn0, bn1, bn2};
+        const bool kp = PER || kk + 1 < nz, km = PER || kk > 0;
+        // the next plane's loads, in flight while this one is worked on
+        const int kn = PER && kk + 1 >= nz ? kk + 1 - nz : kk + 1;
+        const int on = o + (kn > kk ? nxy : -kk * nxy);
+        const int pkn = zoff(kn);
+        if (k + 1 < kend) adj_fe_load(a, on, pi, pj, pkn, own, own && k + 1 >= kz0, nxt);
+        // R3 at (xe, ye, kk)
+        const float s3[3] = {r3_sum(x0, x1, v.x2, v.x3, jp, kp, jp && kp),
+                             r3_sum(y0, y1, v.y2, v.y3, ip, kp, ip && kp),
+                             r3_sum(v.z0, v.z1, v.z2, v.z3, ip, jp, ip && jp)};
+        const float bn[3] = {v.bn0, v.bn1, v.bn2};
         float bnew[3];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            const bool on = PER || act_B(g, cc, xe, ye, kk);
+            const bool on_c = PER || act_B(g, cc, xe, ye, kk);
             const float bnt = bn[cc] + s3[cc];
-            bnew[cc] = on ? bnt : 0.0f;
-            if (slab) a.Bbar[cc][o] = on ? bnt + s3[cc] : 0.0f;
+            bnew[cc] = on_c ? bnt : 0.0f;
+            if (slab) a.Bbar[cc][o] = on_c ? bnt + s3[cc] : 0.0f;
         }
         // R4 at (x, y, kk): the -x neighbour's Bn_bar from lane - 1, the -y
         // neighbour's from row - 1, the -z one from the plane below
@@ -703,17 +759,26 @@ __global__ void __launch_bounds__(kRX * kRY, 4) adj_faces_edges_kernel(const Adj
             const float bx_j = msk(jm, sBx[buf][ty - 1][tx]), bz_j = msk(jm, sBz[buf][ty - 1][tx]);
             const float bx_k = msk(km, pbx), by_k = msk(km, pby);
             const float bz_im = msk(im, bz_i), by_im = msk(im, by_i);
-            const float e0 = ex0 + msk(ip, ex1), e1 = ey0 + msk(jp, ey1), e2 = ez0 + msk(kp, ez1);
+            const float e0 = v.ex0 + msk(ip, v.ex1), e1 = v.ey0 + msk(jp, v.ey1), e2 = ez0 + msk(kp, v.ez1);
             const float bxn = bnew[0], byn = bnew[1], bzn = bnew[2];
             const bool a0 = PER || act_E(g, 0, x, y, kk);
             const bool a1 = PER || act_E(g, 1, x, y, kk);
             const bool a2 = PER || act_E(g, 2, x, y, kk);
-            a.Ebar[0][o] = a0 ? r4_arith(c, E0, e0, byn - by_k - bzn + bz_j) : 0.0f;
-            a.Ebar[1][o] = a1 ? r4_arith(c, E1, e1, -bxn + bx_k + bzn - bz_im) : 0.0f;
-            a.Ebar[2][o] = a2 ? r4_arith(c, E2, e2, bxn - bx_j - byn + by_im) : 0.0f;
+            a.Ebar[0][o] = a0 ? r4_arith(c, v.E0, e0, byn - by_k - bzn + bz_j) : 0.0f;
+            a.Ebar[1][o] = a1 ? r4_arith(c, v.E1, e1, -bxn + bx_k + bzn - bz_im) : 0.0f;
+            a.Ebar[2][o] = a2 ? r4_arith(c, v.E2, e2, bxn - bx_j - byn + by_im) : 0.0f;
         }
         pbx = bnew[0];
         pby = bnew[1];
+        // this plane's values one plane up are the next plane's own
+        x0 = v.x2;
+        x1 = v.x3;
+        y0 = v.y2;
+        y1 = v.y3;
+        ez0 = v.ez1;
+        kk = kn;
+        o = on;
+        pk = pkn;
     }
 }
 
