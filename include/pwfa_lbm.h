@@ -347,7 +347,10 @@ int pwfa_lbm_set_batching(pwfa_lbm_t* h, int32_t enable);
 #define PWFA_FUSION_ON 2
 int pwfa_lbm_set_field_fusion(pwfa_lbm_t* h, int32_t mode);
 
-/* Re-target all later work of the handle to another cudaStream_t. */
+/* Re-target all later work of the handle to another cudaStream_t (NULL:
+ * the legacy default stream). The new stream waits for the work already
+ * queued on the old one (an event, no host wait), so the switch may come
+ * while kernels are in flight. */
 int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream);
 
 /* FP64 diagnostics of a state the caller holds in device memory, computed

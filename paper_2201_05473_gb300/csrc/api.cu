@@ -1617,7 +1617,18 @@ int pwfa_lbm_set_batching(pwfa_lbm_t* h, int32_t enable) {
 
 int pwfa_lbm_set_stream(pwfa_lbm_t* h, void* cuda_stream) {
     if (!h) return fail(PWFA_ERR_PARAM, "null handle");
-    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaStream_t next = static_cast<cudaStream_t>(cuda_stream);
+    if (next != h->stream) {
+        // the new stream's work follows everything already queued on the old
+        // one (no host wait)
+        cudaEvent_t done;
+        PWFA_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming), "cudaEventCreate");
+        cudaError_t e = cudaEventRecord(done, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(next, done, 0);
+        cudaEventDestroy(done);
+        if (e != cudaSuccess) return cuda_fail(e, "stream switch");
+    }
+    h->stream = next;
     return PWFA_OK;
 }
 

@@ -335,6 +335,12 @@ class Simulation:
 
     DIRECT, STAGED = 0, 1
 
+    def set_stream(self, stream):
+        """Queue all later work on another torch.cuda.Stream (ordered after
+        the work already queued on the current one)."""
+        _check(self._lib.pwfa_lbm_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+        self.stream = stream
+
     def set_fluid_variant(self, variant: int, instance: int = 0):
         _check(self._lib.pwfa_lbm_set_fluid_variant(self._h, instance, int(variant)))
 
