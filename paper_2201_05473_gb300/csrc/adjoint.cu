@@ -513,17 +513,42 @@ __global__ void __launch_bounds__(kAdjThreads, PWFA_ADJ_MIN_BLOCKS) adj_fluid_ke
     }
     // transposed pull: f_i(x) = S_i(x - xi_i)  =>  S_bar_i(x - xi_i) = f_bar_i(x)
     const float mk[3] = {k3 * P[0], k3 * P[1], k3 * P[2]};
-#pragma unroll
-    for (int q = 0; q < kQ; ++q) {
-        uint32_t src;
-        if (PER) src = (uint32_t)src_index<true>(g, xs, ys, zs, q);
-        else src = nodec - (uint32_t)(xi_x(q) + xi_y(q) * g.nx) - (uint32_t)xi_z(q) * sxy;
-        src = PWFA_CHECK(s.dbg, src, 0, g.Np, 7u);
+    auto fbar = [&](int q) {
         float fb = Ab;
         if (COLL == 0) fb += (1.0f - om) * S[q];
         else if (COLL == 2) fb += S[q];
         else fb += (float)xi_x(q) * mk[0] + (float)xi_y(q) * mk[1] + (float)xi_z(q) * mk[2];
-        Sout[pop_off(q, src)] = fb;
+        return fb;
+    };
+    if (!PER && (g.nx & 31) == 0) {
+        // nx a multiple of 32: x - xi_i lies xi_y nx + xi_z nx ny nodes (a
+        // whole number of 32-node chunks) from x - xi_x, and x -+ 1 crosses
+        // into the neighbouring chunk only at its first / last lane; so each
+        // slot is one of three per-node bases plus a per-direction shift
+        constexpr uint32_t kC = kQ * 32u;  // elements of one chunk
+        const uint32_t cy = (uint32_t)(g.nx >> 5) * kC, cz = (sxy >> 5) * kC;
+        const uint32_t l0 = nodec & 31u;
+        const uint32_t b0 = (nodec >> 5) * kC + l0;
+        const uint32_t bsrc_p = l0 == 31u ? b0 + kC - 31u : b0 + 1u;  // xi_x = -1: the source is x + 1
+        const uint32_t bsrc_m = l0 == 0u ? b0 - kC + 31u : b0 - 1u;   // xi_x = +1: the source is x - 1
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const uint32_t base = xi_x(q) > 0 ? bsrc_m : (xi_x(q) < 0 ? bsrc_p : b0);
+            uint32_t off = base + (uint32_t)q * 32u;
+            if (xi_y(q) > 0) off -= cy; else if (xi_y(q) < 0) off += cy;
+            if (xi_z(q) > 0) off -= cz; else if (xi_z(q) < 0) off += cz;
+            off = PWFA_CHECK(s.dbg, off, 0, (long long)kQ * g.Np, 7u);
+            Sout[off] = fbar(q);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            uint32_t src;
+            if (PER) src = (uint32_t)src_index<true>(g, xs, ys, zs, q);
+            else src = nodec - (uint32_t)(xi_x(q) + xi_y(q) * g.nx) - (uint32_t)xi_z(q) * sxy;
+            src = PWFA_CHECK(s.dbg, src, 0, g.Np, 7u);
+            Sout[pop_off(q, src)] = fbar(q);
+        }
     }
 }
 
