@@ -86,3 +86,31 @@ def test_production_workload_2000_steps():
         _, E, B = sim.get_state()
         energy = 0.5 * float(E.double().pow(2).sum() + B.double().pow(2).sum()) * w.dx ** 3
         assert energy == pytest.approx(d[4], rel=1e-9)
+
+
+def test_production_workload_16bit_storage_2000_steps():
+    """The production workload's 2000 steps with populations stored as BF16
+    and FP16 deviations: every moment finite and n > 0 throughout (checked by
+    the fused diagnostics every 100 steps), the bubble present at the end,
+    and the relative L2 distance to the FP32 run at step 2000 recorded. In
+    this non-linear regime no accuracy bar is stated for the 16-bit forms
+    (the precision bar belongs to the 256x128x128 linear-driver form); the
+    asserted bounds are regression guards at about three times the measured
+    distances (GB300: FP16 n 1.3e-4, beta_z 3.4e-3, E_z 3.2e-3; BF16 n
+    1.7e-3, beta_z 3.1e-2, E_z 2.6e-2), and FP16 must stay closer than
+    BF16."""
+    mask = lbm.FIELD_N | lbm.FIELD_UZ | lbm.FIELD_EZ | lbm.RAW_YEE
+    runs = {}
+    for st in (W.F32, W.F16, W.BF16):
+        with lbm.Simulation(W.production().replace(storage=st)) as sim:
+            for _ in range(20):
+                d = sim.step_diag(100)[0]  # raises on a non-finite moment or n < 0
+                assert d[7] == 0 and d[5] > 0, (st, d)
+            assert 0 < sim.diag()[5] < 0.5
+            runs[st] = sim.fields(mask).double()
+    dist = {}
+    for st in (W.F16, W.BF16):
+        dist[st] = [float((runs[st][c] - runs[W.F32][c]).norm() / runs[W.F32][c].norm()) for c in range(3)]
+    print("16-bit storage vs FP32 after 2000 production steps (n, beta_z, E_z):", dist)
+    assert all(a < b for a, b in zip(dist[W.F16], dist[W.BF16]))
+    assert max(dist[W.F16]) < 1e-2 and max(dist[W.BF16]) < 1e-1, dist
