@@ -87,6 +87,18 @@ def test_adjoint_open_with_profile(collision):
     run_case(w, 40, 6, random_seed(w, rng))
 
 
+def test_adjoint_with_vacuum_region():
+    """The adjoint through the density floor: a plasma column in vacuum (the
+    profile falls to zero inside the box), so the reverse step takes the
+    derivative of the floored branch p = A / n_floor at the thin and empty
+    nodes; the profile gradient includes the points that are zero."""
+    prof = np.array([1.0, 1.0, 0.7, 0.3, 0.0, 0.0, 0.0, 0.0])
+    w = W.parity_small().replace(nx=16, ny=16, nz=24, alpha=0.5, sigma_r=0.5, sigma_z=0.5, z0=-1.0, tau=0.6,
+                                 profile=prof, profile_rmax=1.6)
+    rng = np.random.default_rng(13)
+    run_case(w, 40, 7, random_seed(w, rng))
+
+
 def test_adjoint_witness_loss_config_copy():
     """Differentiable form on its 64x32x32 copy: n_b/n0 = 0.5, 500 steps,
     checkpoints every 23 steps, loss -mean E_z on the witness slab 1.5

@@ -170,6 +170,30 @@ def test_radial_profile_parity():
         compare(o, sim)
 
 
+@pytest.mark.parametrize("collision", [W.BGK, W.REGULARIZED])
+def test_vacuum_region_density_floor(collision):
+    """A plasma column in vacuum: the profile falls to zero at r = 2.6, so
+    the outer nodes start at n = 0; in the first steps the edge of the column
+    overshoots to small negative densities and thin plasma below n_floor
+    (every one of them on the p = A / max(n, n_floor) branch) before the
+    column's diffusion (tau = 0.8) fills the box. Against the oracle at step
+    10, while the floored branch is taken, and at step 100."""
+    prof = np.array([1.0, 1.0, 1.0, 0.8, 0.5, 0.2, 0.0, 0.0])
+    w = W.parity_small().replace(profile=prof, profile_rmax=3.0, collision=collision, alpha=0.5, tau=0.8)
+    o = make_oracle(w)
+    with lbm.Simulation(w) as sim:
+        n0 = gpu_moments(sim)["n"]
+        assert n0.min() == 0.0 and rel(n0, o.moments()["n"]) < 1e-6
+        o.step(10)
+        sim.step(10)
+        no = o.moments()["n"]
+        assert (no < w.n_floor).sum() > 1000  # the floored branch is taken
+        compare(o, sim)
+        o.step(90)
+        sim.step(90)
+        compare(o, sim)
+
+
 def test_minimum_grid_and_zero_steps():
     w = W.parity_small().replace(nx=3, ny=3, nz=3, alpha=0.5, z0=0.0)
     o = make_oracle(w)

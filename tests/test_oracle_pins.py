@@ -253,6 +253,34 @@ def test_ade_translation_at_beta(oracle_mod):
     assert np.allclose(m["A"][2] / m["n"], p0, rtol=1e-12)
 
 
+def test_density_floor_sets_the_advecting_velocity(oracle_mod):
+    """Plasma thinner than n_floor (the reading p = A / max(n, n_floor)):
+    n = 1e-8 uniform with n p_z = 0.8e-6 uniform, so p = 0.8 through the
+    floor (the unfloored momentum would be 80). A small bump carried by the
+    n p_x lattice (p_x <= 1e-4) then translates at u = beta(0.8) dt/dx lattice
+    units per step to O(p_x^2): a floor that is not applied gives
+    beta(80) = 0.99992 instead of 0.62."""
+    nz = 96
+    nfl = 1e-6
+    o = make(oracle_mod, 3, 3, nz, boundary=oracle_mod.BND_PERIODIC, couple=0, tau=0.6, n_floor=nfl)
+    z = np.arange(nz) - 30.0
+    bump = 1e-10 * np.exp(-z ** 2 / (2 * 4.0 ** 2))
+    A = np.zeros((4, nz, 3, 3))
+    A[0] = 1e-8
+    A[1] = bump[:, None, None]
+    A[3] = 0.8 * nfl
+    o.set_equilibrium(A)
+    u = 0.8 / math.sqrt(1 + 0.8 * 0.8) * o.params["dt"] / o.params["dx"]
+    c0 = (z * bump).sum() / bump.sum()
+    steps = 80
+    o.step(steps)
+    m = o.moments()
+    a1 = m["A"][0].sum(axis=(1, 2))  # the n p_x lattice
+    c1 = (z * a1).sum() / a1.sum()
+    assert abs((c1 - c0) - steps * u) < 1e-6, (c1 - c0, steps * u)
+    assert abs(a1.sum() - 9 * bump.sum()) <= 1e-12 * 9 * bump.sum()
+
+
 # ------------------------------------------------------------ Eq. 5 (Yee)
 @pytest.mark.parametrize("ecomp,axis", [(0, 2), (0, 1), (1, 0), (1, 2), (2, 0), (2, 1)])
 def test_yee_vacuum_standing_wave(oracle_mod, ecomp, axis):
