@@ -57,6 +57,35 @@ def test_window_parity_with_oracle(collision):
     assert max(errs.values()) <= 1e-5, errs
 
 
+def test_window_with_16bit_storage():
+    """The moving window with populations stored as FP16 / BF16 deviations:
+    the plane of fresh plasma that enters at the top of the box must decode
+    to the plasma at rest (deviation zero). 200 steps, 20 moves, against the
+    oracle: FP16 within the reduced-precision bar 1e-3 on n, beta and E_z;
+    BF16 recorded and guarded at about three times its GB300 level (BF16
+    misses the bar; see the precision tests). GB300: FP16 n 3.3e-6, beta
+    1.5e-4, E_z 2.4e-5; BF16 n 1.4e-5, beta 1.2e-3, E_z 2.3e-4."""
+    steps = 200
+    base = window_case(W.BGK)
+    o = oracle.Oracle(base.nx, base.ny, base.nz, base.dx, base.dt, base.tau, collision=base.collision,
+                      alpha=base.alpha, sigma_r=base.sigma_r, sigma_z=base.sigma_z, z0=base.z0, moving_window=1,
+                      window_z=base.window_z)
+    o.step(steps)
+    om = o.moments()
+    E, _ = o.get_fields()
+    m = lbm.FIELD_N | lbm.FIELD_UX | lbm.FIELD_UY | lbm.FIELD_UZ | lbm.FIELD_EZ | lbm.RAW_YEE
+    errs = {}
+    for st in (W.F16, W.BF16):
+        with lbm.Simulation(base.replace(storage=st)) as sim:
+            sim.step(steps)
+            assert sim.window_planes() == 20
+            g = sim.fields(m).cpu().numpy().astype(np.float64)
+        errs[st] = {"n": rel(g[0], om["n"]), "beta": rel(g[1:4], om["beta"]), "Ez": rel(g[4], E[2])}
+    print("window, 16-bit storage vs oracle:", errs)
+    assert max(errs[W.F16].values()) <= 1e-3, errs
+    assert max(errs[W.BF16].values()) <= 4e-3, errs
+
+
 def test_window_move_is_exact_on_integer_populations():
     """Stream-only lattices, no fields, a window move on the first step: the
     state after it is F_i(x + z_hat - xi_i) for the state F set before it,
