@@ -54,7 +54,9 @@ extern "C" {
 #define PWFA_ERR_UNSTABLE (-3) /* diagnostics found a non-finite value or n < 0 */
 #define PWFA_ERR_TIMEOUT (-4)  /* a bounded device-side wait expired (reserved: no kernel of this
                                   library waits on another, so no call returns it at present) */
-#define PWFA_ERR_ALLOC (-5)    /* device memory allocation failed */
+#define PWFA_ERR_ALLOC (-5)    /* device memory allocation failed: the device had no room (a
+                                  cudaMalloc the runtime refuses for another reason, e.g.
+                                  inside the caller's stream capture, returns PWFA_ERR_CUDA) */
 #define PWFA_ERR_STATE (-6)    /* call not valid in the handle's current state */
 
 /* Collision operator of every lattice. */

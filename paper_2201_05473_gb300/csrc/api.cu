@@ -111,15 +111,28 @@ int set_error(int code, const std::string& msg) { return fail(code, msg); }
 namespace {
 std::atomic<long> g_alloc_count{0};
 }
+namespace {
+thread_local cudaError_t t_alloc_error = cudaSuccess;  // of the calling thread's last dev_alloc
+}
 cudaError_t dev_alloc(void** p, size_t bytes) {
     const long k = ++g_alloc_count;
     if (const char* v = std::getenv("PWFA_FAIL_ALLOC_AT")) {
         if (std::atol(v) == k) {
             *p = nullptr;
-            return cudaErrorMemoryAllocation;
+            return t_alloc_error = cudaErrorMemoryAllocation;
         }
     }
-    return cudaMalloc(p, bytes);
+    return t_alloc_error = cudaMalloc(p, bytes);
+}
+// The status of a failed dev_alloc: PWFA_ERR_ALLOC when the device had no
+// room, PWFA_ERR_CUDA when the runtime refused the call for another reason
+// (for instance while the caller captures the stream into a graph); the
+// message names the CUDA error. Clears the runtime's last error.
+int alloc_fail(const std::string& what) {
+    const cudaError_t e = t_alloc_error;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? PWFA_ERR_ALLOC : PWFA_ERR_CUDA,
+                what + " (" + cudaGetErrorString(e) + ")");
 }
 }  // namespace pwfa
 
@@ -269,7 +282,7 @@ int ensure_staging(pwfa_lbm* h, size_t bytes) {
     h->staging_bytes = 0;
     if (dev_alloc((void**)&h->staging, bytes) != cudaSuccess) {
         cudaGetLastError();
-        return fail(PWFA_ERR_ALLOC, "cudaMalloc of the staging buffer failed");
+        return alloc_fail("cudaMalloc of the staging buffer failed");
     }
     h->staging_bytes = bytes;
     return PWFA_OK;
@@ -332,7 +345,7 @@ int alloc_instance(Instance& in, cudaStream_t s) {
         in.arena = nullptr;
         char buf[160];
         std::snprintf(buf, sizeof buf, "cudaMalloc of %.3f GB for one instance failed", total / 1e9);
-        return fail(PWFA_ERR_ALLOC, buf);
+        return alloc_fail(buf);
     }
     char* base = static_cast<char*>(in.arena);
     in.f[0] = base; base += fbytes;
@@ -357,7 +370,7 @@ int alloc_instance(Instance& in, cudaStream_t s) {
                                0x7fffffff, 0x7fffffff, 0x7fffffff, -1, -1, -1};
         if (dev_alloc((void**)&in.jbox, sizeof empty) != cudaSuccess) {
             cudaGetLastError();
-            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the deposit boxes failed");
+            return alloc_fail("cudaMalloc of the deposit boxes failed");
         }
         PWFA_CUDA(cudaMemcpy(in.jbox, empty, sizeof empty, cudaMemcpyHostToDevice), "cudaMemcpy");
     }
@@ -509,7 +522,7 @@ int batch_build(pwfa_lbm* h) {
         if (dev_alloc((void**)&h->d_entries, sizeof(BatchEntry) * n) != cudaSuccess ||
             dev_alloc((void**)&h->d_steps, sizeof(int64_t) * 2 * n) != cudaSuccess) {
             cudaGetLastError();
-            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the batch table failed");
+            return alloc_fail("cudaMalloc of the batch table failed");
         }
         h->entries_cap = n;
     }
@@ -519,7 +532,7 @@ int batch_build(pwfa_lbm* h) {
         h->tile_inst_cap = 0;
         if (dev_alloc((void**)&h->d_tile_inst, sizeof(uint16_t) * (ntiles + nftiles)) != cudaSuccess) {
             cudaGetLastError();
-            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the batch tile map failed");
+            return alloc_fail("cudaMalloc of the batch tile map failed");
         }
         h->tile_inst_cap = ntiles + nftiles;
     }
@@ -924,7 +937,7 @@ int record_instance(pwfa_lbm* h, Instance& in, int32_t nsteps, int32_t ckpt_ever
         std::snprintf(buf, sizeof buf, "recording needs %.2f GB (%d checkpoints + a segment of %d steps)",
                       (r.cp_stride * (r.ncp + 1) + seg_bytes + adj_bytes) / 1e9, r.ncp + 1, r.K);
         free_recording(in);
-        return fail(PWFA_ERR_ALLOC, buf);
+        return alloc_fail(buf);
     }
     // the guards in front of the segment's field slots stay zero
     PWFA_CUDA(cudaMemsetAsync(r.seg, 0, seg_bytes, s), "cudaMemsetAsync");
@@ -1102,7 +1115,7 @@ int ensure_step_diag(pwfa_lbm* h) {
         if (dev_alloc((void**)&h->d_step_diag, sizeof(double) * 8 * h->inst.size()) != cudaSuccess ||
             dev_alloc((void**)&h->d_step_scratch, sizeof(double) * 8 * kDiagBlocks) != cudaSuccess) {
             cudaGetLastError();
-            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics results failed");
+            return alloc_fail("cudaMalloc of the diagnostics results failed");
         }
     }
     if (need > h->step_records_cap || need_e > h->step_energy_cap) {
@@ -1111,7 +1124,7 @@ int ensure_step_diag(pwfa_lbm* h) {
         h->step_records_cap = h->step_energy_cap = 0;
         if (dev_alloc((void**)&h->d_step_records, sizeof(float) * (8 * need + need_e)) != cudaSuccess) {
             cudaGetLastError();
-            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics records failed");
+            return alloc_fail("cudaMalloc of the diagnostics records failed");
         }
         h->step_records_cap = need;
         h->step_energy_cap = need_e;
@@ -1270,7 +1283,7 @@ int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances, void* cu
     if (rc == PWFA_OK) {
         if (dev_alloc((void**)&h->d_partials, sizeof(double) * 8 * (kDiagBlocks + 1)) != cudaSuccess) {
             cudaGetLastError();
-            rc = fail(PWFA_ERR_ALLOC, "cudaMalloc of the diagnostics buffer failed");
+            rc = alloc_fail("cudaMalloc of the diagnostics buffer failed");
         } else {
             h->d_diag = h->d_partials + 8 * kDiagBlocks;
         }
@@ -1461,7 +1474,7 @@ int pwfa_lbm_set_particles(pwfa_lbm_t* h, int32_t instance, int64_t n, const flo
     if (n > 0) {
         if (dev_alloc((void**)&in.particles, sizeof(float) * 6 * (size_t)n) != cudaSuccess) {
             cudaGetLastError();
-            return fail(PWFA_ERR_ALLOC, "cudaMalloc of the particle array failed");
+            return alloc_fail("cudaMalloc of the particle array failed");
         }
         PWFA_CUDA(cudaMemcpyAsync(in.particles, xp, sizeof(float) * 6 * (size_t)n, cudaMemcpyDefault, h->stream),
                   "particle copy");

@@ -14,6 +14,7 @@
 namespace pwfa {
 int set_error(int code, const std::string& msg);  // api.cu
 cudaError_t dev_alloc(void** p, size_t bytes);    // api.cu
+int alloc_fail(const std::string& what);           // api.cu
 }
 
 using pwfa::set_error;
@@ -170,7 +171,7 @@ int pwfa_axi_create(const pwfa_axi_params* params, void* cuda_stream, pwfa_axi_t
     if (pwfa::dev_alloc((void**)&h->arena, total) != cudaSuccess) {
         cudaGetLastError();
         delete h;
-        return set_error(PWFA_ERR_ALLOC, "cudaMalloc of the axisymmetric state failed");
+        return pwfa::alloc_fail("cudaMalloc of the axisymmetric state failed");
     }
     char* b = static_cast<char*>(h->arena);
     h->f[0] = (float*)b; b += fbytes;

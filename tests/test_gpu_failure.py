@@ -89,3 +89,64 @@ def test_allocation_failures_return_err_alloc_and_leak_nothing():
         # the handle is still usable
         assert r["step_after"] == 0 and r["record_again"] == 0 and r["destroy"] == 0, r
         assert abs(r["free_end"] - r["free0"]) <= SLACK, r
+
+
+CHILD_CUDA_ERROR = r"""
+import json, sys
+sys.path.insert(0, %(root)r)
+import torch
+from paper_2201_05473_gb300 import lbm, workloads as W
+lbm.load(build=False)
+w = W.parity_small().replace(nx=16, ny=16, nz=32)
+out = {}
+s = torch.cuda.Stream()
+with torch.cuda.stream(s):
+    sim = lbm.Simulation(w, stream=s)
+    sim.step(2)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    g.capture_begin()
+    try:
+        sim.step_diag(1)  # its host read synchronises the capturing stream
+        out["code"] = 0
+    except lbm.LBMError as e:
+        out["code"] = e.code
+        out["msg"] = str(e)
+    try:
+        g.capture_end()
+        out["capture_end"] = "ok"
+    except Exception as e:
+        out["capture_end"] = type(e).__name__
+    torch.cuda.synchronize()
+    sim.close()
+    # the process and the device carry on: a new handle steps and matches a
+    # handle that never saw the error
+    with lbm.Simulation(w, stream=s) as a:
+        a.step(5)
+        fa = a.fields(lbm.FIELD_N | lbm.FIELD_EZ | lbm.RAW_YEE)
+    with lbm.Simulation(w) as b:
+        b.step(5)
+        fb = b.fields(lbm.FIELD_N | lbm.FIELD_EZ | lbm.RAW_YEE)
+    out["after_equal"] = bool(torch.equal(fa, fb))
+print("RESULT " + json.dumps(out))
+"""
+
+
+def test_cuda_error_is_returned_not_raised_on_the_device():
+    """A CUDA runtime error made on the host, with no device fault: the
+    library's call is made while the caller captures its stream into a
+    graph, so the runtime refuses what the call needs (here the first
+    diagnostics call's cudaMalloc, which is not an out-of-memory). The call
+    returns PWFA_ERR_CUDA, not PWFA_ERR_ALLOC, with the CUDA error named;
+    after the caller ends the
+    (invalidated) capture, the process and the device carry on (a new handle
+    steps and equals one that never saw the error). Child process, like the
+    allocation failures."""
+    cp = subprocess.run([sys.executable, "-c", CHILD_CUDA_ERROR % {"root": ROOT}], capture_output=True, text=True,
+                        timeout=300)
+    assert cp.returncode == 0, cp.stderr[-3000:]
+    r = json.loads([l for l in cp.stdout.splitlines() if l.startswith("RESULT ")][-1][len("RESULT "):])
+    print(r)
+    assert r["code"] == -2, r  # PWFA_ERR_CUDA
+    assert "captur" in r["msg"].lower(), r  # the CUDA error string names the stream capture
+    assert r["after_equal"], r
