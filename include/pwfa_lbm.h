@@ -135,7 +135,13 @@ int pwfa_lbm_create(const pwfa_lbm_params* params, int32_t n_instances,
 
 /* Advance every instance by nsteps (>= 0) time steps: Faraday, fused
  * pull-stream + moments + Lorentz source + collision (Eqs. 6-10, 14), Ampere
- * with J = -n beta and the driver current. Asynchronous on the stream. */
+ * with J = -n beta and the driver current. Asynchronous on the stream. A
+ * caller that captures this call into a graph of its own records kernels
+ * whose arguments (buffer parity, driver time of a single instance) are
+ * fixed at capture, and the handle counts the steps once: replaying such a
+ * graph repeats those steps rather than continuing the run. For repeated
+ * steps use nsteps (the batched path replays its own graphs, whose driver
+ * time advances on the device). */
 int pwfa_lbm_step(pwfa_lbm_t* h, int32_t nsteps);
 
 /* Gradients by the discrete adjoint (the paper has no adjoint; this
