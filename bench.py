@@ -47,6 +47,13 @@ STEP_BYTES = {W.F32: 608 + 48, W.BF16: 304 + 48, W.F16: 304 + 48}
 # and the fields' adjoints read + written (48 B), plus the forward step
 # recomputed from the checkpoint (656 B).
 ADJOINT_BYTES = 984 + 656
+# What this build's reverse step moves per node instead: the recomputed
+# forward step (fluid with its lattice sums 672 B, fused field step 60 B),
+# transposed Ampere 48 B, transposed fluid step 696 B (the lattice sums in
+# place of the forward populations), fused transposed averages + Faraday
+# 72 B; without the recomputation (one-segment recording) the last three.
+ADJOINT_BYTES_MOVED = 672 + 60 + 48 + 696 + 72
+ADJOINT_BYTES_MOVED_NO_RECOMPUTE = 48 + 696 + 72
 # Untimed steps before the warm-up: the driver, started inside the box at
 # z0 = 4 sigma_z, forms the non-linear wake (min n ~0.4 after 300 steps).
 PRELUDE_STEPS = 300
@@ -543,7 +550,10 @@ def run_ours(args):
                 t_adj1 = time.perf_counter() - t0
                 k1, l1 = sim.kernel_times()
                 sim.close()
-                single = {"value": wa.nodes * Ta / t_adj1 / 1e9, "unit": "GLUPS", "ckpt_every": Ta,
+                g1s = wa.nodes * Ta / t_adj1 / 1e9
+                single = {"value": g1s, "unit": "GLUPS", "ckpt_every": Ta,
+                          "bytes_per_node_step_moved": ADJOINT_BYTES_MOVED_NO_RECOMPUTE,
+                          "pct_hbm_of_bytes_moved": g1s * ADJOINT_BYTES_MOVED_NO_RECOMPUTE / hbm_peak()[0],
                           "record_glups": wa.nodes * Ta / t_rec1 / 1e9,
                           "record_plus_adjoint_glups": wa.nodes * Ta / (t_rec1 + t_adj1) / 1e9,
                           "launches_per_reversed_step": {k: l1[k] / Ta for k in l1 if l1[k]},
@@ -559,6 +569,8 @@ def run_ours(args):
                                     "(NULL seed: the built-in witness loss); node-steps of the adjoint / time",
                             "bytes_per_node_step": ADJOINT_BYTES,
                             "pct_hbm": adj_glups * 1e9 * ADJOINT_BYTES / (hbm_peak()[0] * 1e9),
+                            "bytes_per_node_step_moved": ADJOINT_BYTES_MOVED,
+                            "pct_hbm_of_bytes_moved": adj_glups * ADJOINT_BYTES_MOVED / hbm_peak()[0],
                             "record_glups": wa.nodes * Ta / t_rec / 1e9,
                             "record_plus_adjoint_glups": wa.nodes * Ta / (t_rec + t_adj) / 1e9,
                             "grid_zyx": [wa.nz, wa.ny, wa.nx],
