@@ -60,11 +60,16 @@ PRELUDE_STEPS = 300
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fluid_kernel_traffic.json")
 KERNEL_SOURCES = ["paper_2201_05473_gb300/csrc/fluid.cu", "paper_2201_05473_gb300/csrc/fluid_node.cuh",
                   "paper_2201_05473_gb300/csrc/lbm_node.cuh", "paper_2201_05473_gb300/csrc/lbm_device.cuh"]
+# the fused field kernel (Ampere with the next step's Faraday): 60 B/node
+FIELD_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ampere_faraday_kernel_traffic.json")
+FIELD_SOURCES = ["paper_2201_05473_gb300/csrc/fields.cu", "paper_2201_05473_gb300/csrc/fields_fused.cuh",
+                 "paper_2201_05473_gb300/csrc/fields_node.cuh", "paper_2201_05473_gb300/csrc/lbm_device.cuh"]
+FIELD_BYTES = 60
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, p), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -83,16 +88,17 @@ def hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def ncu_traffic(nodes):
-    """DRAM bytes per fluid launch from the committed ncu capture, if it was
-    taken on the current kernel source; else None."""
-    if not os.path.exists(TRAFFIC_FILE):
+def ncu_traffic(nodes, path=TRAFFIC_FILE, sources=None):
+    """DRAM bytes per launch (the fluid kernel by default) from the committed
+    ncu capture, scaled to the launch's node count, if the capture was taken
+    on the current kernel source; else None."""
+    if not os.path.exists(path):
         return None
     try:
-        d = json.load(open(TRAFFIC_FILE))
+        d = json.load(open(path))
     except Exception:
         return None
-    if d.get("source_sha") != kernel_source_hash():
+    if d.get("source_sha") != kernel_source_hash(sources):
         return None
     return float(d["bytes_per_node"]) * nodes
 
@@ -659,6 +665,15 @@ def run_ours(args):
                      "bytes_per_node": FLUID_BYTES[w.storage], "avg_launch_ms": fluid_ms,
                      "step": {"bytes_per_node_step": step_bytes, "achieved": step_achieved,
                               "frac": step_achieved / peak, "ms": ms_max / args.steps}},
+        "roofline_fields": ({"bound": "hbm", "kernel": "ampere_faraday",
+                             "achieved": FIELD_BYTES * N / (kms["ampere"] / kl["ampere"] * 1e-3) / 1e9,
+                             "peak": peak, "unit": "GB/s",
+                             "frac": FIELD_BYTES * N / (kms["ampere"] / kl["ampere"] * 1e-3) / 1e9 / peak,
+                             "peak_kind": peak_kind,
+                             "traffic": ncu_traffic(N, FIELD_TRAFFIC_FILE, FIELD_SOURCES),
+                             "algorithmic_bytes_per_launch": FIELD_BYTES * N, "bytes_per_node": FIELD_BYTES,
+                             "avg_launch_ms": kms["ampere"] / kl["ampere"]}
+                            if kl.get("ampere") and kl.get("faraday", 0) == 0 else None),
         "kernel_ms_per_step": {k: kms[k] / max(kl[k], 1) for k in kms if kl[k]},
         "field_step": ("ampere fused with the next step's faraday (one launch)" if kl.get("faraday", 0) == 0
                        else "separate faraday and ampere launches"),
