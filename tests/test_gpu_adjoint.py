@@ -265,3 +265,38 @@ def test_adjoint_with_16bit_storage():
     assert np.all(np.isfinite(g[W.BF16])) and np.all(np.isfinite(g[W.F16]))
     assert err[W.F16] < err[W.BF16]
     assert err[W.F16] < 1e-5 and err[W.BF16] < 6e-5, err
+
+
+def test_adjoint_full_size_against_finite_differences():
+    """The differentiable form at its full size (256x128x128, n_b/n0 = 0.5,
+    500 steps, checkpoints every ceil(sqrt(500)) = 23, the built-in witness
+    loss, a 64-point profile): the adjoint's derivatives with respect to
+    (n_b/n0, sigma_r, sigma_z) and along a random profile direction against
+    central differences of the FP32 forward with h = 1e-3 (relative for the
+    driver parameters). FP32 forward noise ~ eps |L| / h makes this a check
+    to 1e-2."""
+    prof = np.ones(64)
+    w = W.differentiable().replace(profile=prof, profile_rmax=128 * 0.2 / 2)
+    steps = 500
+
+    def loss(**kw):
+        with lbm.Simulation(w.replace(**kw)) as sim:
+            sim.step(steps)
+            return sim.witness_loss()
+
+    with lbm.Simulation(w) as sim:
+        g = sim.adjoint_step(None, nsteps=steps)
+    rng = np.random.default_rng(21)
+    d = rng.standard_normal(64)
+    checks = []
+    for i, name in enumerate(("alpha", "sigma_r", "sigma_z")):
+        v = getattr(w, name)
+        h = 1e-3 * v
+        fd = (loss(**{name: v + h}) - loss(**{name: v - h})) / (2 * h)
+        checks.append((name, fd, g[i]))
+    h = 1e-3
+    fd = (loss(profile=prof + h * d) - loss(profile=prof - h * d)) / (2 * h)
+    checks.append(("profile", fd, float(d @ g[3:])))
+    print("full-size adjoint vs central differences:", checks)
+    for name, fd, ad in checks:
+        assert abs(fd - ad) <= 1e-2 * abs(ad), (name, fd, ad)

@@ -21,16 +21,17 @@ from paper_2201_05473_gb300 import lbm  # noqa: E402
 MASK = lbm.FIELD_N | lbm.FIELD_UZ | lbm.FIELD_EZ | lbm.FIELD_BY | lbm.RAW_YEE
 
 
-def close(fa, fb, i):
+def close(fa, fb, i, tol=1e-6):
     """The batched kernels inline the same per-node functions, but are
     compiled into different kernels, so FP32 contraction may round
-    differently: agreement to a few ulp per field, relative L2."""
+    differently: agreement to a few ulp per field, relative L2 (tol: 1e-6
+    over tens of steps; longer runs let the differences grow)."""
     for c in range(fa.shape[0]):
         a, b = fa[c].double(), fb[c].double()
         den = max(float(b.norm()), 1e-30)
         err = float((a - b).norm()) / den
         print("instance", i, "field", c, "rel diff", err, "max abs", float((a - b).abs().max()))
-        assert err <= 1e-6, (i, c, err)
+        assert err <= tol, (i, c, err)
 
 
 def scan(n, seed=0, scale=1):
@@ -167,3 +168,28 @@ def test_many_small_instances_batched():
             b.step(12)
             for i in (0, 1, 57, 199):
                 close(a.fields(MASK, instance=i), b.fields(MASK, instance=i), i)
+
+
+def test_config4_scan_full_size():
+    """The batched form on the 64-instance scan itself (grids 64x32x32 to
+    256x128x128, 94 M nodes, n_b/n0 in [0.05, 2]), 500 steps in the
+    benchmarked launch configuration: every instance stays finite with
+    n > 0, and the smallest, a middle and the largest instance equal the
+    same instance stepped alone (a single-instance handle), field by field:
+    over 500 non-linear steps the few-ulp differences of the two
+    compilations grow to ~1e-6 (GB300: at most 1.3e-6), held to the FP32
+    parity bar 1e-5."""
+    ws = W.batched_scan(64, seed=0)
+    order = sorted(range(len(ws)), key=lambda i: ws[i].nodes)
+    pick = [order[0], order[len(order) // 2], order[-1]]
+    with lbm.Simulation(ws) as sb:
+        sb.autotune(2)
+        sb.step(500)
+        for i in range(len(ws)):
+            d = sb.diag(i)
+            assert d[7] == 0 and d[5] > 0, (i, d)
+        got = {i: sb.fields(MASK, instance=i) for i in pick}
+    for i in pick:
+        with lbm.Simulation(ws[i]) as s1:
+            s1.step(500)
+            close(got[i], s1.fields(MASK), i, tol=1e-5)
