@@ -5,7 +5,6 @@ theta = (alpha, sigma_r, sigma_z, profile...); the oracle gives directional
 derivatives dL.v for a few directions v in FP64, independently of the
 reverse sweep. Bar: relative error <= 1e-4.
 """
-import math
 
 import numpy as np
 import pytest

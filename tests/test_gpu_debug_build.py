@@ -11,7 +11,6 @@ one-segment recording and with the separate transposed field kernels) in a
 child process: every call must succeed, and the states must equal those of
 the release build.
 """
-import json
 import os
 import subprocess
 import sys

@@ -5,7 +5,6 @@ Tolerance: FP32 compute and storage against FP64, relative L2 <= 1e-5 on n,
 beta and E_z after 200 steps of the 64x32x32 linear-driver case; the same
 bound elsewhere unless stated. Integer streaming is bit-exact.
 """
-import math
 
 import numpy as np
 import pytest

@@ -9,7 +9,6 @@ previous call's contents). This file is collected last on purpose.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 from paper_2201_05473_gb300 import workloads as W
