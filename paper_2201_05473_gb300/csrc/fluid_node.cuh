@@ -58,36 +58,50 @@ __device__ __forceinline__ void raw_moments(const float (&s)[kQ], float base, fl
     for (int c = 0; c < 3; ++c) m[c] = ka * ma[c] + kd * md[c];
 }
 
-// Everything after the gather: moments, source, collision, stores, current.
-// f holds the pulled populations f^n(x) (of the clamped node when bnd); with
-// RAW (16-bit storage, regularized collision) in stored units, and the
-// post-collision values are formed in stored units too, so that neither the
-// decode nor the encode of the deviations costs a per-value operation.
+// The moments a node's step needs from its pulled populations: the lattice
+// sums A_l, 1/max(n, n_floor), beta, and for the regularized collision the
+// first moments m_l = sum_i xi_i f_l,i (taken here so that the 76 pulled
+// values are dead before the fields are read; a boundary node recomputes
+// them from its equilibrium in fluid_rest).
+struct NodeMoments {
+    float A[kL], inn, beta[3], m[kL][3];
+};
+
+template <int ST, int COLL, bool RAW>
+__device__ __forceinline__ void fluid_moments(const StepArgs& a, const float (&f)[kL][kQ], NodeMoments& s) {
+    constexpr bool RAWR = RAW && ST != 0 && COLL == 1;
+    if constexpr (RAWR) {
+#pragma unroll
+        for (int l = 0; l < kL; ++l) raw_moments<ST>(f[l], l == 0 ? a.n0 : 0.0f, s.A[l], s.m[l]);
+        node_velocity(s.A, a.n_floor, s.inn, s.beta);
+    } else {
+        node_moments(f, a.n_floor, s.A, s.inn, s.beta);
+        if (COLL == 1) {
+#pragma unroll
+            for (int l = 0; l < kL; ++l) first_moments(f[l], s.m[l]);
+        }
+    }
+}
+
+// Everything after the moments: source, collision, stores, current. f holds
+// the pulled populations f^n(x) (of the clamped node when bnd; BGK and
+// stream-only read them, the regularized form only uses f as its output
+// scratch); with RAW (16-bit storage, regularized collision) in stored units,
+// and the post-collision values are formed in stored units too, so that
+// neither the decode nor the encode of the deviations costs a per-value
+// operation.
 template <int ST, int COLL, bool PER, bool DIAG = false, bool RAW = false, bool MOM = false>
-__device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, int z, float (&f)[kL][kQ], bool bnd,
-                                              NodeDiag* nd = nullptr) {
+__device__ __forceinline__ void fluid_rest(const StepArgs& a, int x, int y, int z, float (&f)[kL][kQ], bool bnd,
+                                           NodeMoments& s, NodeDiag* nd = nullptr) {
     using T = typename Codec<ST>::T;
     constexpr bool RAWR = RAW && ST != 0 && COLL == 1;
     const Grid& g = a.g;
     const uint32_t node =
         PWFA_CHECK(a.dbg, ((uint32_t)z * (uint32_t)g.ny + (uint32_t)y) * (uint32_t)g.nx + (uint32_t)x, 0, g.N, 2u);
-
-    float A[kL], inn, beta[3];
-    // Regularized: the first moments m_l = sum_i xi_i f_l,i, taken here so
-    // that the 76 pulled values are dead before the fields are read (a
-    // boundary node recomputes them from its equilibrium below).
-    float m[kL][3];
-    if constexpr (RAWR) {
-#pragma unroll
-        for (int l = 0; l < kL; ++l) raw_moments<ST>(f[l], l == 0 ? a.n0 : 0.0f, A[l], m[l]);
-        node_velocity(A, a.n_floor, inn, beta);
-    } else {
-        node_moments(f, a.n_floor, A, inn, beta);
-        if (COLL == 1) {
-#pragma unroll
-            for (int l = 0; l < kL; ++l) first_moments(f[l], m[l]);
-        }
-    }
+    float(&A)[kL] = s.A;
+    float& inn = s.inn;
+    float(&beta)[3] = s.beta;
+    float(&m)[kL][3] = s.m;
     const float n = A[0];
     if (MOM) {
         // the adjoint's recompute keeps the lattice sums (the reverse step
@@ -223,6 +237,15 @@ __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, i
     __stcs(a.J[0] + node, ngs * ps0);
     __stcs(a.J[1] + node, ngs * ps1);
     __stcs(a.J[2] + node, ngs * ps2);
+}
+
+// Everything after the gather: moments, then fluid_rest.
+template <int ST, int COLL, bool PER, bool DIAG = false, bool RAW = false, bool MOM = false>
+__device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, int z, float (&f)[kL][kQ], bool bnd,
+                                              NodeDiag* nd = nullptr) {
+    NodeMoments s;
+    fluid_moments<ST, COLL, RAW>(a, f, s);
+    fluid_rest<ST, COLL, PER, DIAG, RAW, MOM>(a, x, y, z, f, bnd, s, nd);
 }
 
 template <int ST, int COLL, bool PER, bool DIAG = false, bool MOM = false>
