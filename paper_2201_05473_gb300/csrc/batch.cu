@@ -51,7 +51,7 @@ __device__ __forceinline__ float driver_centre(const BatchEntry& e, int parity, 
 // Phases 0-2 on the fluid tiles: Faraday, the fluid step, Ampere. A block
 // takes kBatchGroup consecutive tiles of one instance.
 template <int ST, int COLL, bool PER, int PHASE>
-__global__ void __launch_bounds__(kBatchTile, PHASE == 1 ? FluidOcc<ST, COLL>::blocks : 8)
+__global__ void __launch_bounds__(kBatchTile, PHASE == 1 ? BatchFluidOcc<ST, COLL>::blocks : 8)
     batch_node_kernel(const BatchEntry* __restrict__ ent, const uint16_t* __restrict__ tile_inst, int parity) {
     __shared__ StepArgs sa;
     __shared__ float s_zc;
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kBatchTile, PHASE == 1 ? FluidOcc<ST, COLL>::b
         int x, y, z;
         if (!tile_node(sa.g, t, tid, x, y, z)) continue;
         if (PHASE == 0) faraday_node<PER>(sa, x, y, z);
-        else if (PHASE == 1) fluid_node<ST, COLL, PER>(sa, x, y, z);
+        else if (PHASE == 1) fluid_node<ST, COLL, PER, false, false, BatchFluidOcc<ST, COLL>::park>(sa, x, y, z);
         else ampere_node<PER>(sa, x, y, z, s_zc);
     }
 }

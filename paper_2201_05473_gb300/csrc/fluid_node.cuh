@@ -83,6 +83,20 @@ __device__ __forceinline__ void fluid_moments(const StepArgs& a, const float (&f
     }
 }
 
+// Shared-memory words of one thread's parked BGK values (lattices 2 and 3),
+// thread index fastest: a warp's 32 accesses of one value hit 32 banks. The
+// accesses are opaque to the compiler, so the parked registers are free
+// until the collision reads the words back.
+constexpr int kStashVals = 2 * kQ;
+__device__ __forceinline__ void stash_st(uint32_t a, float v) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v));
+}
+__device__ __forceinline__ float stash_ld(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+
 // Everything after the moments: source, collision, stores, current. f holds
 // the pulled populations f^n(x) (of the clamped node when bnd; BGK and
 // stream-only read them, the regularized form only uses f as its output
@@ -90,7 +104,7 @@ __device__ __forceinline__ void fluid_moments(const StepArgs& a, const float (&f
 // and the post-collision values are formed in stored units too, so that
 // neither the decode nor the encode of the deviations costs a per-value
 // operation.
-template <int ST, int COLL, bool PER, bool DIAG = false, bool RAW = false, bool MOM = false>
+template <int ST, int COLL, bool PER, bool DIAG = false, bool RAW = false, bool MOM = false, bool PARK = false>
 __device__ __forceinline__ void fluid_rest(const StepArgs& a, int x, int y, int z, float (&f)[kL][kQ], bool bnd,
                                            NodeMoments& s, NodeDiag* nd = nullptr) {
     using T = typename Codec<ST>::T;
@@ -103,6 +117,18 @@ __device__ __forceinline__ void fluid_rest(const StepArgs& a, int x, int y, int 
     float(&beta)[3] = s.beta;
     float(&m)[kL][3] = s.m;
     const float n = A[0];
+    // PARK (BGK): lattices 2 and 3 wait in shared memory while the fields are
+    // read and the source is formed (128 threads per block at most)
+    constexpr bool STASH = PARK && COLL == 0;
+    __shared__ float stash[STASH ? kStashVals : 1][PWFA_FLUID_MAX_THREADS];
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(&stash[0][threadIdx.y * blockDim.x + threadIdx.x]);
+    constexpr uint32_t kSRow = 4u * PWFA_FLUID_MAX_THREADS;
+    if constexpr (STASH) {
+#pragma unroll
+        for (int l = 2; l < kL; ++l)
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) stash_st(sbase + kSRow * ((l - 2) * kQ + q), f[l][q]);
+    }
     if (MOM) {
         // the adjoint's recompute keeps the lattice sums (the reverse step
         // needs nothing else of the populations)
@@ -154,6 +180,12 @@ __device__ __forceinline__ void fluid_rest(const StepArgs& a, int x, int y, int 
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) f[l][q] = fe[q];
             }
+            if constexpr (STASH) {
+                if (l >= 2) {
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) stash_st(sbase + kSRow * ((l - 2) * kQ + q), fe[q]);
+                }
+            }
         }
     }
     // Collide in place, lattice pair by lattice pair; FP32 stores each value
@@ -167,6 +199,12 @@ __device__ __forceinline__ void fluid_rest(const StepArgs& a, int x, int y, int 
             const float Fl = l == 0 ? 0.0f : F[l - 1] * a.dt;
             if (COLL == 0) {
                 // BGK, Eq. 7, plus the source of Eq. 10
+                if constexpr (STASH) {
+                    if (l >= 2) {
+#pragma unroll
+                        for (int q = 0; q < kQ; ++q) f[l][q] = stash_ld(sbase + kSRow * ((l - 2) * kQ + q));
+                    }
+                }
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) f[l][q] = f[l][q] + om * (A[l] * phi[q] - f[l][q]) + wq(q) * Fl;
             } else if (COLL == 1) {
@@ -240,15 +278,15 @@ __device__ __forceinline__ void fluid_rest(const StepArgs& a, int x, int y, int 
 }
 
 // Everything after the gather: moments, then fluid_rest.
-template <int ST, int COLL, bool PER, bool DIAG = false, bool RAW = false, bool MOM = false>
+template <int ST, int COLL, bool PER, bool DIAG = false, bool RAW = false, bool MOM = false, bool PARK = false>
 __device__ __forceinline__ void fluid_compute(const StepArgs& a, int x, int y, int z, float (&f)[kL][kQ], bool bnd,
                                               NodeDiag* nd = nullptr) {
     NodeMoments s;
     fluid_moments<ST, COLL, RAW>(a, f, s);
-    fluid_rest<ST, COLL, PER, DIAG, RAW, MOM>(a, x, y, z, f, bnd, s, nd);
+    fluid_rest<ST, COLL, PER, DIAG, RAW, MOM, PARK>(a, x, y, z, f, bnd, s, nd);
 }
 
-template <int ST, int COLL, bool PER, bool DIAG = false, bool MOM = false>
+template <int ST, int COLL, bool PER, bool DIAG = false, bool MOM = false, bool PARK = false>
 __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int z, NodeDiag* nd = nullptr) {
     using T = typename Codec<ST>::T;
     float f[kL][kQ];
@@ -256,7 +294,7 @@ __device__ __forceinline__ void fluid_node(const StepArgs& a, int x, int y, int 
     // the 16-bit regularized form works in stored units (see fluid_compute)
     constexpr bool RAW = ST != 0 && COLL == 1;
     gather<ST, PER, RAW>(a.g, static_cast<const T*>(a.fin), a.n0, x, y, z, f, bnd, a.src_shift, a.dbg);
-    fluid_compute<ST, COLL, PER, DIAG, RAW, MOM>(a, x, y, z, f, bnd, nd);
+    fluid_compute<ST, COLL, PER, DIAG, RAW, MOM, PARK>(a, x, y, z, f, bnd, nd);
 }
 
 }  // namespace pwfa

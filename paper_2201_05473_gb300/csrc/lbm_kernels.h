@@ -34,6 +34,19 @@ template <int ST, int COLL>
 struct FluidOcc {
     static constexpr int blocks = COLL == 1 ? (ST == 0 ? PWFA_FLUID_MIN_BLOCKS : PWFA_FLUID_MIN_BLOCKS_16) : 4;
 };
+// The batched fluid phase parks BGK's pulled values of lattices 2 and 3 in
+// shared memory between the moments and the collision (fluid_rest), which
+// lets it run at 96 registers and five blocks per SM instead of 128 and
+// four: 64-instance scan 10.99 -> 10.62 ms per step. The single-instance
+// kernel keeps them in registers (3.266 against 3.280 ms parked).
+#ifndef PWFA_BGK_STASH
+#define PWFA_BGK_STASH 1
+#endif
+template <int ST, int COLL>
+struct BatchFluidOcc {
+    static constexpr bool park = COLL == 0 && PWFA_BGK_STASH;
+    static constexpr int blocks = park ? 5 : FluidOcc<ST, COLL>::blocks;
+};
 
 // Where the fused diagnostics of a step go. The fluid launch writes one FP32
 // record of 8 values per warp (sum n, sum n p_x, p_y, p_z, field energy /

@@ -341,13 +341,15 @@ def test_unstable_state_is_reported(defect):
 
 @pytest.mark.parametrize("boundary,collision,nx", [(W.OPEN, W.REGULARIZED, 70), (W.OPEN, W.BGK, 70),
                                                    (W.PERIODIC, W.BGK, 70), (W.OPEN, W.REGULARIZED, 72),
-                                                   (W.OPEN, W.BGK, 72)])
+                                                   (W.OPEN, W.BGK, 72), (W.OPEN, W.BGK, 130),
+                                                   (W.OPEN, W.REGULARIZED, 69), (W.PERIODIC, W.BGK, 69)])
 def test_fused_field_step(boundary, collision, nx):
     """Ampere fused with the next step's Faraday (one kernel, tiles of 31 x 7
     nodes over 16 planes, E of the +1 neighbours evaluated twice) against the
     separate kernels on a grid that spans several tiles in every direction
-    with ragged ends: the same arithmetic, so the same state bit for bit,
-    also across a state import and through the fused step diagnostics."""
+    with ragged ends (nx = 130: four full x tiles and a 6-column one; odd
+    nx, periodic or open): the same arithmetic, so the same state bit for
+    bit, also across a state import and through the fused step diagnostics."""
     w = W.parity_small().replace(nx=nx, ny=23, nz=37, boundary=boundary, collision=collision, alpha=0.5,
                                  z0=-1.0, tau=0.6)
     with lbm.Simulation(w) as a, lbm.Simulation(w) as b:
