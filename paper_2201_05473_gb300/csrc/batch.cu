@@ -17,6 +17,8 @@ namespace {
 
 static_assert(sizeof(StepArgs) % 4 == 0 && sizeof(StepArgs) / 4 <= kBatchTile, "StepArgs copy");
 static_assert(sizeof(FieldPair) % 4 == 0 && sizeof(FieldPair) / 4 <= kBatchTile, "FieldPair copy");
+// the parked BGK values take one shared-memory column per thread of a block
+static_assert(kBatchTile <= PWFA_FLUID_MAX_THREADS, "BGK park columns");
 
 // The block's instance arguments, copied once into shared memory (every
 // thread reads them).
